@@ -1,0 +1,186 @@
+"""Python access to the plain FP64 CPU oracle (oracle/evsl_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` are the only callers.  The CUDA path never imports this package, and this package
+imports nothing from the CUDA path.  Each wrapper names the paper passage the C function
+follows (arXiv:1802.05215, Sections 2.1-2.5 and Algorithm 2).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "evsl_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+DAMP_NONE, DAMP_JACKSON, DAMP_SIGMA = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(_LIB)
+        d, i32, i64, u64 = C.c_double, C.c_int, C.c_int64, C.c_uint64
+        P = C.c_void_p
+        _lib.orc_draw.restype = u64
+        _lib.orc_draw.argtypes = [u64, u64, u64]
+        _lib.orc_splitmix64_next.restype = u64
+        _lib.orc_splitmix64_next.argtypes = [P]
+        _lib.orc_spmv.argtypes = [i64, P, P, P, P, P]
+        _lib.orc_syev.restype = i32
+        _lib.orc_syev.argtypes = [i32, P, P, P]
+        _lib.orc_bounds.restype = i32
+        _lib.orc_bounds.argtypes = [i64, P, P, P, i32, u64, P, P]
+        _lib.orc_kpm_moments.restype = i32
+        _lib.orc_kpm_moments.argtypes = [i64, P, P, P, i32, i32, u64, d, d, P]
+        _lib.orc_jackson.argtypes = [i32, P]
+        _lib.orc_dos_count.restype = d
+        _lib.orc_dos_count.argtypes = [P, i32, d, d, d]
+        _lib.orc_slicer.restype = i32
+        _lib.orc_slicer.argtypes = [P, i32, d, d, d, d, i32, i32, P, P]
+        _lib.orc_filter_build.restype = i32
+        _lib.orc_filter_build.argtypes = [d, d, d, d, d, d, i32, i32, P, P, P, P, i32, P]
+        _lib.orc_filter_apply.argtypes = [i64, P, P, P, d, d, i32, P, i32, P, P]
+        _lib.orc_cheblantr.restype = i32
+        _lib.orc_cheblantr.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d,
+                                       i32, i32, i32, d, d, u64, i32, P, P, P, P, P]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _csr_args(A):
+    return (A.n, _p(A.row_ptr), _p(A.col_idx), _p(A.val))
+
+
+def draw(seed: int, stream: int, k: int) -> int:
+    return int(_load().orc_draw(seed, stream, k))
+
+
+def splitmix64_sequence(seed: int, count: int) -> list[int]:
+    st = C.c_uint64(seed)
+    lib = _load()
+    return [int(lib.orc_splitmix64_next(C.byref(st))) for _ in range(count)]
+
+
+def spmv(A, x: np.ndarray) -> np.ndarray:
+    """y = A x (CSR, Sec. 3.1)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(A.n)
+    _load().orc_spmv(*_csr_args(A), _p(x), _p(y))
+    return y
+
+
+def syev(Amat: np.ndarray):
+    """Eigenvalues (ascending) and eigenvectors of a dense symmetric matrix
+    (Householder tridiagonalisation + implicit symmetric QR)."""
+    n = Amat.shape[0]
+    a = np.asfortranarray(Amat, dtype=np.float64)
+    w = np.empty(n)
+    z = np.empty((n, n), order="F")
+    st = _load().orc_syev(n, _p(a), _p(w), _p(z))
+    if st != 0:
+        raise RuntimeError("oracle syev did not converge")
+    return w, z
+
+
+def bounds(A, steps: int = 80, seed: int = 0):
+    """Spectral bounds by a short Lanczos run (Sec. 2.2.1, LanTrbounds)."""
+    lo, hi = C.c_double(), C.c_double()
+    st = _load().orc_bounds(*_csr_args(A), steps, seed, C.byref(lo), C.byref(hi))
+    if st != 0:
+        raise RuntimeError("oracle bounds failed")
+    return lo.value, hi.value
+
+
+def kpm_moments(A, degree: int, nvec: int, seed: int, lmin: float, lmax: float) -> np.ndarray:
+    """KPM moments mu_0..mu_degree with Rademacher probes (Sec. 2.1)."""
+    mu = np.empty(degree + 1)
+    _load().orc_kpm_moments(*_csr_args(A), degree, nvec, seed, lmin, lmax, _p(mu))
+    return mu
+
+
+def jackson(M: int) -> np.ndarray:
+    g = np.empty(M + 1)
+    _load().orc_jackson(M, _p(g))
+    return g
+
+
+def dos_count(mu: np.ndarray, lmin: float, lmax: float, t: float) -> float:
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    return float(_load().orc_dos_count(_p(mu), len(mu) - 1, lmin, lmax, t))
+
+
+def slicer(mu, lmin, lmax, xi, eta, nslices, npts=None):
+    """DOS-balanced slice ends (Eq. (2.2), spslicer)."""
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    npts = npts or max(2001, 100 * nslices)
+    sli = np.empty(nslices + 1)
+    est = np.empty(nslices)
+    st = _load().orc_slicer(_p(mu), len(mu) - 1, lmin, lmax, xi, eta, nslices, npts,
+                            _p(sli), _p(est))
+    if st != 0:
+        raise ValueError("oracle slicer: bad arguments")
+    return sli, est
+
+
+def filter_build(a, b, lmin, lmax, tau=0.8, damping=DAMP_JACKSON, maxdeg=10000, tau_ext=0.4):
+    """Chebyshev delta filter for [a, b] (Sec. 2.2.1).  Returns a dict."""
+    cap = maxdeg + 1
+    coef = np.empty(cap)
+    deg, gam, bar, bnd = C.c_int(), C.c_double(), C.c_double(), C.c_int()
+    st = _load().orc_filter_build(a, b, lmin, lmax, tau, tau_ext, damping, maxdeg, C.byref(deg),
+                                  C.byref(gam), C.byref(bar), _p(coef), cap, C.byref(bnd))
+    if st not in (0, -2):
+        raise ValueError(f"oracle filter_build failed ({st})")
+    return dict(deg=deg.value, gamma=gam.value, bar=bar.value, coef=coef[:deg.value + 1].copy(),
+                boundary=bnd.value, lmin=lmin, lmax=lmax, a=a, b=b, reached_max=(st == -2))
+
+
+def filter_apply(A, lmin, lmax, coef, X: np.ndarray) -> np.ndarray:
+    """Y = rho(Ahat) X for each column of X (Eq. (2.4))."""
+    X = np.asfortranarray(X.reshape(A.n, -1), dtype=np.float64)
+    nvec = X.shape[1]
+    Y = np.empty_like(X, order="F")
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    _load().orc_filter_apply(*_csr_args(A), lmin, lmax, len(coef) - 1, _p(coef), nvec,
+                             _p(X), _p(Y))
+    return Y
+
+
+def cheblantr(A, a, b, pol, m=100, maxit=None, ncycle=10, tol=1e-8, tau1=1e-10, seed=0,
+              cap=None, right_closed=True):
+    """Filtered thick-restart Lanczos with locking (Algorithm 2).  Returns a dict."""
+    cap = cap or (m + 64)
+    maxit = maxit or 20 * m
+    lam = np.empty(cap)
+    res = np.empty(cap)
+    Y = np.empty((A.n, cap), order="F")
+    nev = C.c_int()
+    stats = np.zeros(4, dtype=np.int64)
+    coef = np.ascontiguousarray(pol["coef"], dtype=np.float64)
+    st = _load().orc_cheblantr(*_csr_args(A), a, b, int(right_closed), pol["lmin"], pol["lmax"],
+                               len(coef) - 1, _p(coef), pol["bar"], m, maxit, ncycle, tol, tau1,
+                               seed, cap, C.byref(nev), _p(lam), _p(Y), _p(res), _p(stats))
+    k = nev.value
+    return dict(status=st, nev=k, lam=lam[:k].copy(), Y=Y[:, :k].copy(), res=res[:k].copy(),
+                niter=int(stats[0]), nmv=int(stats[1]), nrestart=int(stats[2]),
+                npass=int(stats[3]))

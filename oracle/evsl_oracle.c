@@ -1,0 +1,808 @@
+/*
+ * evsl_oracle.c -- plain, slow, FP64 CPU oracle for polynomial-filtered spectrum slicing
+ * (Li, Xi, Erlandson, Saad, "The Eigenvalues Slicing Library (EVSL)", arXiv:1802.05215).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg may load this code.  It shares nothing with the CUDA path: no headers, no helpers, no
+ * tables.  Every loop is written in the order the paper states the method, without blocking,
+ * fusion or reordering, so that it can be read against the paper.  Built with
+ * -ffp-contract=off (no fused multiply-add).
+ *
+ * Contents (paper passage in brackets):
+ *   SplitMix64 counter-based draws  [seeded inputs; Steele-Lea-Flood 2014]
+ *   CSR SpMV                         [Sec. 3.1, CSR storage]
+ *   dense symmetric eigensolver      [Householder tridiagonalisation + implicit symmetric QR
+ *                                     with Wilkinson shift, Golub & Van Loan Sec. 8.3]
+ *   spectral bounds by Lanczos       [Sec. 2.2.1 text after Eq. (2.3); LanTrbounds Sec. 3.1]
+ *   KPM moments, Jackson damping, cumulative DOS, slicer  [Sec. 2.1, Eqs. (2.1)-(2.2)]
+ *   Chebyshev filter build           [Sec. 2.2.1, Eqs. (2.3)-(2.6)]
+ *   filter application               [Eq. (2.4) with the mapping of Eq. (2.3)]
+ *   filtered thick-restart Lanczos with locking  [Sec. 2.3, Eqs. (2.10)-(2.11); Algorithm 2]
+ *
+ * Readings of passages that the paper leaves open are marked READING in the comments.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------------------ */
+/* SplitMix64, used counter-based: draw(s,t,k) = (k+1)-th output of SplitMix64 seeded with
+ * key(s,t) = first output of SplitMix64 seeded with s ^ (t * 0xD1B54A32D192ED03).         */
+static uint64_t orc_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t orc_splitmix64_next(uint64_t *state)
+{
+    *state += 0x9E3779B97F4A7C15ULL;
+    return orc_mix(*state);
+}
+
+uint64_t orc_draw(uint64_t seed, uint64_t stream, uint64_t k)
+{
+    uint64_t s = seed ^ (stream * 0xD1B54A32D192ED03ULL);
+    uint64_t key = orc_splitmix64_next(&s);
+    uint64_t st = key + k * 0x9E3779B97F4A7C15ULL;
+    return orc_splitmix64_next(&st);
+}
+
+static double orc_unit(uint64_t x) { return (double)(x >> 11) * (1.0 / 9007199254740992.0); }
+static double orc_sign(uint64_t x) { return (x >> 63) ? -1.0 : 1.0; }
+
+enum { ORC_STREAM_ANDERSON = 1, ORC_STREAM_KPM = 2, ORC_STREAM_LANCZOS = 3, ORC_STREAM_BOUNDS = 4 };
+
+/* ------------------------------------------------------------------------------------ */
+/* Sparse matrix in CSR form (Sec. 3.1): y = A x.                                          */
+typedef struct {
+    int64_t n;
+    const int64_t *rp;
+    const int32_t *ci;
+    const double *v;
+} orc_csr;
+
+static void orc_matvec(const orc_csr *A, const double *x, double *y)
+{
+    for (int64_t i = 0; i < A->n; i++) {
+        double s = 0.0;
+        for (int64_t p = A->rp[i]; p < A->rp[i + 1]; p++)
+            s += A->v[p] * x[A->ci[p]];
+        y[i] = s;
+    }
+}
+
+void orc_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+              const double *x, double *y)
+{
+    orc_csr A = {n, rp, ci, v};
+    orc_matvec(&A, x, y);
+}
+
+static double orc_dot(int64_t n, const double *x, const double *y)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += x[i] * y[i];
+    return s;
+}
+
+static double orc_nrm2(int64_t n, const double *x) { return sqrt(orc_dot(n, x, x)); }
+
+/* Mapped operator of Eq. (2.3): y = (A x - c x) / d.                                      */
+static void orc_mapped_matvec(const orc_csr *A, double c, double d, const double *x, double *y)
+{
+    orc_matvec(A, x, y);
+    for (int64_t i = 0; i < A->n; i++) y[i] = (y[i] - c * x[i]) / d;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Dense symmetric eigensolver (Golub & Van Loan, Matrix Computations, Sec. 8.3):
+ * Householder tridiagonalisation (Alg. 8.3.1) with the orthogonal factor accumulated,
+ * then the implicit symmetric QR algorithm with Wilkinson shift (Algs. 8.3.2-8.3.3),
+ * every Givens rotation accumulated into the eigenvector matrix.
+ * A: n x n column-major symmetric (read only).  w: eigenvalues ascending.  Z: n x n
+ * column-major eigenvectors (may be NULL).  Returns 0, or -1 if QR did not converge.    */
+#define AT(M, i, j, ld) (M)[(size_t)(j) * (ld) + (i)]
+
+int orc_syev(int n, const double *Ain, double *w, double *Zout)
+{
+    if (n <= 0) return 0;
+    double *A = malloc(sizeof(double) * n * n);
+    double *Q = malloc(sizeof(double) * n * n);
+    double *vv = malloc(sizeof(double) * n);
+    double *pp = malloc(sizeof(double) * n);
+    double *d = malloc(sizeof(double) * n);
+    double *e = malloc(sizeof(double) * n);
+    memcpy(A, Ain, sizeof(double) * n * n);
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) AT(Q, i, j, n) = (i == j) ? 1.0 : 0.0;
+
+    /* Householder tridiagonalisation: at step k reflect x = A[k+1:n, k] onto alpha e_1.  */
+    for (int k = 0; k + 2 < n; k++) {
+        int m = n - k - 1;
+        double xn = 0.0;
+        for (int i = 0; i < m; i++) xn += AT(A, k + 1 + i, k, n) * AT(A, k + 1 + i, k, n);
+        xn = sqrt(xn);
+        if (xn == 0.0) continue;
+        double alpha = (AT(A, k + 1, k, n) > 0.0) ? -xn : xn;
+        for (int i = 0; i < m; i++) vv[i] = AT(A, k + 1 + i, k, n);
+        vv[0] -= alpha;
+        double vn2 = 0.0;
+        for (int i = 0; i < m; i++) vn2 += vv[i] * vv[i];
+        if (vn2 == 0.0) continue;
+        double beta = 2.0 / vn2;
+        /* p = beta * A22 v ; w = p - (beta/2)(p.v) v ; A22 -= v w^T + w v^T              */
+        for (int i = 0; i < m; i++) {
+            double s = 0.0;
+            for (int j = 0; j < m; j++) s += AT(A, k + 1 + i, k + 1 + j, n) * vv[j];
+            pp[i] = beta * s;
+        }
+        double pv = 0.0;
+        for (int i = 0; i < m; i++) pv += pp[i] * vv[i];
+        double K = 0.5 * beta * pv;
+        for (int i = 0; i < m; i++) pp[i] -= K * vv[i];
+        for (int j = 0; j < m; j++)
+            for (int i = 0; i < m; i++)
+                AT(A, k + 1 + i, k + 1 + j, n) -= vv[i] * pp[j] + pp[i] * vv[j];
+        AT(A, k + 1, k, n) = alpha;
+        AT(A, k, k + 1, n) = alpha;
+        for (int i = 1; i < m; i++) {
+            AT(A, k + 1 + i, k, n) = 0.0;
+            AT(A, k, k + 1 + i, n) = 0.0;
+        }
+        /* Q = Q (I - beta v v^T) on columns k+1..n-1                                      */
+        for (int r = 0; r < n; r++) {
+            double s = 0.0;
+            for (int j = 0; j < m; j++) s += AT(Q, r, k + 1 + j, n) * vv[j];
+            s *= beta;
+            for (int j = 0; j < m; j++) AT(Q, r, k + 1 + j, n) -= s * vv[j];
+        }
+    }
+    for (int i = 0; i < n; i++) d[i] = AT(A, i, i, n);
+    for (int i = 0; i + 1 < n; i++) e[i] = AT(A, i + 1, i, n);
+    e[n - 1] = 0.0;
+
+    /* Implicit symmetric QR.  Rotation on (k,k+1): rows' = [c -s; s c] rows, and the same
+     * on columns; the accumulated eigenvector matrix gets col_k' = c col_k - s col_{k+1},
+     * col_{k+1}' = s col_k + c col_{k+1}.                                                 */
+    const double eps = 2.220446049250313e-16;
+    int status = 0;
+    long iter = 0, maxiter = 60L * n + 100;
+    int hi = n - 1;
+    while (hi > 0) {
+        if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+            e[hi - 1] = 0.0;
+            hi--;
+            continue;
+        }
+        int lo = hi - 1;
+        while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) lo--;
+        if (lo > 0) e[lo - 1] = 0.0;
+        if (++iter > maxiter) { status = -1; break; }
+        /* Wilkinson shift from the trailing 2x2 of the block                               */
+        double del = 0.5 * (d[hi - 1] - d[hi]);
+        double eb = e[hi - 1];
+        double sg = (del >= 0.0) ? 1.0 : -1.0;
+        double mu = d[hi] - eb * eb / (del + sg * sqrt(del * del + eb * eb));
+        double x = d[lo] - mu, z = e[lo];
+        double bulge = 0.0;
+        for (int k = lo; k < hi; k++) {
+            double r = sqrt(x * x + z * z);
+            double c = (r == 0.0) ? 1.0 : x / r;
+            double s = (r == 0.0) ? 0.0 : -z / r;
+            if (k > lo) {
+                /* rotate column k-1: [e[k-1]; bulge] -> [r; 0]                              */
+                e[k - 1] = c * e[k - 1] - s * bulge;
+            }
+            double a = d[k], b = e[k], cc = d[k + 1];
+            d[k] = c * c * a - 2.0 * c * s * b + s * s * cc;
+            d[k + 1] = s * s * a + 2.0 * c * s * b + c * c * cc;
+            e[k] = c * s * (a - cc) + (c * c - s * s) * b;
+            if (k + 1 < hi) {
+                bulge = -s * e[k + 1];
+                e[k + 1] = c * e[k + 1];
+                x = e[k];
+                z = bulge;
+            }
+            for (int rr = 0; rr < n; rr++) {
+                double qk = AT(Q, rr, k, n), qk1 = AT(Q, rr, k + 1, n);
+                AT(Q, rr, k, n) = c * qk - s * qk1;
+                AT(Q, rr, k + 1, n) = s * qk + c * qk1;
+            }
+        }
+    }
+    /* sort ascending (selection sort keeps it obvious)                                     */
+    for (int i = 0; i < n; i++) {
+        int best = i;
+        for (int j = i + 1; j < n; j++)
+            if (d[j] < d[best]) best = j;
+        if (best != i) {
+            double t = d[i]; d[i] = d[best]; d[best] = t;
+            for (int rr = 0; rr < n; rr++) {
+                double q = AT(Q, rr, i, n);
+                AT(Q, rr, i, n) = AT(Q, rr, best, n);
+                AT(Q, rr, best, n) = q;
+            }
+        }
+    }
+    for (int i = 0; i < n; i++) w[i] = d[i];
+    if (Zout) memcpy(Zout, Q, sizeof(double) * n * n);
+    free(A); free(Q); free(vv); free(pp); free(d); free(e);
+    return status;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Full reorthogonalisation (Sec. 2.3): at most two passes of classical Gram-Schmidt
+ * against the columns of the blocks, the second pass taken only when the DGKS test
+ * ||z_after|| < eta ||z_before|| (eta = 1/sqrt(2)) says that the first one lost too much.
+ * READING: eta = 1/sqrt(2), the classical Daniel-Gragg-Kaufman-Stewart choice.
+ * Blocks are column-major n x ncol with leading dimension n.  Returns the number of passes. */
+static int orc_reorth(int64_t n, double *z, const double *B1, int nc1, const double *B2, int nc2)
+{
+    double *h = malloc(sizeof(double) * (size_t)(nc1 + nc2 + 1));
+    int passes = 0;
+    for (int pass = 0; pass < 2; pass++) {
+        double before = orc_nrm2(n, z);
+        for (int j = 0; j < nc1; j++) h[j] = orc_dot(n, B1 + (size_t)j * n, z);
+        for (int j = 0; j < nc2; j++) h[nc1 + j] = orc_dot(n, B2 + (size_t)j * n, z);
+        for (int j = 0; j < nc1; j++) {
+            const double *b = B1 + (size_t)j * n;
+            for (int64_t i = 0; i < n; i++) z[i] -= h[j] * b[i];
+        }
+        for (int j = 0; j < nc2; j++) {
+            const double *b = B2 + (size_t)j * n;
+            for (int64_t i = 0; i < n; i++) z[i] -= h[nc1 + j] * b[i];
+        }
+        passes++;
+        double after = orc_nrm2(n, z);
+        if (after >= 0.7071067811865476 * before) break;
+    }
+    free(h);
+    return passes;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Spectral bounds (Sec. 2.2.1: "a few steps of the Lanczos algorithm"; LanTrbounds).
+ * READING: `steps` Lanczos steps with full reorthogonalisation from the seeded start vector
+ * (stream 4); the bounds are the extreme Ritz values widened by their residual bounds,
+ * lmin = theta_1 - |beta_{m+1} s_{m,1}|, lmax = theta_m + |beta_{m+1} s_{m,m}|.            */
+int orc_bounds(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+               int steps, uint64_t seed, double *lmin, double *lmax)
+{
+    orc_csr A = {n, rp, ci, v};
+    if (steps > n) steps = (int)n;
+    if (steps < 1) return -1;
+    double *Q = calloc((size_t)n * (steps + 1), sizeof(double));
+    double *T = calloc((size_t)steps * steps, sizeof(double));
+    double *z = malloc(sizeof(double) * n);
+    for (int64_t i = 0; i < n; i++)
+        Q[i] = 2.0 * orc_unit(orc_draw(seed, ORC_STREAM_BOUNDS, (uint64_t)i)) - 1.0;
+    double nq = orc_nrm2(n, Q);
+    for (int64_t i = 0; i < n; i++) Q[i] /= nq;
+    double beta = 0.0;
+    int m = 0;
+    for (int j = 0; j < steps; j++) {
+        double *qj = Q + (size_t)j * n;
+        orc_matvec(&A, qj, z);
+        if (j > 0) {
+            double *qp = Q + (size_t)(j - 1) * n;
+            for (int64_t i = 0; i < n; i++) z[i] -= beta * qp[i];
+        }
+        double alpha = orc_dot(n, qj, z);
+        for (int64_t i = 0; i < n; i++) z[i] -= alpha * qj[i];
+        orc_reorth(n, z, Q, j + 1, NULL, 0);
+        AT(T, j, j, steps) = alpha;
+        beta = orc_nrm2(n, z);
+        m = j + 1;
+        if (j + 1 < steps) {
+            AT(T, j, j + 1, steps) = beta;
+            AT(T, j + 1, j, steps) = beta;
+        }
+        if (beta == 0.0) break;
+        double *qn = Q + (size_t)(j + 1) * n;
+        for (int64_t i = 0; i < n; i++) qn[i] = z[i] / beta;
+    }
+    double *Tm = malloc(sizeof(double) * m * m), *w = malloc(sizeof(double) * m),
+           *S = malloc(sizeof(double) * m * m);
+    for (int j = 0; j < m; j++)
+        for (int i = 0; i < m; i++) AT(Tm, i, j, m) = AT(T, i, j, steps);
+    int st = orc_syev(m, Tm, w, S);
+    *lmin = w[0] - fabs(beta * AT(S, m - 1, 0, m));
+    *lmax = w[m - 1] + fabs(beta * AT(S, m - 1, m - 1, m));
+    free(Q); free(T); free(z); free(Tm); free(w); free(S);
+    return st;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Kernel polynomial method (Sec. 2.1; the paper cites Lin, Saad and Yang for the formulas).
+ * With Ahat = (A - cI)/d of Eq. (2.3) and nvec Rademacher probes v_l (stream 2, k = l*n+i):
+ *   mu_k = (1/nvec) sum_l v_l^T T_k(Ahat) v_l ,  k = 0..M   (so mu_0 = n exactly),
+ * by the three-term recurrence w_0 = v, w_1 = Ahat v, w_{k+1} = 2 Ahat w_k - w_{k-1}.      */
+int orc_kpm_moments(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                    int M, int nvec, uint64_t seed, double lmin, double lmax, double *mu)
+{
+    orc_csr A = {n, rp, ci, v};
+    double c = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+    double *vl = malloc(sizeof(double) * n), *w0 = malloc(sizeof(double) * n),
+           *w1 = malloc(sizeof(double) * n), *w2 = malloc(sizeof(double) * n);
+    for (int k = 0; k <= M; k++) mu[k] = 0.0;
+    for (int l = 0; l < nvec; l++) {
+        for (int64_t i = 0; i < n; i++)
+            vl[i] = orc_sign(orc_draw(seed, ORC_STREAM_KPM, (uint64_t)l * (uint64_t)n + (uint64_t)i));
+        memcpy(w0, vl, sizeof(double) * n);
+        mu[0] += orc_dot(n, vl, w0);
+        if (M >= 1) {
+            orc_mapped_matvec(&A, c, d, w0, w1);
+            mu[1] += orc_dot(n, vl, w1);
+        }
+        for (int k = 1; k < M; k++) {
+            orc_mapped_matvec(&A, c, d, w1, w2);
+            for (int64_t i = 0; i < n; i++) w2[i] = 2.0 * w2[i] - w0[i];
+            mu[k + 1] += orc_dot(n, vl, w2);
+            double *t = w0; w0 = w1; w1 = w2; w2 = t;
+        }
+    }
+    for (int k = 0; k <= M; k++) mu[k] /= nvec;
+    free(vl); free(w0); free(w1); free(w2);
+    return 0;
+}
+
+/* Jackson damping factors for a degree-M expansion (standard KPM kernel, Weisse et al.,
+ * Rev. Mod. Phys. 78 (2006)); READING: the variant with M+2 in the denominator.
+ *   g_k = [(M-k+2) cos(k a) + sin(k a) cot(a)] / (M+2),  a = pi/(M+2),  k = 0..M.         */
+void orc_jackson(int M, double *g)
+{
+    double a = M_PI / (M + 2);
+    for (int k = 0; k <= M; k++)
+        g[k] = ((M - k + 2) * cos(k * a) + sin(k * a) * (cos(a) / sin(a))) / (M + 2);
+}
+
+/* Cumulative DOS count on [lmin, t] from Jackson-damped moments (Eq. (2.1) integrated):
+ * with th = arccos(that), that = (t-c)/d clamped to [-1,1],
+ *   N(t) = (1/pi) [ g_0 mu_0 (pi - th) - 2 sum_{k>=1} g_k mu_k sin(k th)/k ].              */
+double orc_dos_count(const double *mu, int M, double lmin, double lmax, double t)
+{
+    double c = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+    double th = (t - c) / d;
+    if (th < -1.0) th = -1.0;
+    if (th > 1.0) th = 1.0;
+    th = acos(th);
+    double *g = malloc(sizeof(double) * (M + 1));
+    orc_jackson(M, g);
+    double s = g[0] * mu[0] * (M_PI - th);
+    for (int k = 1; k <= M; k++) s -= 2.0 * g[k] * mu[k] * sin(k * th) / k;
+    free(g);
+    return s / M_PI;
+}
+
+/* Slicer of Eq. (2.2) (spslicer): npts evenly spaced x_j on [xi, eta]; C_j = N(x_j);
+ * t_i = the first x_j with C_j - C_0 >= (i/ns)(C_{N-1} - C_0), refined by linear
+ * interpolation between x_{j-1} and x_j.  READING: first crossing + linear interpolation.
+ * est[i] = N(t_{i+1}) - N(t_i) from the same DOS.                                         */
+int orc_slicer(const double *mu, int M, double lmin, double lmax, double xi, double eta,
+               int ns, int npts, double *sli, double *est)
+{
+    if (ns < 1 || npts < 2 || !(eta > xi)) return -1;
+    double *x = malloc(sizeof(double) * npts), *C = malloc(sizeof(double) * npts);
+    for (int j = 0; j < npts; j++) {
+        x[j] = xi + (eta - xi) * j / (npts - 1);
+        C[j] = orc_dos_count(mu, M, lmin, lmax, x[j]);
+    }
+    double total = C[npts - 1] - C[0];
+    sli[0] = xi;
+    sli[ns] = eta;
+    int j = 1;
+    for (int i = 1; i < ns; i++) {
+        double target = total * i / ns;
+        while (j < npts - 1 && C[j] - C[0] < target) j++;
+        double c0 = C[j - 1] - C[0], c1 = C[j] - C[0];
+        double f = (c1 > c0) ? (target - c0) / (c1 - c0) : 1.0;
+        if (f < 0.0) f = 0.0;
+        if (f > 1.0) f = 1.0;
+        sli[i] = x[j - 1] + f * (x[j] - x[j - 1]);
+    }
+    for (int i = 0; i < ns; i++)
+        est[i] = orc_dos_count(mu, M, lmin, lmax, sli[i + 1]) - orc_dos_count(mu, M, lmin, lmax, sli[i]);
+    free(x); free(C);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Chebyshev delta filter (Sec. 2.2.1).  rho(t) = sum_j g_j mu_j T_j(t) / sum_j g_j mu_j T_j(gamma)
+ * with mu_0 = 1/2, mu_j = cos(j arccos gamma) (Eqs. (2.4)-(2.5)) and damping g_j (Eq. (2.6)).
+ * T_j is evaluated from its definition cos(j arccos t) (cosh form outside [-1,1]).        */
+enum { ORC_DAMP_NONE = 0, ORC_DAMP_JACKSON = 1, ORC_DAMP_SIGMA = 2 };
+
+static double orc_chebT(int j, double t)
+{
+    if (t >= -1.0 && t <= 1.0) return cos(j * acos(t));
+    double s = (t < 0.0 && (j & 1)) ? -1.0 : 1.0;
+    return s * cosh(j * acosh(fabs(t)));
+}
+
+static void orc_damping(int type, int k, double *g)
+{
+    g[0] = 1.0;
+    for (int j = 1; j <= k; j++) {
+        if (type == ORC_DAMP_SIGMA) {              /* Lanczos sigma factors, Eq. (2.6)    */
+            double th = M_PI / (k + 1);
+            g[j] = sin(j * th) / (j * th);
+        } else if (type == ORC_DAMP_JACKSON) {     /* Jackson factors for degree k        */
+            double a = M_PI / (k + 2);
+            g[j] = ((k - j + 2) * cos(j * a) + sin(j * a) * (cos(a) / sin(a))) / (k + 2);
+        } else {
+            g[j] = 1.0;
+        }
+    }
+}
+
+/* Unnormalised filter value P(t) = sum_j g_j mu_j(gamma) T_j(t), gamma = cos(th).         */
+static double orc_P(int k, const double *g, double th, double t)
+{
+    double s = 0.5 * g[0];
+    for (int j = 1; j <= k; j++) s += g[j] * cos(j * th) * orc_chebT(j, t);
+    return s;
+}
+
+/* Balance equation of Eq. (2.7): rho(ta) - rho(tb) = 0 in the unknown gamma = cos(th).
+ * READING: the garbled index in Eq. (2.7) is read as the two ends of the same interval.
+ * Since both sides share the denominator, solve f(th) = P(ta) - P(tb) = 0 for th in
+ * [acos(tb), acos(ta)] by Newton's method safeguarded with bisection.                     */
+static double orc_balance(int k, const double *g, double ta, double tb)
+{
+    double lo = acos(tb), hi = acos(ta);    /* acos decreasing: lo < hi                    */
+    double flo = orc_P(k, g, lo, ta) - orc_P(k, g, lo, tb);
+    double fhi = orc_P(k, g, hi, ta) - orc_P(k, g, hi, tb);
+    if (flo * fhi > 0.0) return 0.5 * (lo + hi);   /* no sign change: centre of interval  */
+    double th = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; it++) {
+        double f = 0.0, fp = 0.0;
+        for (int j = 1; j <= k; j++) {
+            double dT = orc_chebT(j, ta) - orc_chebT(j, tb);
+            f += g[j] * cos(j * th) * dT;
+            fp -= g[j] * j * sin(j * th) * dT;
+        }
+        if ((f < 0.0) == (flo < 0.0)) { lo = th; flo = f; } else { hi = th; }
+        double nt = (fp != 0.0) ? th - f / fp : 0.5 * (lo + hi);
+        if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
+        double step = fabs(nt - th);
+        th = nt;
+        if (step < 1e-14) break;
+    }
+    return th;
+}
+
+/* Filter construction (find_pol, Sec. 2.2.1): for k = 2, 3, ... balance gamma, and stop at
+ * the first k whose end value bar = rho(ta) = rho(tb) is <= tau (default 0.8).
+ * Boundary slices (READING; the paper only says that a special, lower-degree filter is
+ * used for them, Sec. 4.2): when ta <= -1 the filter is centred at gamma = -1 (the left end
+ * of the spectrum) with the same damping, and k grows until rho(tb) <= tau_ext (default
+ * 0.4); bar = rho(tb).  Mirrored (gamma = 1, rho(ta) <= tau_ext) when tb >= 1.  With Lanczos
+ * sigma damping this reproduces the boundary-slice degrees 5, 6, 7, 8, 8, 9 of Table 4.
+ * An interval covering the whole spectrum (ta <= -1 and tb >= 1) is rejected.
+ * Output coef[j] = g_j mu_j / P(gamma), j = 0..deg.  Returns 0, -1 on bad input, -2 if
+ * maxdeg was reached, -5 if cap < deg+1 (deg then holds the needed degree).              */
+int orc_filter_build(double a, double b, double lmin, double lmax, double tau, double tau_ext,
+                     int damping, int maxdeg, int *deg, double *gamma, double *bar,
+                     double *coef, int cap, int *boundary)
+{
+    if (!(b > a) || !(lmax > lmin) || maxdeg < 2) return -1;
+    double c = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+    double ta = (a - c) / d, tb = (b - c) / d;
+    int left = (ta <= -1.0), right = (tb >= 1.0);
+    if (left && right) return -1;
+    double *g = malloc(sizeof(double) * (maxdeg + 1));
+    *boundary = left ? -1 : (right ? 1 : 0);
+    int status = -2, k;
+    double th = 0.0, bv = 0.0, Pg = 1.0;
+    for (k = 2; k <= maxdeg; k++) {
+        if (left || right) {
+            orc_damping(damping, k, g);
+            th = left ? M_PI : 0.0;
+            Pg = orc_P(k, g, th, cos(th));
+            bv = orc_P(k, g, th, left ? tb : ta) / Pg;
+            if (bv <= tau_ext) { status = 0; break; }
+        } else {
+            orc_damping(damping, k, g);
+            th = orc_balance(k, g, ta, tb);
+            Pg = orc_P(k, g, th, cos(th));
+            bv = orc_P(k, g, th, ta) / Pg;
+            if (bv <= tau) { status = 0; break; }
+        }
+    }
+    if (status != 0) k = maxdeg;
+    *deg = k;
+    *gamma = cos(th);
+    *bar = bv;
+    if (k + 1 > cap) { free(g); return status ? status : -5; }
+    coef[0] = 0.5 * g[0] / Pg;
+    for (int j = 1; j <= k; j++) coef[j] = g[j] * cos(j * th) / Pg;
+    free(g);
+    return status;
+}
+
+/* Filter application y = rho(Ahat) x = sum_j coef_j T_j(Ahat) x with the three-term
+ * recurrence of the Chebyshev polynomials and Ahat of Eq. (2.3).                          */
+static void orc_filter_apply_csr(const orc_csr *A, double c, double d, int deg,
+                                 const double *coef, const double *x, double *y,
+                                 double *w0, double *w1, double *w2)
+{
+    int64_t n = A->n;
+    memcpy(w0, x, sizeof(double) * n);
+    for (int64_t i = 0; i < n; i++) y[i] = coef[0] * w0[i];
+    if (deg < 1) return;
+    orc_mapped_matvec(A, c, d, w0, w1);
+    for (int64_t i = 0; i < n; i++) y[i] += coef[1] * w1[i];
+    for (int j = 1; j < deg; j++) {
+        orc_mapped_matvec(A, c, d, w1, w2);
+        for (int64_t i = 0; i < n; i++) w2[i] = 2.0 * w2[i] - w0[i];
+        for (int64_t i = 0; i < n; i++) y[i] += coef[j + 1] * w2[i];
+        double *t = w0; w0 = w1; w1 = w2; w2 = t;
+    }
+}
+
+void orc_filter_apply(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                      double lmin, double lmax, int deg, const double *coef, int nvec,
+                      const double *X, double *Y)
+{
+    orc_csr A = {n, rp, ci, v};
+    double c = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+    double *w0 = malloc(sizeof(double) * n), *w1 = malloc(sizeof(double) * n),
+           *w2 = malloc(sizeof(double) * n);
+    for (int l = 0; l < nvec; l++)
+        orc_filter_apply_csr(&A, c, d, deg, coef, X + (size_t)l * n, Y + (size_t)l * n, w0, w1, w2);
+    free(w0); free(w1); free(w2);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Filtered thick-restart Lanczos with locking (Algorithm 2, Sec. 2.5) for A x = lambda x.
+ *
+ * Operator: (I - U U^T) rho(A) with rho the filter above; the deflation by the locked set U
+ * is applied through the full reorthogonalisation against [U, Q] (U has orthonormal columns
+ * orthogonal to Q, so the Rayleigh quotients q^T (I-UU^T) rho(A) q equal q^T rho(A) q).
+ * Lanczos step (Eq. (2.10)): y = rho(A) q_i; z = y - beta_i q_{i-1}; alpha_i = q_i^T z;
+ * z -= alpha_i q_i; full reorthogonalisation of z against [U, Q_i]; beta_{i+1} = ||z||.
+ * Special TR step: with TR vectors u_1..u_l (Ritz values theta_j, couplings s_j) and
+ * q_{l+1}: y = rho(A) q_{l+1}; alpha = q_{l+1}^T y; z = y - sum_j s_j u_j - alpha q_{l+1};
+ * reorthogonalise; the projected matrix is the arrowhead diag(theta) bordered by s, followed
+ * by the tridiagonal of the ordinary steps (thick restart of Wu and Simon).
+ * Early-restart test every Ncycle steps: t = sum of the Ritz values >= bar; restart when it
+ * changed by less than tau1 * max(1, |t|) since the previous test of the same cycle
+ * (READING: and at least one Ritz value is >= bar, so that a cycle is never cut short
+ * before anything has emerged above the threshold).
+ * At restart every Ritz pair with theta >= bar is a candidate: u = Q s normalised,
+ * lambda = u^T A u; pairs with lambda outside the slice are ignored; pairs with
+ * ||A u - lambda u|| <= tol * ||A|| are locked; the others form the next TR set.
+ *
+ * READINGS (the paper leaves these open):
+ *   - the candidate threshold is bar = rho(t_i) = rho(t_{i+1}) of the built filter (the
+ *     paper writes tau, but eigenvalues just inside the slice map to [bar, tau) when bar<tau);
+ *   - ||A|| = max(|lmin|, |lmax|);
+ *   - slice membership is [a, b) when right_closed == 0 and [a, b] otherwise;
+ *   - a restart that yields no candidate in the slice makes the next cycle start from a fresh
+ *     seeded random vector orthogonalised against U (stream 3, index = restart count); the
+ *     run stops after two consecutive restarts without candidates (the paper's "extra
+ *     restart"), or when Its exceeds maxit;
+ *   - a Lanczos breakdown (beta <= 1e-13 * ||y||) continues with a fresh seeded vector
+ *     orthogonalised against [U, Q] and a zero coupling.
+ * Y: n x cap column-major, lam/res: cap.  stats[0..3] = iterations, matvecs, restarts,
+ * reorth passes.  Returns 0, -4 if maxit was exceeded, -5 if more than cap converged
+ * (nev then holds the number found so far).                                               */
+typedef struct {
+    const orc_csr *A;
+    double c, d;
+    int deg;
+    const double *coef;
+    double *w0, *w1, *w2;
+    long nmv;
+} orc_filt;
+
+static void orc_apply_filter(orc_filt *F, const double *x, double *y)
+{
+    orc_filter_apply_csr(F->A, F->c, F->d, F->deg, F->coef, x, y, F->w0, F->w1, F->w2);
+    F->nmv += F->deg;
+}
+
+static void orc_fresh_vector(int64_t n, uint64_t seed, uint64_t index, double *q,
+                             const double *U, int nlock, const double *Q, int nq)
+{
+    for (int64_t i = 0; i < n; i++)
+        q[i] = 2.0 * orc_unit(orc_draw(seed, ORC_STREAM_LANCZOS, index * (uint64_t)n + (uint64_t)i)) - 1.0;
+    orc_reorth(n, q, U, nlock, Q, nq);
+    orc_reorth(n, q, U, nlock, Q, nq);
+    double nr = orc_nrm2(n, q);
+    for (int64_t i = 0; i < n; i++) q[i] /= nr;
+}
+
+int orc_cheblantr(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                  double a, double b, int right_closed, double lmin, double lmax,
+                  int deg, const double *coef, double bar,
+                  int m, int maxit, int ncycle, double tol, double tau1, uint64_t seed,
+                  int cap, int *nev, double *lam, double *Y, double *res, long *stats)
+{
+    orc_csr A = {n, rp, ci, v};
+    orc_filt F = {&A, 0.5 * (lmax + lmin), 0.5 * (lmax - lmin), deg, coef, NULL, NULL, NULL, 0};
+    F.w0 = malloc(sizeof(double) * n);
+    F.w1 = malloc(sizeof(double) * n);
+    F.w2 = malloc(sizeof(double) * n);
+    double normA = fmax(fabs(lmin), fabs(lmax));
+    if (m > n) m = (int)n;
+    double *U = calloc((size_t)n * (cap > 0 ? cap : 1), sizeof(double));
+    double *Q = calloc((size_t)n * (m + 1), sizeof(double));
+    double *T = calloc((size_t)(m + 1) * (m + 1), sizeof(double));
+    double *y = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+    double *u = malloc(sizeof(double) * n), *Au = malloc(sizeof(double) * n);
+    double *theta = malloc(sizeof(double) * (m + 1)), *S = malloc(sizeof(double) * (m + 1) * (m + 1));
+    double *Tk = malloc(sizeof(double) * (m + 1) * (m + 1));
+    double *trv = malloc(sizeof(double) * (size_t)n * (m + 1));
+    double *trtheta = malloc(sizeof(double) * (m + 1)), *trs = malloc(sizeof(double) * (m + 1));
+    int nlock = 0, l = 0, its = 0, nrestart = 0, nocand = 0, status = 0;
+    long npass = 0;
+    uint64_t fresh_index = 0;
+
+    orc_fresh_vector(n, seed, fresh_index++, Q, U, 0, NULL, 0);
+    while (its <= maxit) {
+        int k;                        /* number of basis vectors whose T-columns are complete */
+        memset(T, 0, sizeof(double) * (m + 1) * (m + 1));
+        if (l > 0) {
+            /* special TR step on q_{l+1} = Q[:, l]                                           */
+            for (int j = 0; j < l; j++) {
+                AT(T, j, j, m + 1) = trtheta[j];
+                AT(T, j, l, m + 1) = trs[j];
+                AT(T, l, j, m + 1) = trs[j];
+            }
+            double *ql = Q + (size_t)l * n;
+            orc_apply_filter(&F, ql, y);
+            its++;
+            double alpha = orc_dot(n, ql, y);
+            for (int64_t i = 0; i < n; i++) z[i] = y[i];
+            for (int j = 0; j < l; j++) {
+                const double *uj = Q + (size_t)j * n;
+                for (int64_t i = 0; i < n; i++) z[i] -= trs[j] * uj[i];
+            }
+            for (int64_t i = 0; i < n; i++) z[i] -= alpha * ql[i];
+            npass += orc_reorth(n, z, U, nlock, Q, l + 1);
+            AT(T, l, l, m + 1) = alpha;
+            double beta = orc_nrm2(n, z);
+            double *qn = Q + (size_t)(l + 1) * n;
+            if (beta <= 1e-13 * orc_nrm2(n, y)) {
+                orc_fresh_vector(n, seed, fresh_index++, qn, U, nlock, Q, l + 1);
+                beta = 0.0;
+            } else {
+                for (int64_t i = 0; i < n; i++) qn[i] = z[i] / beta;
+            }
+            AT(T, l, l + 1, m + 1) = beta;
+            AT(T, l + 1, l, m + 1) = beta;
+            k = l + 1;
+        } else {
+            k = 0;
+        }
+        int lstart = k;
+        double t_old = 0.0;
+        int have_old = 0;
+        for (int i = k; i < m; i++) {
+            its++;
+            double *qi = Q + (size_t)i * n;
+            orc_apply_filter(&F, qi, y);
+            for (int64_t r = 0; r < n; r++) z[r] = y[r];
+            if (i > 0) {
+                double bi = AT(T, i - 1, i, m + 1);
+                const double *qp = Q + (size_t)(i - 1) * n;
+                for (int64_t r = 0; r < n; r++) z[r] -= bi * qp[r];
+            }
+            double alpha = orc_dot(n, qi, z);
+            for (int64_t r = 0; r < n; r++) z[r] -= alpha * qi[r];
+            npass += orc_reorth(n, z, U, nlock, Q, i + 1);
+            AT(T, i, i, m + 1) = alpha;
+            double beta = orc_nrm2(n, z);
+            double *qn = Q + (size_t)(i + 1) * n;
+            if (beta <= 1e-13 * orc_nrm2(n, y)) {
+                orc_fresh_vector(n, seed, fresh_index++, qn, U, nlock, Q, i + 1);
+                beta = 0.0;
+            } else {
+                for (int64_t r = 0; r < n; r++) qn[r] = z[r] / beta;
+            }
+            AT(T, i, i + 1, m + 1) = beta;
+            AT(T, i + 1, i, m + 1) = beta;
+            k = i + 1;
+            if ((k - lstart) % ncycle == 0) {
+                for (int jj = 0; jj < k; jj++)
+                    for (int ii = 0; ii < k; ii++) AT(Tk, ii, jj, k) = AT(T, ii, jj, m + 1);
+                orc_syev(k, Tk, theta, NULL);
+                double t_new = 0.0;
+                int nabove = 0;
+                for (int jj = 0; jj < k; jj++)
+                    if (theta[jj] >= bar) { t_new += theta[jj]; nabove++; }
+                if (have_old && nabove > 0 && fabs(t_new - t_old) < tau1 * fmax(1.0, fabs(t_new)))
+                    break;
+                t_old = t_new;
+                have_old = 1;
+            }
+            if (its > maxit) break;
+        }
+        /* restart: Ritz pairs of T_k                                                         */
+        nrestart++;
+        for (int jj = 0; jj < k; jj++)
+            for (int ii = 0; ii < k; ii++) AT(Tk, ii, jj, k) = AT(T, ii, jj, m + 1);
+        orc_syev(k, Tk, theta, S);
+        double betak = AT(T, k - 1, k, m + 1);
+        int ncand = 0, ntr = 0;
+        for (int jj = k - 1; jj >= 0; jj--) {          /* candidates, largest theta first     */
+            if (theta[jj] < bar) break;
+            const double *s = S + (size_t)jj * k;
+            for (int64_t r = 0; r < n; r++) {
+                double acc = 0.0;
+                for (int p = 0; p < k; p++) acc += Q[(size_t)p * n + r] * s[p];
+                u[r] = acc;
+            }
+            double nu = orc_nrm2(n, u);
+            for (int64_t r = 0; r < n; r++) u[r] /= nu;
+            orc_matvec(&A, u, Au);
+            double lamj = orc_dot(n, u, Au);
+            int inside = (lamj >= a) && (right_closed ? (lamj <= b) : (lamj < b));
+            if (!inside) continue;
+            ncand++;
+            for (int64_t r = 0; r < n; r++) Au[r] -= lamj * u[r];
+            double rj = orc_nrm2(n, Au) / normA;
+            if (rj <= tol) {
+                if (nlock >= cap) { status = -5; goto done; }
+                memcpy(U + (size_t)nlock * n, u, sizeof(double) * n);
+                lam[nlock] = lamj;
+                res[nlock] = rj;
+                nlock++;
+            } else {
+                memcpy(trv + (size_t)ntr * n, u, sizeof(double) * n);
+                trtheta[ntr] = theta[jj];
+                trs[ntr] = betak * s[k - 1];
+                ntr++;
+            }
+        }
+        if (ncand == 0) nocand++; else nocand = 0;
+        if (nocand >= 2) break;
+        if (its > maxit) { status = -4; break; }
+        if (ncand == 0) {
+            l = 0;
+            orc_fresh_vector(n, seed, fresh_index++, Q, U, nlock, NULL, 0);
+        } else {
+            /* next cycle: TR vectors, then the residual direction q_{k+1}                      */
+            memcpy(Q + (size_t)ntr * n, Q + (size_t)k * n, sizeof(double) * n);
+            memcpy(Q, trv, sizeof(double) * (size_t)n * ntr);
+            l = ntr;
+            if (l == 0) {
+                /* continue from q_{k+1}, re-orthogonalised against the new locked vectors */
+                npass += orc_reorth(n, Q, U, nlock, NULL, 0);
+                double nr = orc_nrm2(n, Q);
+                for (int64_t r = 0; r < n; r++) Q[r] /= nr;
+            }
+        }
+    }
+done:
+    /* sort the locked pairs by eigenvalue, ascending (selection sort)                      */
+    for (int i = 0; i < nlock; i++) {
+        int best = i;
+        for (int j = i + 1; j < nlock; j++)
+            if (lam[j] < lam[best]) best = j;
+        if (best != i) {
+            double t = lam[i]; lam[i] = lam[best]; lam[best] = t;
+            t = res[i]; res[i] = res[best]; res[best] = t;
+            for (int64_t r = 0; r < n; r++) {
+                t = U[(size_t)i * n + r];
+                U[(size_t)i * n + r] = U[(size_t)best * n + r];
+                U[(size_t)best * n + r] = t;
+            }
+        }
+    }
+    if (Y) memcpy(Y, U, sizeof(double) * (size_t)n * nlock);
+    *nev = nlock;
+    if (stats) {
+        stats[0] = its;
+        stats[1] = F.nmv;
+        stats[2] = nrestart;
+        stats[3] = npass;
+    }
+    free(F.w0); free(F.w1); free(F.w2); free(U); free(Q); free(T); free(y); free(z);
+    free(u); free(Au); free(theta); free(S); free(Tk); free(trv); free(trtheta); free(trs);
+    return status;
+}

@@ -1,0 +1,360 @@
+"""Pins of the CPU oracle against facts fixed outside it: the paper's printed tables, closed
+forms, exact identities, published generator outputs and brute-force dense eigensolves.
+
+Each test names what it pins and where the expected value comes from.  numpy/scipy dense
+routines appear here only as independent checks (never inside the oracle).
+"""
+import numpy as np
+import pytest
+from numpy.polynomial import chebyshev as npcheb
+
+from closed_form import count_in, lap_eigs, nnz_formula
+from conftest import golden
+from paper_1802_05215_gb300 import inputs as I
+
+
+# ---------------------------------------------------------------- SplitMix64 (seeded inputs)
+def test_splitmix64_published_vectors(oracle_mod):
+    for seed, *outs in golden("splitmix64_vectors.txt"):
+        want = [int(x) for x in outs]
+        assert oracle_mod.splitmix64_sequence(int(seed), 3) == want
+        assert [int(x) for x in I.splitmix64_sequence(int(seed), 3)] == want
+
+
+def test_counter_draw_matches_sequential_definition(oracle_mod):
+    # draw(s, t, k) = the (k+1)-th output of SplitMix64 seeded with key(s, t), and
+    # key(s, t) = first output of SplitMix64 seeded with s ^ (t * 0xD1B54A32D192ED03).
+    for seed, stream in [(0, 1), (7, 2), (2**63 + 5, 3)]:
+        s0 = (seed ^ (stream * 0xD1B54A32D192ED03)) & (2**64 - 1)
+        key = oracle_mod.splitmix64_sequence(s0, 1)[0]
+        seq = oracle_mod.splitmix64_sequence(key, 6)
+        assert [oracle_mod.draw(seed, stream, k) for k in range(6)] == seq
+        # the numpy implementation of the input module agrees
+        assert [int(x) for x in I.draw(seed, stream, np.arange(6))] == seq
+
+
+# ---------------------------------------------------------------- generators vs Table 1
+def test_generator_structure_and_table1_nnz():
+    for dim, nx, n, nnz, *_ in golden("table1_laplacians.txt"):
+        dim, nx, n, nnz = int(dim), int(nx), int(n), int(nnz)
+        assert nx ** dim == n
+        assert nnz_formula(dim, nx) == nnz
+    for dim, nx in [(2, 1), (2, 5), (2, 17), (3, 2), (3, 6), (3, 9)]:
+        A = I.laplacian_2d(nx) if dim == 2 else I.laplacian_3d(nx)
+        assert A.nnz == nnz_formula(dim, nx)
+        D = A.to_dense()
+        assert np.array_equal(D, D.T)
+        for r in range(A.n):  # sorted columns
+            assert np.all(np.diff(A.col_idx[A.row_ptr[r]:A.row_ptr[r + 1]]) > 0)
+    A = I.laplacian_3d(49)
+    assert (A.n, A.nnz) == (117649, 809137)
+
+
+@pytest.mark.parametrize("dim,nx", [(2, 12), (3, 7)])
+def test_generator_spectrum_is_closed_form(dim, nx):
+    A = I.laplacian_2d(nx) if dim == 2 else I.laplacian_3d(nx)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    assert np.max(np.abs(ev - lap_eigs(dim, nx))) < 1e-12
+
+
+def test_closed_form_reproduces_table1_counts():
+    for dim, nx, n, nnz, a, b, xi, eta, nu in golden("table1_laplacians.txt"):
+        e = lap_eigs(int(dim), int(nx))
+        assert count_in(e, float(xi), float(eta)) == int(nu)
+
+
+def test_anderson_diagonal_is_seeded_uniform():
+    A = I.anderson_3d(6, 4.0, 0)
+    diag = A.to_dense().diagonal()
+    assert np.all(diag >= 4.0) and np.all(diag < 8.0)
+    assert np.array_equal(diag, 6.0 + I.anderson_diagonal(216, 4.0, 0))
+    assert not np.array_equal(diag, 6.0 + I.anderson_diagonal(216, 4.0, 1))
+
+
+# ---------------------------------------------------------------- dense symmetric eigensolver
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 40, 97])
+def test_syev_random(oracle_mod, n):
+    rng = np.random.default_rng(n)
+    M = rng.standard_normal((n, n))
+    M = M + M.T
+    w, Z = oracle_mod.syev(M)
+    scale = max(1.0, np.abs(M).max())
+    assert np.max(np.abs(w - np.linalg.eigvalsh(M))) < 1e-13 * n * scale
+    assert np.all(np.diff(w) >= 0)
+    assert np.max(np.abs(Z.T @ Z - np.eye(n))) < 1e-13 * n
+    assert np.max(np.abs(M @ Z - Z * w)) < 1e-13 * n * scale
+
+
+def test_syev_special_structures(oracle_mod):
+    # repeated eigenvalues: Q diag(1,1,1,2,2,5) Q^T
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((6, 6)))
+    lam = np.array([1, 1, 1, 2, 2, 5.0])
+    M = (Q * lam) @ Q.T
+    w, Z = oracle_mod.syev(M)
+    assert np.max(np.abs(w - lam)) < 1e-13
+    assert np.max(np.abs(M @ Z - Z * w)) < 1e-13
+    # already diagonal, and an arrowhead + tridiagonal matrix as thick restart produces
+    w, _ = oracle_mod.syev(np.diag([3.0, -1.0, 2.0]))
+    assert np.array_equal(w, [-1.0, 2.0, 3.0])
+    T = np.diag([0.9, 0.95, 0.99, 0.3, 0.1, -0.2])
+    T[:3, 3] = T[3, :3] = [1e-3, -2e-2, 5e-4]
+    T[3, 4] = T[4, 3] = 0.4
+    T[4, 5] = T[5, 4] = 0.1
+    w, Z = oracle_mod.syev(T)
+    assert np.max(np.abs(w - np.linalg.eigvalsh(T))) < 1e-14
+
+
+# ---------------------------------------------------------------- spectral bounds
+@pytest.mark.parametrize("dim,nx", [(2, 20), (3, 10), (2, 100)])
+def test_bounds_enclose_closed_form_extremes(oracle_mod, dim, nx):
+    A = I.laplacian_2d(nx) if dim == 2 else I.laplacian_3d(nx)
+    e = lap_eigs(dim, nx)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    # enclosure up to rounding (a fully converged run gives the extremes to ~1e-15)
+    assert lo <= e[0] + 1e-13 * e[-1] and hi >= e[-1] - 1e-13 * e[-1]
+    assert (e[0] - lo) < 1e-2 * e[-1] and (hi - e[-1]) < 1e-2 * e[-1]
+
+
+# ---------------------------------------------------------------- KPM moments and DOS
+def _diag_csr(d):
+    n = len(d)
+    return I.CSR(n, np.arange(n + 1), np.arange(n, dtype=np.int32), np.asarray(d, float))
+
+
+def test_kpm_exact_on_diagonal_matrix(oracle_mod):
+    # For A = diag(lambda_i) and Rademacher v (v_i^2 = 1): v^T T_k(Ahat) v = sum_i T_k(lambda_hat_i)
+    rng = np.random.default_rng(0)
+    d = np.sort(rng.uniform(-3, 5, 300))
+    lmin, lmax = -3.5, 5.25
+    mu = oracle_mod.kpm_moments(_diag_csr(d), 60, 3, 11, lmin, lmax)
+    lh = (d - 0.5 * (lmax + lmin)) / (0.5 * (lmax - lmin))
+    want = np.array([np.cos(k * np.arccos(lh)).sum() for k in range(61)])
+    assert mu[0] == len(d)
+    assert np.max(np.abs(mu - want)) < 1e-12 * len(d)
+
+
+def test_kpm_matches_dense_spectral_formula(oracle_mod):
+    # mu_k = mean_l v_l^T Z diag(T_k(lambda_hat)) Z^T v_l, with Z from a dense eigensolve
+    A = I.anderson_3d(5, 3.0, 2)
+    lmin, lmax = -1.0, 14.0
+    M, nv, seed = 30, 4, 5
+    mu = oracle_mod.kpm_moments(A, M, nv, seed, lmin, lmax)
+    w, Z = np.linalg.eigh(A.to_dense())
+    lh = (w - 6.5) / 7.5           # c = (lmax + lmin)/2, d = (lmax - lmin)/2
+    V = I.rademacher_block(A.n, nv, seed)
+    P = Z.T @ V
+    want = np.array([np.mean(np.sum(P * P * np.cos(k * np.arccos(lh))[:, None], axis=0))
+                     for k in range(M + 1)])
+    assert np.max(np.abs(mu - want)) < 1e-11 * A.n
+
+
+def test_kpm_statistics_against_closed_form_trace(oracle_mod):
+    # E[v^T T_k v] = tr T_k(Ahat) = sum_i cos(k arccos lambda_hat_i) (closed-form spectrum);
+    # the stochastic error is below 6 sqrt(2 ||T_k||_F^2 / nvec).
+    nx, M, nv = 30, 40, 20
+    A = I.laplacian_2d(nx)
+    e = lap_eigs(2, nx)
+    lmin, lmax = 0.0, 8.0
+    mu = oracle_mod.kpm_moments(A, M, nv, 0, lmin, lmax)
+    lh = (e - 4.0) / 4.0
+    for k in range(M + 1):
+        tk = np.cos(k * np.arccos(lh))
+        sig = np.sqrt(2.0 * np.sum(tk * tk) / nv)
+        assert abs(mu[k] - tk.sum()) <= 6 * sig + 1e-9
+
+
+def test_jackson_coefficients_identities(oracle_mod):
+    for M in [1, 5, 80, 300]:
+        g = oracle_mod.jackson(M)
+        a = np.pi / (M + 2)
+        assert abs(g[0] - 1.0) < 1e-15
+        assert abs(g[1] - np.cos(a)) < 1e-14          # first factor is cos(pi/(M+2))
+        assert np.all(np.diff(g) <= 1e-15)            # decreasing
+        # the damped delta kernel g_0/2 + sum g_k T_k(x) T_k(y) is non-negative
+        x = np.cos(np.linspace(0, np.pi, 301))
+        for y in [-0.9, 0.0, 0.37]:
+            ker = 0.5 * g[0] + sum(g[k] * np.cos(k * np.arccos(x)) * np.cos(k * np.arccos(y))
+                                   for k in range(1, M + 1))
+            assert ker.min() > -1e-12 * ker.max()
+
+
+def test_dos_count_endpoints_and_monotone(oracle_mod):
+    A = I.laplacian_2d(40)
+    lo, hi = oracle_mod.bounds(A, 60, 0)
+    mu = oracle_mod.kpm_moments(A, 80, 10, 1, lo, hi)
+    assert mu[0] == A.n
+    assert abs(oracle_mod.dos_count(mu, lo, hi, hi) - A.n) < 1e-9
+    # (t - c)/d at t = lmin is -1 only up to rounding; arccos is sqrt-sensitive there
+    assert abs(oracle_mod.dos_count(mu, lo, hi, lo)) < 1e-9 * A.n
+    ts = np.linspace(lo, hi, 200)
+    N = np.array([oracle_mod.dos_count(mu, lo, hi, t) for t in ts])
+    assert np.all(np.diff(N) >= -1e-8 * A.n)
+    # smoothed count tracks the exact count to within the kernel width
+    e = lap_eigs(2, 40)
+    exact = np.array([np.count_nonzero(e <= t) for t in ts])
+    assert np.max(np.abs(N - exact)) < 0.05 * A.n
+
+
+def test_slicer_balances_table4_case(oracle_mod):
+    # 49^3 Laplacian on [0, 1]: exact per-slice counts from the closed form must be balanced
+    # (Table 4's own spread is 307..345 around 328.5 for six slices)
+    A = I.laplacian_3d(49)
+    e = lap_eigs(3, 49)
+    assert count_in(e, 0.0, 1.0) == 1971
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    mu = oracle_mod.kpm_moments(A, 100, 10, 0, lo, hi)
+    for ns in [2, 6]:
+        sli, est = oracle_mod.slicer(mu, lo, hi, 0.0, 1.0, ns)
+        assert sli[0] == 0.0 and sli[-1] == 1.0 and np.all(np.diff(sli) > 0)
+        counts = [count_in(e, sli[i], sli[i + 1], right_closed=(i == ns - 1)) for i in range(ns)]
+        assert sum(counts) == 1971
+        assert max(counts) / min(counts) < 1.3
+        assert abs(sum(est) - 1971) < 0.1 * 1971
+
+
+# ---------------------------------------------------------------- filter construction
+def _rho(pol, t):
+    c = 0.5 * (pol["lmax"] + pol["lmin"])
+    d = 0.5 * (pol["lmax"] - pol["lmin"])
+    return npcheb.chebval((np.asarray(t) - c) / d, pol["coef"])
+
+
+def test_filter_degrees_table2(oracle_mod):
+    # sigma damping, tau = 0.8, [a, b] from Table 1.  10 of 12 printed degrees are met
+    # exactly; 81^3 [0.40, 0.45] (141) and 100^3 [1.00, 1.018] (588) come out one lower,
+    # which the unprinted digits of b = 11.9882 can account for.
+    off = []
+    for dim, nx, xi, eta, deg in golden("table2_degrees.txt"):
+        b = 7.9998 if dim == "2" else 11.9882
+        pol = oracle_mod.filter_build(float(xi), float(eta), 0.0, b, damping=oracle_mod.DAMP_SIGMA)
+        if pol["deg"] != int(deg):
+            off.append((nx, xi, int(deg), pol["deg"]))
+    assert off == [("81", "0.40", 141, 140), ("100", "1.00", 588, 587)]
+
+
+def test_filter_degrees_table4(oracle_mod):
+    # all 21 printed degrees, interior slices and the left boundary slices
+    for ns, i, left, right, nu, deg in golden("table4_slices.txt"):
+        pol = oracle_mod.filter_build(float(left), float(right), 0.0, 11.9882,
+                                      damping=oracle_mod.DAMP_SIGMA)
+        assert pol["deg"] == int(deg), (ns, i)
+        assert pol["boundary"] == (-1 if i == "0" else 0)
+
+
+@pytest.mark.parametrize("damping", [0, 1, 2])
+def test_filter_shape_properties(oracle_mod, damping):
+    lmin, lmax = 0.0, 8.0
+    a, b = 0.40, 0.48
+    pol = oracle_mod.filter_build(a, b, lmin, lmax, damping=damping)
+    k = pol["deg"]
+    assert abs(_rho(pol, 4.0 + 4.0 * pol["gamma"]) - 1.0) < 1e-12        # rho(gamma) = 1
+    ra, rb = _rho(pol, a), _rho(pol, b)
+    assert abs(ra - rb) < 1e-10 and abs(ra - pol["bar"]) < 1e-10 and pol["bar"] <= 0.8
+    assert a < 4.0 + 4.0 * pol["gamma"] < b
+    if damping == 1:
+        assert k == 97
+    # minimality: the balanced filter of degree k-1 does not reach tau
+    from oracle import _load  # noqa: F401  (library already loaded)
+    prev = oracle_mod.filter_build(a, b, lmin, lmax, damping=damping, maxdeg=k - 1)
+    assert prev["reached_max"] and prev["bar"] > 0.8
+
+
+def test_filter_apply_matches_spectral_evaluation(oracle_mod):
+    A = I.laplacian_3d(6)
+    lmin, lmax = 0.0, 12.0
+    pol = oracle_mod.filter_build(2.0, 2.5, lmin, lmax)
+    X = np.random.default_rng(0).standard_normal((A.n, 3))
+    Y = oracle_mod.filter_apply(A, lmin, lmax, pol["coef"], X)
+    w, Z = np.linalg.eigh(A.to_dense())
+    want = Z @ (_rho(pol, w)[:, None] * (Z.T @ X))
+    assert np.max(np.abs(Y - want)) < 1e-12 * np.abs(X).max() * len(pol["coef"])
+
+
+# ---------------------------------------------------------------- filtered TR Lanczos
+def _check_eigs(A, r, ex, tol_res=1e-8):
+    assert r["nev"] == len(ex)
+    lam = r["lam"]
+    assert np.all(np.abs(lam - ex) <= 1e-9 * np.maximum(1.0, np.abs(ex)))
+    Y = r["Y"]
+    normA = np.abs(np.linalg.eigvalsh(A.to_dense())).max() if A.n <= 2000 else None
+    R = np.column_stack([A.to_dense() @ Y[:, j] for j in range(Y.shape[1])]) if A.n <= 2000 \
+        else None
+    if R is not None:
+        res = np.linalg.norm(R - Y * lam, axis=0) / normA
+        assert res.max() <= tol_res
+    assert np.max(np.abs(Y.T @ Y - np.eye(len(lam)))) <= 1e-10
+
+
+@pytest.mark.parametrize("case", [
+    ("2d", 20, 1.0, 1.6), ("3d", 12, 0.8, 1.6), ("3d", 10, 2.0, 2.6), ("3d", 12, 0.0, 0.9),
+])
+def test_cheblantr_against_closed_form(oracle_mod, case):
+    kind, nx, a, b = case
+    A = I.laplacian_2d(nx) if kind == "2d" else I.laplacian_3d(nx)
+    e = lap_eigs(2 if kind == "2d" else 3, nx)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    ex = e[(e >= a) & (e <= b)]
+    r = oracle_mod.cheblantr(A, a, b, pol, m=max(2 * len(ex) + 40, 100))
+    assert r["status"] == 0
+    _check_eigs(A, r, ex)
+
+
+def test_cheblantr_multiplicity_eigenspaces(oracle_mod):
+    # 3-D Laplacian has eigenvalues of multiplicity 3 and 6: compare eigenspaces, not vectors
+    A = I.laplacian_3d(10)
+    w, Z = np.linalg.eigh(A.to_dense())
+    a, b = 2.0, 2.6
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    r = oracle_mod.cheblantr(A, a, b, pol, m=120)
+    sel = (w >= a) & (w <= b)
+    P_ref = Z[:, sel] @ Z[:, sel].T
+    P = r["Y"] @ r["Y"].T
+    assert np.linalg.norm(P - P_ref, 2) < 1e-7
+
+
+@pytest.mark.parametrize("a,b", [(-1.0, 1.0), (3.0, 5.0), (6.0, 6.5)])
+def test_cheblantr_anderson_bruteforce(oracle_mod, a, b):
+    A = I.anderson_3d(7, 4.0, 0)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    assert lo <= ev[0] + 1e-13 * ev[-1] and hi >= ev[-1] - 1e-13 * ev[-1]
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    ex = ev[(ev >= a) & (ev <= b)]
+    r = oracle_mod.cheblantr(A, a, b, pol, m=max(2 * len(ex) + 40, 100))
+    assert r["status"] == 0
+    _check_eigs(A, r, ex)
+
+
+def test_cheblantr_half_open_slices_partition(oracle_mod):
+    # adjacent half-open slices [a, cut) and [cut, b] neither lose nor duplicate eigenvalues
+    # (cut midway between two distinct eigenvalues, so rounding cannot decide membership)
+    A = I.laplacian_2d(16)
+    e = lap_eigs(2, 16)
+    cut = 0.5 * (e[100] + e[102]) if e[102] - e[100] > 1e-6 else 0.5 * (e[100] + e[101])
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    found = []
+    for (a, b, rc) in [(cut - 0.3, cut, False), (cut, cut + 0.3, True)]:
+        pol = oracle_mod.filter_build(a, b, lo, hi)
+        r = oracle_mod.cheblantr(A, a, b, pol, m=120, right_closed=rc)
+        found.append(r["lam"])
+    allf = np.sort(np.concatenate(found))
+    ex = e[(e >= cut - 0.3) & (e <= cut + 0.3)]
+    assert len(allf) == len(ex) and np.max(np.abs(allf - ex)) < 1e-12
+
+
+def test_cheblantr_config_2d_100(oracle_mod):
+    # the 100 x 100 2-D Laplacian on [0.40, 0.48]: exactly 69 eigenvalues (multiplicity 2)
+    A = I.laplacian_2d(100)
+    e = lap_eigs(2, 100)
+    ex = e[(e >= 0.40) & (e <= 0.48)]
+    assert len(ex) == 69
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(0.40, 0.48, lo, hi)
+    r = oracle_mod.cheblantr(A, 0.40, 0.48, pol, m=2 * 69 + 40)
+    assert r["status"] == 0 and r["nev"] == 69
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * ex)
+    assert r["res"].max() <= 1e-8
+    assert np.max(np.abs(r["Y"].T @ r["Y"] - np.eye(69))) <= 1e-10
