@@ -1,0 +1,194 @@
+/*
+ * evsl_gb300.h -- C ABI of the GB300 (sm_103a) implementation of polynomial-filtered spectrum
+ * slicing for large sparse symmetric eigenproblems (Li, Xi, Erlandson, Saad, "The Eigenvalues
+ * Slicing Library (EVSL)", arXiv:1802.05215).
+ *
+ * Problem (Sec. 1, Eq. (1.2); Sec. 2.1): find all eigenpairs (lambda, x) of a real symmetric
+ * sparse A with lambda in [xi, eta].  Workflow of the paper's Example 1 (Sec. 3.1):
+ *   evsl_create -> evsl_set_csr -> evsl_bounds -> evsl_kpm_dos -> evsl_slice_by_dos ->
+ *   for each slice: evsl_cheb_filter_build -> evsl_chebLanTr -> evsl_destroy.
+ *
+ * Conventions for every call:
+ *   - Return value is an evsl_status (0 = EVSL_OK, negative = error).  On error the context's
+ *     message is available from evsl_last_error(); output arguments are left unspecified
+ *     unless the call says otherwise.
+ *   - Host pointers are read or written only during the call and never retained.
+ *   - Device memory is owned by the context and freed by evsl_destroy.
+ *   - A context is bound to one CUDA device and one CUDA stream; use it from one host thread
+ *     at a time.  Calls are synchronous with respect to the host unless stated otherwise.
+ *   - Dense vectors and blocks are column-major (vector j of an n x k block starts at j*n).
+ *   - Nothing in this library falls back to the CPU: without a usable GPU the calls that need
+ *     one return EVSL_ERR_CUDA.
+ */
+#ifndef EVSL_GB300_H
+#define EVSL_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct evsl_ctx evsl_ctx;
+
+typedef enum {
+    EVSL_OK = 0,
+    EVSL_ERR_ARG = -1,      /* invalid argument (sizes, pointers, intervals)            */
+    EVSL_ERR_NOMEM = -2,    /* device allocation failed or the HBM budget is exceeded   */
+    EVSL_ERR_CUDA = -3,     /* a CUDA runtime call or kernel launch failed              */
+    EVSL_ERR_NOCONV = -4,   /* iteration limit reached; partial results are returned    */
+    EVSL_ERR_CAPACITY = -5, /* caller buffer too small; the needed size is reported     */
+    EVSL_ERR_TIMEOUT = -6,  /* a bounded device-side wait gave up                       */
+    EVSL_ERR_STATE = -7     /* call out of order (e.g. no matrix set)                   */
+} evsl_status;
+
+typedef enum { EVSL_DAMP_NONE = 0, EVSL_DAMP_JACKSON = 1, EVSL_DAMP_SIGMA = 2 } evsl_damping;
+typedef enum { EVSL_FP64 = 0, EVSL_FP32 = 1 } evsl_precision;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Context.  Replaces the paper's global state (EVSLStart/EVSLFinish, Sec. 3.1).
+ * device: CUDA ordinal.  hbm_budget_bytes: cap on the device memory the context may hold
+ * (0 = no cap); allocations beyond it fail with EVSL_ERR_NOMEM.  *ctx is set to NULL on error. */
+int evsl_create(evsl_ctx **ctx, int device, size_t hbm_budget_bytes);
+void evsl_destroy(evsl_ctx *ctx);
+/* Message of the last failed call on ctx (empty string if none); valid until the next call. */
+const char *evsl_last_error(const evsl_ctx *ctx);
+/* Run the context's work on an existing stream (a cudaStream_t passed as void*); NULL restores
+ * the context's own stream.  The caller keeps ownership of the stream. */
+int evsl_set_stream(evsl_ctx *ctx, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Matrix (Sec. 3.1: CSR storage; SetAMatrix).  A is symmetric with both triangles stored,
+ * 0-based, column indices sorted within each row.  row_ptr[n+1] (row_ptr[0] = 0,
+ * non-decreasing), col_idx[nnz], val[nnz] are HOST arrays, copied in; the caller keeps them.
+ * The device copy is a sliced ELLPACK layout (32-row slices) in FP64 with an FP32 mirror.
+ * Replaces any previous matrix.  Symmetry is assumed, not checked.  Errors: EVSL_ERR_ARG for
+ * n < 1, nnz >= 2^31, a bad row_ptr or an out-of-range column index. */
+int evsl_set_csr(evsl_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                 const double *val);
+
+/* Spectral bounds (Sec. 2.2.1, text after Eq. (2.3); LanTrbounds, Sec. 3.1): `steps` Lanczos
+ * steps (full reorthogonalisation) from the seeded start vector; returns the extreme Ritz values
+ * widened by their residual bounds, lmin = theta_1 - |beta s_{m,1}|, lmax = theta_m +
+ * |beta s_{m,m}|.  lmin/lmax are host pointers. */
+int evsl_bounds(evsl_ctx *ctx, int steps, uint64_t seed, double *lmin, double *lmax);
+
+/* KPM spectral density (Sec. 2.1; kpmdos): with Ahat = (A - cI)/d, c and d the centre and
+ * half-width of [lmin, lmax] (Eq. (2.3)), and nvec Rademacher probes v_l drawn by SplitMix64
+ * from `seed` (sign of draw(seed, 2, l*n + i)),
+ *     mu[k] = (1/nvec) * sum_l v_l^T T_k(Ahat) v_l ,   k = 0..degree   (so mu[0] == n).
+ * mu[degree+1] is a HOST array.  prec selects FP64 or FP32 vectors and matrix values in the
+ * recurrence (per-row dot products are accumulated in FP64 either way). */
+int evsl_kpm_dos(evsl_ctx *ctx, int degree, int nvec, uint64_t seed, double lmin, double lmax,
+                 evsl_precision prec, double *mu);
+
+/* DOS slicer (Sec. 2.1, Eq. (2.2); spslicer).  Pure host function, no context.  From the
+ * Jackson-damped KPM density it places npts evenly spaced points on [xi, eta], and puts the
+ * slice ends t_1..t_{ns-1} where the cumulative count crosses i/ns of the total (first crossing,
+ * refined by linear interpolation); sli[0] = xi, sli[nslices] = eta.  est[i] is the estimated
+ * eigenvalue count of slice i.  sli[nslices+1] and est[nslices] are caller-owned host arrays.
+ * n is the matrix order (mu[0] should equal it).  npts <= 0 selects max(2001, 100*nslices). */
+int evsl_slice_by_dos(const double *mu, int degree, int64_t n, double lmin, double lmax,
+                      double xi, double eta, int nslices, int npts, double *sli, double *est);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Chebyshev delta filter (Sec. 2.2.1, Eqs. (2.4)-(2.7); find_pol).
+ * rho(t) = sum_{j<=deg} coef[j] T_j((t - c)/d).  Interior slices: for deg = 2, 3, ... the
+ * centre gamma is balanced by Newton's method so that rho(a) = rho(b) (Eq. (2.7)), and the
+ * first degree with end value bar <= tau (default 0.8) is kept.  Slices whose mapped left end
+ * is <= -1 (right end >= 1) are boundary slices: gamma = -1 (+1), same damping, and the degree
+ * grows until rho(inner end) <= tau_ext (default 0.4).  `bar` is the end value, i.e. the
+ * threshold that separates wanted from unwanted Ritz values of rho(A). */
+typedef struct {
+    double tau;             /* end-value threshold for interior slices (0.8)            */
+    double tau_ext;         /* end-value threshold for boundary slices (0.4)            */
+    evsl_damping damping;   /* EVSL_DAMP_JACKSON (default), EVSL_DAMP_SIGMA, NONE       */
+    int max_deg;            /* largest degree tried (10000)                             */
+} evsl_filter_opts;
+
+typedef struct {
+    int deg;                /* polynomial degree                                        */
+    int boundary;           /* -1 left boundary slice, +1 right, 0 interior             */
+    double gamma;           /* centre in the mapped variable                            */
+    double bar;             /* rho at the slice ends (interior) / inner end (boundary)  */
+    double lmin, lmax;      /* spectral interval used for the mapping                   */
+    double a, b;            /* the slice                                                */
+    const double *coef;     /* deg+1 Chebyshev coefficients (caller-owned host memory)  */
+} evsl_polfilt;
+
+/* Pure host function.  opts may be NULL (defaults).  coef[cap] is a caller-owned host array;
+ * on success pol->coef == coef.  Errors: EVSL_ERR_ARG (b <= a, lmax <= lmin, or [a, b]
+ * covering the whole spectral interval or lying outside it); EVSL_ERR_CAPACITY if cap < deg+1 (pol->deg then
+ * holds the degree needed); EVSL_ERR_NOCONV if max_deg was reached (the max_deg filter is
+ * returned). */
+int evsl_cheb_filter_build(double a, double b, double lmin, double lmax,
+                           const evsl_filter_opts *opts, evsl_polfilt *pol, double *coef, int cap);
+
+/* Filter application (Eq. (2.4) with the three-term Chebyshev recurrence): Y = rho(Ahat) X for
+ * nvec columns.  X and Y are DEVICE pointers to n x nvec column-major FP64 blocks (Y must not
+ * overlap X).  prec = EVSL_FP32 runs the recurrence in FP32 (X/Y stay FP64). */
+int evsl_filter_apply(evsl_ctx *ctx, const evsl_polfilt *pol, int nvec, const double *X,
+                      double *Y, evsl_precision prec);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Filtered thick-restart Lanczos with locking (Sec. 2.5, Algorithm 2; ChebLanTr) on the slice
+ * [a, b] with filter pol (built for the same slice).  Candidates are the Ritz values of
+ * rho(A) at or above pol->bar; their Rayleigh quotients u^T A u outside the slice are ignored;
+ * pairs with ||A u - lambda u|| <= tol * max(|lmin|, |lmax|) are locked and deflated.
+ * The run stops after two consecutive restarts without candidates (a restart without
+ * candidates makes the next cycle start from a fresh seeded vector orthogonal to the locked
+ * ones), or with EVSL_ERR_NOCONV when maxit filtered matvec steps were spent.
+ * Outputs: *nev pairs, eigenvalues ascending in lam[cap] and res[cap] (relative residuals) on
+ * the HOST, eigenvectors in Y (n x cap column-major), which may be host or device memory
+ * (detected).  If more than cap pairs converge: EVSL_ERR_CAPACITY, *nev = cap, outputs hold
+ * the first cap found. */
+typedef struct {
+    int m;                  /* Krylov dimension before a restart                        */
+    int maxit;              /* limit on Lanczos steps (0 = 20*m)                        */
+    int ncycle;             /* early-restart test period (10)                           */
+    double tol;             /* residual tolerance relative to ||A|| (1e-8)              */
+    double tau1;            /* early-restart tolerance on the Ritz-value sum (1e-10)     */
+    uint64_t seed;          /* start vectors: SplitMix64 stream 3                       */
+    evsl_precision prec;    /* filter precision: EVSL_FP64 or EVSL_FP32                 */
+    int right_closed;       /* 1: lambda in [a, b]; 0: lambda in [a, b)                 */
+} evsl_lan_opts;
+
+typedef struct {
+    int64_t niter;          /* Lanczos steps                                            */
+    int64_t nmv;            /* sparse matrix-vector products inside the filter          */
+    int64_t nrestart;       /* restarts                                                 */
+    int64_t npass;          /* Gram-Schmidt passes                                      */
+    double t_filter;        /* seconds in filter application                            */
+    double t_orth;          /* seconds in reorthogonalisation                           */
+    double t_restart;       /* seconds in restarts (small eigensolves, Ritz vectors)     */
+    double t_total;         /* seconds in the call                                      */
+} evsl_stats;
+
+int evsl_chebLanTr(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol,
+                   const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
+                   double *res, evsl_stats *stats);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Instrumentation (no counterpart in the paper).
+ * evsl_launch_count: kernels launched by this context since its creation.
+ * evsl_profile: 1 starts timing the launch groups of each kernel family with CUDA events on
+ * the context's stream, 0 stops; evsl_profile_get returns, for family `kernel` (EVSL_K_*),
+ * the launches timed and their summed device time in milliseconds since profiling started. */
+typedef enum {
+    EVSL_K_CHEB_STEP = 0,   /* fused Chebyshev filter step (SpMM + recurrence + axpy)   */
+    EVSL_K_KPM_STEP = 1,    /* KPM moment step (SpMM + recurrence + probe dots)         */
+    EVSL_K_REORTH = 2,      /* Gram-Schmidt projections against the basis               */
+    EVSL_K_RITZ_GEMM = 3,   /* Ritz vectors Y = Q S                                     */
+    EVSL_K_SMALL_EIG = 4,   /* Jacobi / bisection on the projected matrix               */
+    EVSL_K_COUNT = 5
+} evsl_kernel_family;
+
+int64_t evsl_launch_count(const evsl_ctx *ctx);
+int evsl_profile(evsl_ctx *ctx, int enable);
+int evsl_profile_get(evsl_ctx *ctx, int kernel, int64_t *launches, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EVSL_GB300_H */

@@ -481,7 +481,8 @@ static double orc_balance(int k, const double *g, double ta, double tb)
  * of the spectrum) with the same damping, and k grows until rho(tb) <= tau_ext (default
  * 0.4); bar = rho(tb).  Mirrored (gamma = 1, rho(ta) <= tau_ext) when tb >= 1.  With Lanczos
  * sigma damping this reproduces the boundary-slice degrees 5, 6, 7, 8, 8, 9 of Table 4.
- * An interval covering the whole spectrum (ta <= -1 and tb >= 1) is rejected.
+ * An interval covering the whole spectrum (ta <= -1 and tb >= 1), or lying outside it
+ * (tb <= -1 or ta >= 1), is rejected.
  * Output coef[j] = g_j mu_j / P(gamma), j = 0..deg.  Returns 0, -1 on bad input, -2 if
  * maxdeg was reached, -5 if cap < deg+1 (deg then holds the needed degree).              */
 int orc_filter_build(double a, double b, double lmin, double lmax, double tau, double tau_ext,
@@ -493,6 +494,7 @@ int orc_filter_build(double a, double b, double lmin, double lmax, double tau, d
     double ta = (a - c) / d, tb = (b - c) / d;
     int left = (ta <= -1.0), right = (tb >= 1.0);
     if (left && right) return -1;
+    if (tb <= -1.0 || ta >= 1.0) return -1;   /* slice outside the spectral interval */
     double *g = malloc(sizeof(double) * (maxdeg + 1));
     *boundary = left ? -1 : (right ? 1 : 0);
     int status = -2, k;
@@ -586,7 +588,9 @@ void orc_filter_apply(int64_t n, const int64_t *rp, const int32_t *ci, const dou
  *     run stops after two consecutive restarts without candidates (the paper's "extra
  *     restart"), or when Its exceeds maxit;
  *   - a Lanczos breakdown (beta <= 1e-13 * ||y||) continues with a fresh seeded vector
- *     orthogonalised against [U, Q] and a zero coupling.
+ *     orthogonalised against [U, Q] and a zero coupling;
+ *   - the TR set keeps at most m/2 vectors (those with the largest Ritz values), so that every
+ *     cycle adds at least m/2 - 1 Lanczos steps and the basis never exceeds m+1 vectors.
  * Y: n x cap column-major, lam/res: cap.  stats[0..3] = iterations, matvecs, restarts,
  * reorth passes.  Returns 0, -4 if maxit was exceeded, -5 if more than cap converged
  * (nev then holds the number found so far).                                               */
@@ -752,7 +756,7 @@ int orc_cheblantr(int64_t n, const int64_t *rp, const int32_t *ci, const double 
                 lam[nlock] = lamj;
                 res[nlock] = rj;
                 nlock++;
-            } else {
+            } else if (ntr < m / 2) {
                 memcpy(trv + (size_t)ntr * n, u, sizeof(double) * n);
                 trtheta[ntr] = theta[jj];
                 trs[ntr] = betak * s[k - 1];

@@ -1,0 +1,284 @@
+// C ABI entry points (include/evsl_gb300.h) and context services: error reporting, the
+// HBM budget, grow-only workspaces and event-based kernel timing.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "evsl_internal.h"
+
+int ctx_fail(evsl_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int ctx_cuda(evsl_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return ctx_fail(c, EVSL_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return ctx_fail(c, EVSL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int check_launch(evsl_ctx *c, const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, what);
+}
+
+int ctx_alloc(evsl_ctx *c, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) return EVSL_OK;
+    if (c->budget && c->used + bytes > c->budget)
+        return ctx_fail(c, EVSL_ERR_NOMEM, "HBM budget exceeded (%zu + %zu > %zu bytes)", c->used,
+                        bytes, c->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return ctx_fail(c, EVSL_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    c->used += bytes;
+    return EVSL_OK;
+}
+
+void ctx_free(evsl_ctx *c, void *p, size_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    c->used -= std::min(c->used, bytes);
+}
+
+// Grow-only workspace: the returned buffer holds at least `bytes`; growing discards contents.
+void *ctx_ws(evsl_ctx *c, int slot, size_t bytes, int *status)
+{
+    if (c->ws_ptr.size() < WS_COUNT) {
+        c->ws_ptr.resize(WS_COUNT, nullptr);
+        c->ws_bytes.resize(WS_COUNT, 0);
+    }
+    if (c->ws_bytes[slot] >= bytes && c->ws_ptr[slot]) return c->ws_ptr[slot];
+    if (c->ws_ptr[slot]) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            *status = ctx_cuda(c, e, "workspace sync");
+            return nullptr;
+        }
+        ctx_free(c, c->ws_ptr[slot], c->ws_bytes[slot]);
+        c->ws_ptr[slot] = nullptr;
+        c->ws_bytes[slot] = 0;
+    }
+    size_t want = bytes < 256 ? 256 : bytes;
+    void *p = nullptr;
+    int st = ctx_alloc(c, &p, want);
+    if (st != EVSL_OK) {
+        *status = st;
+        return nullptr;
+    }
+    c->ws_ptr[slot] = p;
+    c->ws_bytes[slot] = want;
+    return p;
+}
+
+static cudaEvent_t take_event(evsl_ctx *c)
+{
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static void prof_resolve(evsl_ctx *c)
+{
+    for (ProfGroup &g : c->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(g.b) == cudaSuccess && cudaEventElapsedTime(&ms, g.a, g.b) == cudaSuccess) {
+            c->prof_ms[g.family] += ms;
+            c->prof_launches[g.family] += g.launches;
+        }
+        c->ev_pool.push_back(g.a);
+        c->ev_pool.push_back(g.b);
+    }
+    c->prof_pending.clear();
+}
+
+void prof_begin(evsl_ctx *c, int family, ProfGroup *g)
+{
+    g->family = family;
+    g->launches = 0;
+    g->a = g->b = nullptr;
+    if (!c->prof) return;
+    g->a = take_event(c);
+    g->b = take_event(c);
+    cudaEventRecord(g->a, c->stream);
+}
+
+void prof_end(evsl_ctx *c, ProfGroup *g, int launches)
+{
+    if (!c->prof || !g->a) return;
+    cudaEventRecord(g->b, c->stream);
+    g->launches = launches;
+    c->prof_pending.push_back(*g);
+    if (c->prof_pending.size() > 4096) prof_resolve(c);
+}
+
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+int evsl_create(evsl_ctx **out, int device, size_t hbm_budget_bytes)
+{
+    if (!out) return EVSL_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return EVSL_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return EVSL_ERR_CUDA;
+    evsl_ctx *c = new evsl_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return EVSL_ERR_CUDA;
+    }
+    c->stream = c->own_stream;
+    cudaDeviceGetAttribute(&c->dev_sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (c->dev_sm_count <= 0) c->dev_sm_count = 1;
+    *out = c;
+    return EVSL_OK;
+}
+
+void evsl_destroy(evsl_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    prof_resolve(c);
+    sell_free(c);
+    for (size_t i = 0; i < c->ws_ptr.size(); i++) ctx_free(c, c->ws_ptr[i], c->ws_bytes[i]);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+const char *evsl_last_error(const evsl_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int evsl_set_stream(evsl_ctx *c, void *stream)
+{
+    if (!c) return EVSL_ERR_ARG;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "set_stream");
+    c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+    return EVSL_OK;
+}
+
+int evsl_set_csr(evsl_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                 const double *val)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    cudaSetDevice(c->device);
+    return sell_upload(c, n, row_ptr, col_idx, val);
+}
+
+int evsl_bounds(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax)
+{
+    if (!c || !lmin || !lmax || steps < 2) return c ? ctx_fail(c, EVSL_ERR_ARG, "bounds: bad arguments") : EVSL_ERR_ARG;
+    c->err.clear();
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "bounds: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_bounds(c, steps, seed, lmin, lmax);
+}
+
+int evsl_kpm_dos(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax,
+                 evsl_precision prec, double *mu)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!mu || degree < 0 || nvec < 1 || !(lmax > lmin) || (prec != EVSL_FP64 && prec != EVSL_FP32))
+        return ctx_fail(c, EVSL_ERR_ARG, "kpm_dos: bad arguments");
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "kpm_dos: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_kpm(c, degree, nvec, seed, lmin, lmax, prec, mu);
+}
+
+int evsl_slice_by_dos(const double *mu, int degree, int64_t n, double lmin, double lmax,
+                      double xi, double eta, int nslices, int npts, double *sli, double *est)
+{
+    return host_slicer(mu, degree, n, lmin, lmax, xi, eta, nslices, npts, sli, est);
+}
+
+int evsl_cheb_filter_build(double a, double b, double lmin, double lmax,
+                           const evsl_filter_opts *opts, evsl_polfilt *pol, double *coef, int cap)
+{
+    return host_filter_build(a, b, lmin, lmax, opts, pol, coef, cap);
+}
+
+int evsl_filter_apply(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const double *X, double *Y,
+                      evsl_precision prec)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!pol || !pol->coef || pol->deg < 0 || nvec < 1 || !X || !Y)
+        return ctx_fail(c, EVSL_ERR_ARG, "filter_apply: bad arguments");
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "filter_apply: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_filter_apply(c, pol, nvec, X, Y, prec);
+}
+
+int evsl_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
+                   const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
+                   double *res, evsl_stats *stats)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!pol || !pol->coef || !opts || !nev || !lam || !res || cap < 1 || !(b > a) || opts->m < 2)
+        return ctx_fail(c, EVSL_ERR_ARG, "chebLanTr: bad arguments");
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "chebLanTr: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_chebLanTr(c, a, b, pol, opts, cap, nev, lam, Y, res, stats);
+}
+
+int64_t evsl_launch_count(const evsl_ctx *c) { return c ? c->launches : 0; }
+
+int evsl_profile(evsl_ctx *c, int enable)
+{
+    if (!c) return EVSL_ERR_ARG;
+    cudaSetDevice(c->device);
+    if (enable) {
+        prof_resolve(c);
+        for (int i = 0; i < EVSL_K_COUNT; i++) {
+            c->prof_ms[i] = 0.0;
+            c->prof_launches[i] = 0;
+        }
+        c->prof = true;
+    } else {
+        prof_resolve(c);
+        c->prof = false;
+    }
+    return EVSL_OK;
+}
+
+int evsl_profile_get(evsl_ctx *c, int kernel, int64_t *launches, double *ms)
+{
+    if (!c || kernel < 0 || kernel >= EVSL_K_COUNT || !launches || !ms) return EVSL_ERR_ARG;
+    cudaSetDevice(c->device);
+    prof_resolve(c);
+    *launches = c->prof_launches[kernel];
+    *ms = c->prof_ms[kernel];
+    return EVSL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,442 @@
+// Sparse kernels for sm_103a: sliced-ELLPACK upload, the fused Chebyshev filter step
+// (SpMM + three-term recurrence + coefficient axpy, Eq. (2.4) with the mapping of Eq. (2.3)),
+// the plain SpMV/SpMM, and the KPM moment step (Sec. 2.1) with in-kernel probe dots.
+//
+// Layout: one warp per 32-row slice, lane = row.  For a slice, value/column loads are
+// contiguous across the warp (256 B of FP64 values, 128 B of indices per nonzero position),
+// and the gathers x[col] of 32 consecutive rows of a stencil matrix are near-contiguous, so
+// each pass over the matrix is one coalesced HBM stream with the vector reused from L2.
+// For a block of nvec columns (column-major, ld = n) the row's nonzeros stay in registers
+// and the columns are streamed, so the matrix is read once per step for all columns.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "evsl_internal.h"
+
+namespace {
+
+constexpr uint64_t SM_GOLDEN = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t SM_STREAM_MUL = 0xD1B54A32D192ED03ull;
+
+__host__ __device__ __forceinline__ uint64_t sm_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// key of a stream: first output of SplitMix64 seeded with seed ^ (stream * C)
+__host__ __device__ __forceinline__ uint64_t sm_key(uint64_t seed, uint64_t stream)
+{
+    return sm_mix((seed ^ (stream * SM_STREAM_MUL)) + SM_GOLDEN);
+}
+
+// (k+1)-th output of SplitMix64 seeded with key
+__device__ __forceinline__ uint64_t sm_draw(uint64_t key, uint64_t k)
+{
+    return sm_mix(key + (k + 1) * SM_GOLDEN);
+}
+
+constexpr int TPB = 256;  // threads per block for the warp-per-slice kernels
+constexpr int WREG = 8;   // slice widths up to WREG keep their nonzeros in registers
+
+template <typename V>
+__global__ void k_sell_fill(int64_t n, int64_t nslices, const int64_t *__restrict__ rp,
+                            const int32_t *__restrict__ ci, const double *__restrict__ cv,
+                            const int64_t *__restrict__ sptr, int32_t *__restrict__ col,
+                            double *__restrict__ val, float *__restrict__ val32)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t s = r >> 5;
+    if (s >= nslices) return;
+    int lane = (int)(r & 31);
+    int64_t base = sptr[s];
+    int w = (int)((sptr[s + 1] - base) >> 5);
+    int64_t b = 0, e = 0;
+    if (r < n) { b = rp[r]; e = rp[r + 1]; }
+    int32_t padc = (r < n) ? (int32_t)r : 0;
+    if (e > b) padc = ci[e - 1];
+    for (int j = 0; j < w; j++) {
+        int64_t dst = base + (int64_t)j * 32 + lane;
+        if (b + j < e) {
+            col[dst] = ci[b + j];
+            val[dst] = cv[b + j];
+            val32[dst] = (float)cv[b + j];
+        } else {
+            col[dst] = padc;
+            val[dst] = 0.0;
+            val32[dst] = 0.0f;
+        }
+    }
+}
+
+// Fused Chebyshev step.  MODE 0: out = sc (A x - cc x); y = c0 x + cj out.
+//                        MODE 1: out = sc (A x - cc x) - xprev; y += cj out.
+//                        MODE 2: out = A x.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(TPB)
+k_cheb_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
+            const int32_t *__restrict__ col, const T *__restrict__ val, int nvec,
+            const T *__restrict__ x, const T *xprev, T *out, T *y, T cc, T sc, T c0, T cj)
+{
+    int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (s >= nslices) return;
+    int lane = threadIdx.x & 31;
+    int64_t base = sptr[s] + lane;
+    int w = (int)((sptr[s + 1] - sptr[s]) >> 5);
+    int64_t r = s * 32 + lane;
+    T v[WREG];
+    int c[WREG];
+    const bool inreg = (w <= WREG);
+    if (inreg) {
+#pragma unroll
+        for (int j = 0; j < WREG; j++) {
+            if (j < w) {
+                v[j] = val[base + 32 * j];
+                c[j] = col[base + 32 * j];
+            } else {
+                v[j] = T(0);
+                c[j] = 0;
+            }
+        }
+    }
+    for (int l = 0; l < nvec; l++) {
+        const T *xl = x + (int64_t)l * n;
+        T acc = T(0);
+        if (inreg) {
+#pragma unroll
+            for (int j = 0; j < WREG; j++)
+                if (j < w) acc += v[j] * __ldg(xl + c[j]);
+        } else {
+            for (int j = 0; j < w; j++) acc += val[base + 32 * j] * __ldg(xl + col[base + 32 * j]);
+        }
+        if (r < n) {
+            int64_t o = (int64_t)l * n + r;
+            if (MODE == 2) {
+                out[o] = acc;
+            } else {
+                T xr = xl[r];
+                T wv = (acc - cc * xr) * sc;
+                if (MODE == 1) wv -= xprev[o];
+                out[o] = wv;
+                if (MODE == 0)
+                    y[o] = c0 * xr + cj * wv;
+                else
+                    y[o] += cj * wv;
+            }
+        }
+    }
+}
+
+// KPM step: the same recurrence without y, plus the moment partial sums
+// sum_l sum_r v_l[r] out_l[r], with v_l[r] = +-1 read from the bit-packed probes
+// (bit `lane` of word bits[l * nslices + s] set <=> v = -1).  Grid-stride over slices with
+// a fixed grid so that the partials of one step fill exactly part[0..gridDim.x).
+template <typename T>
+__global__ void __launch_bounds__(TPB)
+k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
+           const int32_t *__restrict__ col, const T *__restrict__ val, int nvec,
+           const uint32_t *__restrict__ bits, const T *__restrict__ x, const T *xprev, T *out,
+           T cc, T sc, double *__restrict__ part)
+{
+    __shared__ double red[TPB / 32];
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double mom = 0.0;
+    for (int64_t s = warp; s < nslices; s += nwarps) {
+        int64_t base = sptr[s] + lane;
+        int w = (int)((sptr[s + 1] - sptr[s]) >> 5);
+        int64_t r = s * 32 + lane;
+        T v[WREG];
+        int c[WREG];
+        const bool inreg = (w <= WREG);
+        if (inreg) {
+#pragma unroll
+            for (int j = 0; j < WREG; j++) {
+                if (j < w) {
+                    v[j] = val[base + 32 * j];
+                    c[j] = col[base + 32 * j];
+                } else {
+                    v[j] = T(0);
+                    c[j] = 0;
+                }
+            }
+        }
+        T rowmom = T(0);
+        for (int l = 0; l < nvec; l++) {
+            const T *xl = x + (int64_t)l * n;
+            T acc = T(0);
+            if (inreg) {
+#pragma unroll
+                for (int j = 0; j < WREG; j++)
+                    if (j < w) acc += v[j] * __ldg(xl + c[j]);
+            } else {
+                for (int j = 0; j < w; j++)
+                    acc += val[base + 32 * j] * __ldg(xl + col[base + 32 * j]);
+            }
+            uint32_t word = bits[(int64_t)l * nslices + s];
+            if (r < n) {
+                int64_t o = (int64_t)l * n + r;
+                T wv = (acc - cc * xl[r]) * sc;
+                if (mode == 1) wv -= xprev[o];
+                out[o] = wv;
+                rowmom += ((word >> lane) & 1u) ? -wv : wv;
+            }
+        }
+        mom += (double)rowmom;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mom += __shfl_xor_sync(0xffffffffu, mom, off);
+    if (lane == 0) red[threadIdx.x >> 5] = mom;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < TPB / 32; i++) t += red[i];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Probes: W0[l*n + r] = sign of draw(seed, KPM, l*n + r); bits as above.
+template <typename T>
+__global__ void k_kpm_init(int64_t n, int64_t nslices, int nvec, uint64_t key, T *W0,
+                           uint32_t *bits)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t total = nslices * 32 * (int64_t)nvec;
+    if (t >= total) return;  // whole warps exit together: total is a multiple of 32
+    int64_t l = t / (nslices * 32);
+    int64_t r = t - l * nslices * 32;
+    bool neg = false;
+    if (r < n) {
+        uint64_t x = sm_draw(key, (uint64_t)l * (uint64_t)n + (uint64_t)r);
+        neg = (x >> 63) != 0;
+        W0[l * n + r] = neg ? T(-1) : T(1);
+    }
+    uint32_t word = __ballot_sync(0xffffffffu, neg);
+    if ((threadIdx.x & 31) == 0) bits[l * nslices + (r >> 5)] = word;
+}
+
+__global__ void k_f64_to_f32(int64_t count, const double *__restrict__ x, float *__restrict__ y)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) y[i] = (float)x[i];
+}
+
+__global__ void k_f32_to_f64(int64_t count, const float *__restrict__ x, double *__restrict__ y)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) y[i] = (double)x[i];
+}
+
+// uniform(-1, 1) from draw(seed, stream, index*n + i)
+__global__ void k_fill_uniform(int64_t n, uint64_t key, uint64_t index, double *x)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        uint64_t v = sm_draw(key, index * (uint64_t)n + (uint64_t)i);
+        x[i] = 2.0 * ((double)(v >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    }
+}
+
+inline unsigned blocks_for(int64_t threads, int tpb) { return (unsigned)((threads + tpb - 1) / tpb); }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, const double *cv)
+{
+    if (n < 1 || !rp || !ci || !cv) return ctx_fail(c, EVSL_ERR_ARG, "set_csr: bad arguments");
+    if (rp[0] != 0) return ctx_fail(c, EVSL_ERR_ARG, "set_csr: row_ptr[0] != 0");
+    int64_t nnz = rp[n];
+    if (nnz < 1 || nnz >= (int64_t(1) << 31))
+        return ctx_fail(c, EVSL_ERR_ARG, "set_csr: nnz %lld out of range", (long long)nnz);
+    int64_t nslices = (n + 31) / 32;
+    std::vector<int64_t> sptr(nslices + 1);
+    sptr[0] = 0;
+    int maxw = 0;
+    for (int64_t s = 0; s < nslices; s++) {
+        int w = 0;
+        for (int64_t r = s * 32; r < std::min(n, s * 32 + 32); r++) {
+            int64_t len = rp[r + 1] - rp[r];
+            if (len < 0) return ctx_fail(c, EVSL_ERR_ARG, "set_csr: row_ptr decreases at %lld", (long long)r);
+            if (len > w) w = (int)len;
+        }
+        if (w > maxw) maxw = w;
+        sptr[s + 1] = sptr[s] + 32 * (int64_t)w;
+    }
+    for (int64_t p = 0; p < nnz; p++)
+        if (ci[p] < 0 || ci[p] >= n)
+            return ctx_fail(c, EVSL_ERR_ARG, "set_csr: column index %d out of range at %lld", ci[p], (long long)p);
+    sell_free(c);
+    DevMatrix &A = c->A;
+    int64_t ns = sptr[nslices];
+    int64_t *d_rp = nullptr;
+    int32_t *d_ci = nullptr;
+    double *d_cv = nullptr;
+    int st = EVSL_OK;
+    if ((st = ctx_alloc(c, (void **)&A.sptr, sizeof(int64_t) * (nslices + 1))) ||
+        (st = ctx_alloc(c, (void **)&A.col, sizeof(int32_t) * ns)) ||
+        (st = ctx_alloc(c, (void **)&A.val, sizeof(double) * ns)) ||
+        (st = ctx_alloc(c, (void **)&A.val32, sizeof(float) * ns))) {
+        sell_free(c);
+        return st;
+    }
+    A.n = n;
+    A.nnz = nnz;
+    A.nslices = nslices;
+    A.nstored = ns;
+    A.maxw = maxw;
+    if ((st = ctx_alloc(c, (void **)&d_rp, sizeof(int64_t) * (n + 1))) ||
+        (st = ctx_alloc(c, (void **)&d_ci, sizeof(int32_t) * nnz)) ||
+        (st = ctx_alloc(c, (void **)&d_cv, sizeof(double) * nnz))) {
+        ctx_free(c, d_rp, sizeof(int64_t) * (n + 1));
+        ctx_free(c, d_ci, sizeof(int32_t) * nnz);
+        sell_free(c);
+        return st;
+    }
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaMemcpyAsync(A.sptr, sptr.data(), sizeof(int64_t) * (nslices + 1),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ci, ci, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cv, cv, sizeof(double) * nnz, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_sell_fill<double><<<blocks_for(nslices * 32, 256), 256, 0, s>>>(n, nslices, d_rp, d_ci, d_cv,
+                                                                          A.sptr, A.col, A.val, A.val32);
+        c->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    ctx_free(c, d_rp, sizeof(int64_t) * (n + 1));
+    ctx_free(c, d_ci, sizeof(int32_t) * nnz);
+    ctx_free(c, d_cv, sizeof(double) * nnz);
+    if (e != cudaSuccess) {
+        sell_free(c);
+        return ctx_cuda(c, e, "set_csr upload");
+    }
+    return EVSL_OK;
+}
+
+void sell_free(evsl_ctx *c)
+{
+    DevMatrix &A = c->A;
+    ctx_free(c, A.sptr, sizeof(int64_t) * (A.nslices + 1));
+    ctx_free(c, A.col, sizeof(int32_t) * A.nstored);
+    ctx_free(c, A.val, sizeof(double) * A.nstored);
+    ctx_free(c, A.val32, sizeof(float) * A.nstored);
+    A = DevMatrix();
+}
+
+template <typename T>
+static int cheb_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xprev, T *out,
+                       T *y, double cc, double sc, double c0, double cj, const T *val)
+{
+    const DevMatrix &A = c->A;
+    unsigned grid = blocks_for(A.nslices * 32, TPB);
+    T tcc = (T)cc, tsc = (T)sc, tc0 = (T)c0, tcj = (T)cj;
+    if (mode == 0)
+        k_cheb_step<T, 0><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec, x,
+                                                      xprev, out, y, tcc, tsc, tc0, tcj);
+    else if (mode == 1)
+        k_cheb_step<T, 1><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec, x,
+                                                      xprev, out, y, tcc, tsc, tc0, tcj);
+    else
+        k_cheb_step<T, 2><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec, x,
+                                                      xprev, out, y, tcc, tsc, tc0, tcj);
+    c->launches++;
+    return check_launch(c, "cheb_step");
+}
+
+int cheb_step_f64(evsl_ctx *c, int mode, int nvec, const double *x, const double *xprev,
+                  double *out, double *y, double cc, double sc, double c0, double cj)
+{
+    return cheb_step_t<double>(c, mode, nvec, x, xprev, out, y, cc, sc, c0, cj, c->A.val);
+}
+
+int cheb_step_f32(evsl_ctx *c, int mode, int nvec, const float *x, const float *xprev,
+                  float *out, float *y, double cc, double sc, double c0, double cj)
+{
+    return cheb_step_t<float>(c, mode, nvec, x, xprev, out, y, cc, sc, c0, cj, c->A.val32);
+}
+
+int spmv_f64(evsl_ctx *c, int nvec, const double *X, double *Y)
+{
+    return cheb_step_t<double>(c, 2, nvec, X, nullptr, Y, nullptr, 0.0, 1.0, 0.0, 0.0, c->A.val);
+}
+
+int kpm_nblocks(evsl_ctx *c)
+{
+    int64_t need = (c->A.nslices * 32 + TPB - 1) / TPB;
+    int64_t cap = (int64_t)c->dev_sm_count * 8;
+    return (int)std::max<int64_t>(1, std::min(need, cap));
+}
+
+static uint32_t *kpm_bits(evsl_ctx *c, int nvec, int *st)
+{
+    return (uint32_t *)ctx_ws(c, WS_TMP_STAGE, sizeof(uint32_t) * c->A.nslices * nvec, st);
+}
+
+template <typename T>
+static int kpm_init_t(evsl_ctx *c, int nvec, uint64_t seed, T *W0)
+{
+    int st = EVSL_OK;
+    uint32_t *bits = kpm_bits(c, nvec, &st);
+    if (st) return st;
+    int64_t total = c->A.nslices * 32 * (int64_t)nvec;
+    k_kpm_init<T><<<blocks_for(total, 256), 256, 0, c->stream>>>(c->A.n, c->A.nslices, nvec,
+                                                                 sm_key(seed, SM_STREAM_KPM), W0, bits);
+    c->launches++;
+    return check_launch(c, "kpm_init");
+}
+
+int kpm_init_f64(evsl_ctx *c, int nvec, uint64_t seed, double *W0) { return kpm_init_t(c, nvec, seed, W0); }
+int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0) { return kpm_init_t(c, nvec, seed, W0); }
+
+template <typename T>
+static int kpm_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xprev, T *out,
+                      double cc, double sc, double *part, int k, int nblk, const T *val)
+{
+    int st = EVSL_OK;
+    uint32_t *bits = kpm_bits(c, nvec, &st);
+    if (st) return st;
+    const DevMatrix &A = c->A;
+    k_kpm_step<T><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, nvec, bits,
+                                               x, xprev, out, (T)cc, (T)sc, part + (int64_t)k * nblk);
+    c->launches++;
+    return check_launch(c, "kpm_step");
+}
+
+int kpm_step_f64(evsl_ctx *c, int mode, int nvec, uint64_t, const double *x, const double *xprev,
+                 double *out, double cc, double sc, double *part, int k, int nblk)
+{
+    return kpm_step_t<double>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val);
+}
+
+int kpm_step_f32(evsl_ctx *c, int mode, int nvec, uint64_t, const float *x, const float *xprev,
+                 float *out, double cc, double sc, double *part, int k, int nblk)
+{
+    return kpm_step_t<float>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val32);
+}
+
+int convert_f64_to_f32(evsl_ctx *c, int64_t count, const double *x, float *y)
+{
+    k_f64_to_f32<<<blocks_for(count, 256), 256, 0, c->stream>>>(count, x, y);
+    c->launches++;
+    return check_launch(c, "f64_to_f32");
+}
+
+int convert_f32_to_f64(evsl_ctx *c, int64_t count, const float *x, double *y)
+{
+    k_f32_to_f64<<<blocks_for(count, 256), 256, 0, c->stream>>>(count, x, y);
+    c->launches++;
+    return check_launch(c, "f32_to_f64");
+}
+
+int fill_uniform_f64(evsl_ctx *c, int64_t n, uint64_t seed, int stream, uint64_t index, double *x)
+{
+    k_fill_uniform<<<blocks_for(n, 256), 256, 0, c->stream>>>(n, sm_key(seed, (uint64_t)stream), index, x);
+    c->launches++;
+    return check_launch(c, "fill_uniform");
+}

@@ -1,0 +1,246 @@
+"""Thin Python binding of the C ABI in include/evsl_gb300.h (argument marshalling only).
+
+Every numerical step runs inside libevsl_gb300.so; this module converts numpy arrays and
+torch CUDA tensors to plain pointers.  Loading fails loudly if the library is missing: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+EVSL_OK = 0
+ERRORS = {-1: "EVSL_ERR_ARG", -2: "EVSL_ERR_NOMEM", -3: "EVSL_ERR_CUDA", -4: "EVSL_ERR_NOCONV",
+          -5: "EVSL_ERR_CAPACITY", -6: "EVSL_ERR_TIMEOUT", -7: "EVSL_ERR_STATE"}
+DAMP_NONE, DAMP_JACKSON, DAMP_SIGMA = 0, 1, 2
+FP64, FP32 = 0, 1
+K_CHEB_STEP, K_KPM_STEP, K_REORTH, K_RITZ_GEMM, K_SMALL_EIG = range(5)
+
+
+class EvslError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class FilterOpts(C.Structure):
+    _fields_ = [("tau", C.c_double), ("tau_ext", C.c_double), ("damping", C.c_int),
+                ("max_deg", C.c_int)]
+
+
+class PolFilt(C.Structure):
+    _fields_ = [("deg", C.c_int), ("boundary", C.c_int), ("gamma", C.c_double),
+                ("bar", C.c_double), ("lmin", C.c_double), ("lmax", C.c_double),
+                ("a", C.c_double), ("b", C.c_double), ("coef", C.POINTER(C.c_double))]
+
+
+class LanOpts(C.Structure):
+    _fields_ = [("m", C.c_int), ("maxit", C.c_int), ("ncycle", C.c_int), ("tol", C.c_double),
+                ("tau1", C.c_double), ("seed", C.c_uint64), ("prec", C.c_int),
+                ("right_closed", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("niter", C.c_int64), ("nmv", C.c_int64), ("nrestart", C.c_int64),
+                ("npass", C.c_int64), ("t_filter", C.c_double), ("t_orth", C.c_double),
+                ("t_restart", C.c_double), ("t_total", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libevsl_gb300.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"{_build.LIB} is missing; run paper_1802_05215_gb300.build.build()")
+    lib = C.CDLL(_build.LIB)
+    P, d, i32, i64, u64, sz = C.c_void_p, C.c_double, C.c_int, C.c_int64, C.c_uint64, C.c_size_t
+    sig = {
+        "evsl_create": (i32, [C.POINTER(P), i32, sz]),
+        "evsl_destroy": (None, [P]),
+        "evsl_last_error": (C.c_char_p, [P]),
+        "evsl_set_stream": (i32, [P, P]),
+        "evsl_set_csr": (i32, [P, i64, P, P, P]),
+        "evsl_bounds": (i32, [P, i32, u64, P, P]),
+        "evsl_kpm_dos": (i32, [P, i32, i32, u64, d, d, i32, P]),
+        "evsl_slice_by_dos": (i32, [P, i32, i64, d, d, d, d, i32, i32, P, P]),
+        "evsl_cheb_filter_build": (i32, [d, d, d, d, P, P, P, i32]),
+        "evsl_filter_apply": (i32, [P, P, i32, P, P, i32]),
+        "evsl_chebLanTr": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
+        "evsl_launch_count": (i64, [P]),
+        "evsl_profile": (i32, [P, i32]),
+        "evsl_profile_get": (i32, [P, i32, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _addr(a):
+    return C.c_void_p(_ptr(a))
+
+
+class Filter:
+    """A built Chebyshev filter; owns its coefficient array."""
+
+    def __init__(self, pol: PolFilt, coef: np.ndarray, status: int):
+        self.coef = coef
+        self.pol = pol
+        self.pol.coef = coef.ctypes.data_as(C.POINTER(C.c_double))
+        self.status = status
+
+    deg = property(lambda s: s.pol.deg)
+    bar = property(lambda s: s.pol.bar)
+    gamma = property(lambda s: s.pol.gamma)
+    boundary = property(lambda s: s.pol.boundary)
+    lmin = property(lambda s: s.pol.lmin)
+    lmax = property(lambda s: s.pol.lmax)
+
+
+def cheb_filter_build(a, b, lmin, lmax, tau=0.8, tau_ext=0.4, damping=DAMP_JACKSON,
+                      max_deg=10000) -> Filter:
+    lib = load()
+    opts = FilterOpts(tau, tau_ext, damping, max_deg)
+    pol = PolFilt()
+    coef = np.zeros(max_deg + 1)
+    st = lib.evsl_cheb_filter_build(a, b, lmin, lmax, C.byref(opts), C.byref(pol),
+                                    _addr(coef), len(coef))
+    if st not in (EVSL_OK, -4):
+        raise EvslError(st, "cheb_filter_build")
+    coef = coef[:pol.deg + 1].copy()
+    return Filter(pol, coef, st)
+
+
+def slice_by_dos(mu, n, lmin, lmax, xi, eta, nslices, npts=0):
+    lib = load()
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    sli = np.zeros(nslices + 1)
+    est = np.zeros(nslices)
+    st = lib.evsl_slice_by_dos(_addr(mu), len(mu) - 1, n, lmin, lmax, xi, eta, nslices, npts,
+                               _addr(sli), _addr(est))
+    if st != EVSL_OK:
+        raise EvslError(st, "slice_by_dos")
+    return sli, est
+
+
+class Context:
+    """One evsl_ctx: a CUDA device, a stream, the device matrix and workspaces."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.evsl_create(C.byref(h), device, hbm_budget)
+        if st != EVSL_OK:
+            raise EvslError(st, f"evsl_create(device={device}) failed")
+        self.h = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.evsl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st, what):
+        if st != EVSL_OK:
+            raise EvslError(st, f"{what}: {self.lib.evsl_last_error(self.h).decode()}")
+        return st
+
+    def set_stream(self, stream_handle: int | None):
+        self._check(self.lib.evsl_set_stream(self.h, C.c_void_p(stream_handle or 0)), "set_stream")
+
+    def set_csr(self, A):
+        self._check(self.lib.evsl_set_csr(self.h, A.n, _addr(A.row_ptr), _addr(A.col_idx),
+                                          _addr(A.val)), "set_csr")
+        self.n = A.n
+
+    def bounds(self, steps=80, seed=0):
+        lo, hi = C.c_double(), C.c_double()
+        self._check(self.lib.evsl_bounds(self.h, steps, seed, C.byref(lo), C.byref(hi)), "bounds")
+        return lo.value, hi.value
+
+    def kpm_dos(self, degree, nvec, seed, lmin, lmax, prec=FP64):
+        mu = np.zeros(degree + 1)
+        self._check(self.lib.evsl_kpm_dos(self.h, degree, nvec, seed, lmin, lmax, prec,
+                                          _addr(mu)), "kpm_dos")
+        return mu
+
+    def filter_apply(self, filt: Filter, X, Y, prec=FP64):
+        """Y = rho(Ahat) X for device blocks X, Y (n x nvec column-major, e.g. torch tensors
+        of shape (nvec, n) on the GPU)."""
+        nvec = X.numel() // self.n
+        self._check(self.lib.evsl_filter_apply(self.h, C.byref(filt.pol), nvec, _addr(X),
+                                               _addr(Y), prec), "filter_apply")
+
+    def chebLanTr(self, a, b, filt: Filter, m=100, maxit=0, ncycle=10, tol=1e-8, tau1=1e-10,
+                  seed=0, prec=FP64, right_closed=True, cap=None, Y=None, allow_partial=False):
+        """Filtered thick-restart Lanczos on [a, b].  Y: None (host numpy result) or a
+        caller-provided buffer (numpy host array or torch CUDA tensor of n*cap doubles)."""
+        cap = cap or (m + 64)
+        opts = LanOpts(m, maxit, ncycle, tol, tau1, seed, prec, int(right_closed))
+        lam = np.zeros(cap)
+        res = np.zeros(cap)
+        if Y is None:
+            Y = np.zeros((cap, self.n))       # row j = eigenvector j (column-major n x cap)
+        nev = C.c_int()
+        stats = Stats()
+        st = self.lib.evsl_chebLanTr(self.h, a, b, C.byref(filt.pol), C.byref(opts), cap,
+                                     C.byref(nev), _addr(lam), _addr(Y), _addr(res),
+                                     C.byref(stats))
+        if st != EVSL_OK and not (allow_partial and st in (-4, -5)):
+            self._check(st, "chebLanTr")
+        k = nev.value
+        return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
+                    stats=stats.as_dict())
+
+    def launch_count(self) -> int:
+        return int(self.lib.evsl_launch_count(self.h))
+
+    def profile(self, enable: bool):
+        self._check(self.lib.evsl_profile(self.h, int(enable)), "profile")
+
+    def profile_get(self, kernel: int):
+        n = C.c_int64()
+        ms = C.c_double()
+        self._check(self.lib.evsl_profile_get(self.h, kernel, C.byref(n), C.byref(ms)),
+                    "profile_get")
+        return n.value, ms.value

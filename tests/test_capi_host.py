@@ -1,0 +1,90 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a and exports every declared
+symbol, and its pure-host entry points (filter construction, DOS slicer) agree with the
+oracle.  No GPU is needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT, golden
+
+HEADER = os.path.join(ROOT, "include", "evsl_gb300.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(evsl_[A-Za-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_1802_05215_gb300 import native
+    native.load()
+    return native
+
+
+def test_library_exports_every_declared_symbol(native):
+    names = declared_functions()
+    assert len(names) >= 14
+    lib = ctypes.CDLL(native.library_path())
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_library_is_built_for_sm103a(native):
+    # the fatbinary of an sm_103a build carries the architecture name
+    data = open(native.library_path(), "rb").read()
+    assert b"sm_103a" in data
+
+
+def test_filter_build_matches_oracle(native, oracle_mod):
+    cases = [(0.40, 0.48, 0.0, 8.0), (1.0, 1.3, 0.01, 7.99), (0.2, 0.24, 0.0029, 11.997),
+             (-1.0, -0.2, -0.4, 12.36), (11.5, 12.5, 0.0, 12.0), (0.0, 0.9, 0.1, 11.7)]
+    for damping in (native.DAMP_JACKSON, native.DAMP_SIGMA, native.DAMP_NONE):
+        for a, b, lo, hi in cases:
+            f = native.cheb_filter_build(a, b, lo, hi, damping=damping)
+            o = oracle_mod.filter_build(a, b, lo, hi, damping=damping)
+            assert f.deg == o["deg"] and f.boundary == o["boundary"], (a, b, damping)
+            assert abs(f.bar - o["bar"]) < 1e-12 and abs(f.gamma - o["gamma"]) < 1e-12
+            assert np.max(np.abs(f.coef - o["coef"])) < 1e-12 * np.abs(o["coef"]).max()
+
+
+def test_filter_build_table4_degrees(native):
+    for ns, i, left, right, nu, deg in golden("table4_slices.txt"):
+        f = native.cheb_filter_build(float(left), float(right), 0.0, 11.9882,
+                                     damping=native.DAMP_SIGMA)
+        assert f.deg == int(deg)
+
+
+def test_filter_build_errors(native):
+    with pytest.raises(native.EvslError):
+        native.cheb_filter_build(0.5, 0.4, 0.0, 8.0)             # b <= a
+    with pytest.raises(native.EvslError):
+        native.cheb_filter_build(-1.0, 9.0, 0.0, 8.0)            # whole spectrum
+    with pytest.raises(native.EvslError):
+        native.cheb_filter_build(-1.0, -0.5, 0.0, 8.0)           # below the spectrum
+    f = native.cheb_filter_build(0.40, 0.4000001, 0.0, 8.0, max_deg=50)
+    assert f.status == -4 and f.deg == 50                        # max degree reached
+
+
+def test_slicer_matches_oracle(native, oracle_mod):
+    from paper_1802_05215_gb300 import inputs
+    A = inputs.laplacian_2d(60)
+    lo, hi = oracle_mod.bounds(A, 60, 0)
+    mu = oracle_mod.kpm_moments(A, 60, 8, 0, lo, hi)
+    for ns, npts in [(1, 0), (4, 0), (10, 3001), (7, 50)]:
+        s, e = native.slice_by_dos(mu, A.n, lo, hi, 0.3, 2.5, ns, npts)
+        so, eo = oracle_mod.slicer(mu, lo, hi, 0.3, 2.5, ns, npts or None)
+        assert np.max(np.abs(s - so)) < 1e-12 and np.max(np.abs(e - eo)) < 1e-9
+
+
+def test_context_needs_a_gpu(native):
+    # without a usable device the library refuses instead of computing on the CPU
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(native.EvslError):
+        native.Context(0)

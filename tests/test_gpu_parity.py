@@ -1,0 +1,269 @@
+"""GPU parity: the sm_103a kernels behind the C ABI against the FP64 CPU oracle.
+
+Sizes are chosen so that the oracle finishes in seconds while the GPU path spans many
+32-row slices and reduction chunks with a ragged tail (n not a multiple of 32).
+Tolerances: KPM moments |mu_gpu - mu_oracle| <= 1e-12 n (FP64) / 1e-5 n (FP32), n being the
+largest any moment can be (|v^T T_k(Ahat) v| <= ||v||^2 = n); filter outputs relative to
+sum_j |c_j| ||x||_inf; eigenpairs: exact count, eigenvalues within 1e-9 relative, residual
+||Ax - lambda x|| / ||A|| <= 1e-8, ||Y^T Y - I|| <= 1e-10, eigenspaces by projectors.
+"""
+import numpy as np
+import pytest
+
+from closed_form import lap_eigs
+from paper_1802_05215_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1802_05215_gb300 import native
+    native.load()
+    return native
+
+
+@pytest.fixture(scope="module")
+def ctx(nat):
+    c = nat.Context(0)
+    yield c
+    c.close()
+
+
+def _dense_residuals(A, lam, Y):
+    D = A.to_dense()
+    normA = np.abs(np.linalg.eigvalsh(D)).max()
+    return np.linalg.norm(D @ Y - Y * lam, axis=0) / normA
+
+
+# ------------------------------------------------------------------------------ KPM
+@pytest.mark.parametrize("mat", ["lap2d_45", "anderson_13", "lap3d_9"])
+def test_kpm_fp64_matches_oracle(ctx, oracle_mod, mat):
+    A = {"lap2d_45": lambda: I.laplacian_2d(45), "anderson_13": lambda: I.anderson_3d(13, 4.0, 1),
+         "lap3d_9": lambda: I.laplacian_3d(9)}[mat]()
+    ctx.set_csr(A)
+    lo, hi = oracle_mod.bounds(A, 60, 0)
+    for M, nv, seed in [(50, 7, 0), (1, 1, 5), (0, 3, 2)]:
+        mu = ctx.kpm_dos(M, nv, seed, lo, hi)
+        mo = oracle_mod.kpm_moments(A, M, nv, seed, lo, hi)
+        assert mu[0] == A.n
+        assert np.max(np.abs(mu - mo)) <= 1e-12 * A.n
+
+
+def test_kpm_fp32_matches_oracle(ctx, nat, oracle_mod):
+    A = I.anderson_3d(14, 4.0, 0)
+    ctx.set_csr(A)
+    lo, hi = oracle_mod.bounds(A, 60, 0)
+    mu = ctx.kpm_dos(80, 9, 1, lo, hi, prec=nat.FP32)
+    mo = oracle_mod.kpm_moments(A, 80, 9, 1, lo, hi)
+    assert np.max(np.abs(mu - mo)) <= 1e-5 * A.n
+
+
+def test_kpm_is_deterministic(ctx):
+    A = I.laplacian_3d(20)
+    ctx.set_csr(A)
+    m1 = ctx.kpm_dos(40, 5, 9, 0.0, 12.0)
+    m2 = ctx.kpm_dos(40, 5, 9, 0.0, 12.0)
+    assert np.array_equal(m1, m2)
+
+
+def test_kpm_config_2d_100(ctx, oracle_mod):
+    # 100 x 100 Laplacian, degree 80, 20 probes, seed 0
+    A = I.laplacian_2d(100)
+    ctx.set_csr(A)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    mu = ctx.kpm_dos(80, 20, 0, lo, hi)
+    mo = oracle_mod.kpm_moments(A, 80, 20, 0, lo, hi)
+    assert np.max(np.abs(mu - mo)) <= 1e-12 * A.n
+
+
+def test_kpm_full_size_3d_100(ctx, nat, oracle_mod):
+    # n = 1e6, degree 120: 40 probes on the GPU; probes are independent of nvec, so the first
+    # two are checked against the oracle one by one, and the full set against the closed-form
+    # trace statistics and the FP32 run.
+    A = I.laplacian_3d(100)
+    ctx.set_csr(A)
+    lo, hi = 0.0, 12.0
+    mu40 = ctx.kpm_dos(120, 40, 0, lo, hi)
+    mu2 = ctx.kpm_dos(120, 2, 0, lo, hi)
+    mo2 = oracle_mod.kpm_moments(A, 120, 2, 0, lo, hi)
+    assert np.max(np.abs(mu2 - mo2)) <= 1e-12 * A.n
+    assert mu40[0] == A.n
+    e = lap_eigs(3, 100)
+    lh = (e - 6.0) / 6.0
+    for k in range(0, 121, 10):
+        tk = np.cos(k * np.arccos(np.clip(lh, -1, 1)))
+        sig = np.sqrt(2.0 * np.sum(tk * tk) / 40)
+        assert abs(mu40[k] - tk.sum()) <= 6 * sig + 1e-6
+    m32 = ctx.kpm_dos(120, 40, 0, lo, hi, prec=nat.FP32)
+    assert np.max(np.abs(m32 - mu40)) <= 1e-5 * A.n
+
+
+# ------------------------------------------------------------------------------ filter
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-5)])
+def test_filter_apply_matches_oracle(ctx, nat, oracle_mod, prec, tol):
+    import torch
+    A = I.laplacian_2d(45)
+    ctx.set_csr(A)
+    lo, hi = 0.0, 8.0
+    f = nat.cheb_filter_build(1.0, 1.2, lo, hi)
+    assert f.deg > 20
+    X = np.random.default_rng(0).standard_normal((3, A.n))
+    Xd = torch.tensor(X, device="cuda")
+    Yd = torch.empty_like(Xd)
+    ctx.filter_apply(f, Xd, Yd, prec=prec)
+    Y = Yd.cpu().numpy()
+    Yo = oracle_mod.filter_apply(A, lo, hi, f.coef, X.T.copy()).T
+    scale = np.abs(f.coef).sum() * np.abs(X).max()
+    assert np.max(np.abs(Y - Yo)) <= tol * scale
+
+
+def test_filter_apply_degree_edge_cases(ctx, nat, oracle_mod):
+    import torch
+    A = I.anderson_3d(7, 4.0, 0)          # n = 343: 10 full slices + a ragged one
+    ctx.set_csr(A)
+    lo, hi = oracle_mod.bounds(A, 60, 0)
+    X = np.random.default_rng(1).standard_normal((1, A.n))
+    Xd = torch.tensor(X, device="cuda")
+    for coef in [np.array([0.7]), np.array([0.1, -0.4]), np.array([0.2, 0.3, -0.5])]:
+        f = nat.cheb_filter_build(5.0, 6.0, lo, hi)
+        f.coef = coef.copy()
+        f.pol.deg = len(coef) - 1
+        f.pol.coef = f.coef.ctypes.data_as(nat.C.POINTER(nat.C.c_double))
+        Yd = torch.empty_like(Xd)
+        ctx.filter_apply(f, Xd, Yd)
+        Yo = oracle_mod.filter_apply(A, lo, hi, coef, X.T.copy()).T
+        assert np.max(np.abs(Yd.cpu().numpy() - Yo)) <= 1e-13 * np.abs(X).max()
+
+
+# ------------------------------------------------------------------------------ bounds
+@pytest.mark.parametrize("dim,nx", [(2, 30), (3, 11)])
+def test_bounds_match_oracle_and_enclose(ctx, oracle_mod, dim, nx):
+    A = I.laplacian_2d(nx) if dim == 2 else I.laplacian_3d(nx)
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(80, 0)
+    olo, ohi = oracle_mod.bounds(A, 80, 0)
+    e = lap_eigs(dim, nx)
+    assert abs(lo - olo) <= 1e-9 * e[-1] and abs(hi - ohi) <= 1e-9 * e[-1]
+    assert lo <= e[0] + 1e-12 * e[-1] and hi >= e[-1] - 1e-12 * e[-1]
+
+
+# ------------------------------------------------------------------------------ Lanczos
+def _solve_both(ctx, nat, oracle_mod, A, a, b, m=None, tol=1e-8, **kw):
+    ctx.set_csr(A)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    f = nat.cheb_filter_build(a, b, lo, hi)
+    of = oracle_mod.filter_build(a, b, lo, hi)
+    r = ctx.chebLanTr(a, b, f, m=m, tol=tol, **kw)
+    o = oracle_mod.cheblantr(A, a, b, of, m=m, tol=tol, **kw)
+    return r, o
+
+
+@pytest.mark.parametrize("case", [("2d", 20, 1.0, 1.6), ("3d", 12, 0.8, 1.6),
+                                  ("3d", 12, 0.0, 0.9), ("2d", 33, 7.5, 8.0)])
+def test_cheblantr_laplacian(ctx, nat, oracle_mod, case):
+    kind, nx, a, b = case
+    A = I.laplacian_2d(nx) if kind == "2d" else I.laplacian_3d(nx)
+    e = lap_eigs(2 if kind == "2d" else 3, nx)
+    ex = e[(e >= a) & (e <= b)]
+    r, o = _solve_both(ctx, nat, oracle_mod, A, a, b, m=max(2 * len(ex) + 40, 100))
+    assert r["status"] == 0
+    assert r["nev"] == o["nev"] == len(ex)
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.maximum(1, np.abs(ex)))
+    Y = r["Y"][:r["nev"]].T
+    assert np.max(_dense_residuals(A, r["lam"], Y)) <= 1e-8
+    assert np.max(np.abs(r["res"] - _dense_residuals(A, r["lam"], Y))) <= 1e-12
+    assert np.max(np.abs(Y.T @ Y - np.eye(r["nev"]))) <= 1e-10
+    # same eigenspace as the oracle (vectors of repeated eigenvalues are not unique)
+    P, Po = Y @ Y.T, o["Y"] @ o["Y"].T
+    assert np.linalg.norm(P - Po, 2) <= 1e-7
+
+
+@pytest.mark.parametrize("a,b", [(-1.0, 1.0), (3.0, 5.0)])
+def test_cheblantr_anderson_bruteforce(ctx, nat, oracle_mod, a, b):
+    A = I.anderson_3d(7, 4.0, 0)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    ex = ev[(ev >= a) & (ev <= b)]
+    r, o = _solve_both(ctx, nat, oracle_mod, A, a, b, m=max(2 * len(ex) + 40, 100))
+    assert r["nev"] == o["nev"] == len(ex)
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.maximum(1, np.abs(ex)))
+    assert np.max(_dense_residuals(A, r["lam"], r["Y"][:r["nev"]].T)) <= 1e-8
+
+
+def test_cheblantr_config_2d_100(ctx, nat, oracle_mod):
+    A = I.laplacian_2d(100)
+    e = lap_eigs(2, 100)
+    ex = e[(e >= 0.40) & (e <= 0.48)]
+    r, o = _solve_both(ctx, nat, oracle_mod, A, 0.40, 0.48, m=2 * 69 + 40)
+    assert r["status"] == 0 and r["nev"] == o["nev"] == 69
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * ex)
+    assert np.all(np.abs(r["lam"] - o["lam"]) <= 1e-9 * ex)
+    assert r["res"].max() <= 1e-8
+    Y = r["Y"][:69].T
+    assert np.max(np.abs(Y.T @ Y - np.eye(69))) <= 1e-10
+    res = np.array([np.linalg.norm(oracle_mod.spmv(A, Y[:, j]) - r["lam"][j] * Y[:, j])
+                    for j in range(69)]) / 8.0
+    assert res.max() <= 1e-8
+
+
+def test_cheblantr_device_output_matches_host_output(ctx, nat, oracle_mod):
+    import torch
+    A = I.laplacian_2d(24)
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(60, 0)
+    f = nat.cheb_filter_build(2.0, 2.5, lo, hi)
+    rh = ctx.chebLanTr(2.0, 2.5, f, m=100, cap=80)
+    Yd = torch.zeros((80, A.n), dtype=torch.float64, device="cuda")
+    rd = ctx.chebLanTr(2.0, 2.5, f, m=100, cap=80, Y=Yd)
+    k = rh["nev"]
+    assert rd["nev"] == k and np.array_equal(rh["lam"], rd["lam"])
+    assert np.array_equal(rh["Y"][:k], Yd[:k].cpu().numpy())
+
+
+def test_cheblantr_capacity_and_empty_slice(ctx, nat):
+    A = I.laplacian_2d(24)
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(60, 0)
+    f = nat.cheb_filter_build(2.0, 2.5, lo, hi)
+    r = ctx.chebLanTr(2.0, 2.5, f, m=100, cap=5, allow_partial=True)
+    assert r["status"] == -5 and r["nev"] == 5
+    # a slice between two consecutive distinct eigenvalues holds nothing
+    e = lap_eigs(2, 24)
+    u = np.unique(np.round(e, 12))
+    gap = np.argmax(np.diff(u[100:200])) + 100
+    a, b = u[gap] + 1e-3, u[gap + 1] - 1e-3
+    f = nat.cheb_filter_build(a, b, lo, hi)
+    r = ctx.chebLanTr(a, b, f, m=60)
+    assert r["status"] == 0 and r["nev"] == 0
+
+
+def test_set_csr_validation_and_budget(nat):
+    A = I.laplacian_2d(10)
+    with nat.Context(0) as c:
+        bad = I.CSR(A.n, A.row_ptr, A.col_idx.copy(), A.val)
+        bad.col_idx[5] = A.n
+        with pytest.raises(nat.EvslError) as ei:
+            c.set_csr(bad)
+        assert ei.value.code == -1
+        with pytest.raises(nat.EvslError) as ei:
+            c.bounds(10, 0)                    # no matrix set
+        assert ei.value.code == -7
+    with nat.Context(0, hbm_budget=1024) as c:
+        with pytest.raises(nat.EvslError) as ei:
+            c.set_csr(A)
+        assert ei.value.code == -2
+
+
+def test_launch_counter_and_profile(ctx, nat):
+    A = I.laplacian_2d(64)
+    ctx.set_csr(A)
+    n0 = ctx.launch_count()
+    ctx.profile(True)
+    ctx.kpm_dos(30, 4, 0, 0.0, 8.0)
+    launches, ms = ctx.profile_get(nat.K_KPM_STEP)
+    ctx.profile(False)
+    assert launches == 30 and ms > 0
+    assert ctx.launch_count() - n0 >= 31
