@@ -1,0 +1,391 @@
+"""Benchmark of the spectrum-slicing hot path (KPM density, DOS slicing, filter build and
+filtered thick-restart Lanczos) on the 100^3 7-point Laplacian, interval [0.20, 0.60] cut into
+10 DOS-balanced slices (KPM degree 120, 40 Rademacher probes), FP64 filtered Lanczos one
+slice at a time.
+
+One step = one pass of the whole path for one slice: spectral bounds, KPM moments, slicing,
+filter build for the slice, then filtered TR Lanczos on it.  Steps walk through the slices
+each rank owns (longest-processing-time assignment on count x degree; weak scaling, no
+data-path collective).
+  value  : eigenpairs/s with the matrix resident in HBM and the eigenvectors left in HBM
+  e2e    : the same through the C ABI with host buffers: every step uploads the CSR matrix
+           from pinned host memory (evsl_set_csr) and copies the eigenvectors back to pinned
+           host memory (evsl_chebLanTr with a host Y)
+  roofline: the fused Chebyshev filter step (the dominant kernel), algorithmic bytes per
+           launch / mean launch time measured with CUDA events on the library's stream.
+  cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload.
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1802_05215_gb300 import inputs  # noqa: E402
+from paper_1802_05215_gb300.schedule import assign_slices, slice_costs  # noqa: E402
+
+WORKLOAD = "lap3d_100"
+XI, ETA, NSLICES = 0.20, 0.60, 10
+KPM_DEG, KPM_NVEC, SEED = 120, 40, 0
+BOUNDS_STEPS = 80
+TOL = 1e-8
+METRIC = "eigenpairs/s at resid<=1e-8"
+UNIT = "eigenpairs/s"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def lanczos_m(est: float) -> int:
+    # Krylov dimension from the DOS estimate of the slice count (memory grows with it)
+    return int(max(2 * est + 40, 100))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cheb_step_bytes(n: int, nnz: int, nvec: int = 1, b: int = 8) -> float:
+    # algorithmic bytes of one fused filter step: matrix values + column indices, row pointers,
+    # and per column read w_j, w_{j-1}, y and write w_{j+1}, y
+    return nnz * (b + 4) + 8 * (n + 1) + 5 * nvec * n * b
+
+
+def kernel_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1802_05215_gb300", "csrc", "kernels_sparse.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the filter step from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "cheb_step_lap3d_100.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1802_05215_gb300 import native
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    A = inputs.workload(WORKLOAD)["matrix"]()
+    n, nnz = A.n, A.nnz
+    # pinned host copies of the inputs for the end-to-end leg
+    pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+    rp_p, ci_p, v_p = pin(A.row_ptr), pin(A.col_idx), pin(A.val)
+    Apin = inputs.CSR(n, rp_p.numpy(), ci_p.numpy(), v_p.numpy(), A.name)
+    ctx = native.Context(local)
+    ctx.set_csr(A)
+
+    def one_step(t: int, e2e: bool):
+        """Whole path for this rank's t-th slice (LPT assignment, cycled)."""
+        s = owned[t % len(owned)]
+        if e2e:
+            ctx.set_csr(Apin)                       # host -> device copy of the inputs
+        lo, hi = ctx.bounds(BOUNDS_STEPS, SEED)
+        mu = ctx.kpm_dos(KPM_DEG, KPM_NVEC, SEED, lo, hi)
+        sli, est = native.slice_by_dos(mu, n, lo, hi, XI, ETA, NSLICES)
+        a, b = sli[s], sli[s + 1]
+        f = native.cheb_filter_build(a, b, lo, hi)
+        m = lanczos_m(est[s])
+        cap = int(m)
+        Ybuf = Yhost[:cap * n] if e2e else Ydev[:cap * n]
+        r = ctx.chebLanTr(a, b, f, m=m, tol=TOL, seed=SEED, cap=cap, Y=Ybuf,
+                          right_closed=(s == NSLICES - 1))
+        return dict(slice=s, a=a, b=b, deg=f.deg, m=m, nev=r["nev"], est=float(est[s]),
+                    res_max=float(r["res"].max()) if r["nev"] else 0.0, stats=r["stats"])
+
+    # the largest Krylov dimension any slice can use bounds the eigenvector buffers
+    lo, hi = ctx.bounds(BOUNDS_STEPS, SEED)
+    mu = ctx.kpm_dos(KPM_DEG, KPM_NVEC, SEED, lo, hi)
+    sli0, est0 = native.slice_by_dos(mu, n, lo, hi, XI, ETA, NSLICES)
+    capmax = lanczos_m(float(np.max(est0)))
+    degs = [native.cheb_filter_build(sli0[i], sli0[i + 1], lo, hi).deg for i in range(NSLICES)]
+    owned = assign_slices(slice_costs(est0, degs), world)[rank] or [rank % NSLICES]
+    Ydev = torch.empty(capmax * n, dtype=torch.float64, device="cuda")
+    Yhost = torch.empty(capmax * n, dtype=torch.float64).pin_memory().numpy()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    step = 0
+    for _ in range(args.warmup):
+        one_step(step, False)
+        step += 1
+
+    # ---- device-resident leg
+    ctx.profile(True)
+    launches0 = ctx.launch_count()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record()
+        t0 = time.perf_counter()
+        recs = []
+        for _ in range(args.steps):
+            ts = time.perf_counter()
+            rec = one_step(step, False)
+            rec["latency_s"] = time.perf_counter() - ts
+            recs.append(rec)
+            step += 1
+        torch.cuda.synchronize()
+        ev1.record()
+        barrier()
+        wall = time.perf_counter() - t0
+    dev_s = max_over_ranks(max(ev0.elapsed_time(ev1) * 1e-3, 0.0) or wall)
+    launches = ctx.launch_count() - launches0
+    k_launch, k_ms = ctx.profile_get(native.K_CHEB_STEP)
+    prof = {name: ctx.profile_get(k) for name, k in
+            [("cheb_step", native.K_CHEB_STEP), ("kpm_step", native.K_KPM_STEP),
+             ("reorth", native.K_REORTH), ("ritz_gemm", native.K_RITZ_GEMM),
+             ("small_eig", native.K_SMALL_EIG)]}
+    ctx.profile(False)
+    eig_total = sum_over_ranks(float(sum(r["nev"] for r in recs)))
+    value = eig_total / dev_s
+
+    # ---- end-to-end leg through the C ABI with pinned host buffers
+    barrier()
+    t0 = time.perf_counter()
+    e2e_recs = []
+    for _ in range(args.steps):
+        e2e_recs.append(one_step(step, True))
+        step += 1
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_total = sum_over_ranks(float(sum(r["nev"] for r in e2e_recs)))
+    h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.val.nbytes
+    d2h = float(np.mean([r["nev"] * n * 8 for r in e2e_recs]))
+
+    # ---- roofline of the filter step
+    hbm, peak_kind = peaks()
+    per_launch_s = (k_ms / k_launch) * 1e-3 if k_launch else float("nan")
+    alg = cheb_step_bytes(n, nnz)
+    achieved = alg / per_launch_s / 1e9 if k_launch else None
+    roof = {"bound": "hbm", "kernel": "cheb_step (fused SpMV + recurrence + axpy, FP64, s=1)",
+            "achieved": achieved, "peak": hbm, "peak_source": peak_kind, "unit": "GB/s",
+            "frac": achieved / hbm if achieved else None,
+            "alg_bytes_per_launch": alg, "mean_launch_us": per_launch_s * 1e6,
+            "traffic": profiled_traffic()}
+
+    result = None
+    if rank == 0:
+        cpu = cpu_baseline(A, recs[0], lo, hi) if (world == 1 and not args.no_cpu) else None
+        lat = [r["latency_s"] for r in recs]
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_s / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded, deterministic 7-point Laplacian)",
+            "config": {"workload": "3-D 7-point Laplacian 100^3 (n=1e6, nnz=6.94e6), [0.20,0.60] "
+                                   "in 10 KPM-DOS slices (degree 120, 40 probes), Jackson filter, "
+                                   "FP64 thick-restart Lanczos per slice",
+                       "slices_timed": [r["slice"] for r in recs],
+                       "l2": "inputs larger than L2 (Lanczos basis >= 8 GB per slice)"},
+            "e2e": {"value": e2e_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "slice_latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "kernel_ms": {k: v[1] for k, v in prof.items()},
+            "kernel_launches": {k: v[0] for k, v in prof.items()},
+            "steps_detail": [{k: v for k, v in r.items() if k != "stats"} | {
+                "niter": r["stats"]["niter"], "t_filter": r["stats"]["t_filter"],
+                "t_orth": r["stats"]["t_orth"], "t_restart": r["stats"]["t_restart"],
+                "t_total": r["stats"]["t_total"]} for r in recs],
+        }
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return result
+
+
+# ------------------------------------------------------------------------------------------
+def cpu_baseline(A, rec, lo, hi, budget_s: float = 20.0):
+    """The oracle, as it stands, on a bounded sample of the same slice: one filter application
+    of the slice's degree and full reorthogonalisations of one vector against a sample of
+    basis columns, extrapolated with the GPU run's own step count and mean basis width."""
+    import oracle
+    oracle.build()
+    n = A.n
+    pol = oracle.filter_build(rec["a"], rec["b"], lo, hi)
+    x = np.random.default_rng(0).standard_normal(n)
+    t0 = time.perf_counter()
+    oracle.filter_apply(A, lo, hi, pol["coef"], x)
+    t_filter = time.perf_counter() - t0
+    ncol = 64
+    B = np.asfortranarray(np.linalg.qr(np.random.default_rng(1).standard_normal((n, ncol)))[0])
+    z = np.random.default_rng(2).standard_normal(n)
+    t0 = time.perf_counter()
+    oracle.reorth(z, B)
+    t_orth_col = (time.perf_counter() - t0) / ncol
+    niter = rec["stats"]["niter"]
+    mean_cols = rec["nev"] / 2.0 + rec["m"] / 2.0      # locked vectors grow to nev, basis to m
+    t_slice = niter * (t_filter + t_orth_col * mean_cols)
+    return {"value": rec["nev"] / t_slice, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"slice {rec['slice']}: one degree-{pol['deg']} filter application "
+                       f"({t_filter:.2f} s) + one CGS reorthogonalisation against {ncol} columns, "
+                       f"extrapolated to the GPU run's {niter} Lanczos steps at a mean basis of "
+                       f"{mean_cols:.0f} columns (restarts not counted)"),
+            "extrapolated_slice_s": t_slice}
+
+
+def run_reference(args):
+    """Reference arm: the oracle, timed on the host cores, on the same metric and workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    A = inputs.workload(WORKLOAD)["matrix"]()
+    lo, hi = oracle.bounds(A, BOUNDS_STEPS, SEED)
+    # the DOS slicing of the reference arm with a reduced probe count keeps a step bounded
+    mu = oracle.kpm_moments(A, KPM_DEG, 2, SEED, lo, hi)
+    sli, est = oracle.slicer(mu, lo, hi, XI, ETA, NSLICES)
+    vals = []
+    for t in range(args.warmup + args.steps):
+        s = t % NSLICES
+        m = lanczos_m(est[s])
+        nev_est = float(est[s])
+        rec = {"slice": s, "a": sli[s], "b": sli[s + 1], "m": m, "nev": nev_est,
+               "stats": {"niter": int(3 * nev_est)}}
+        cb = cpu_baseline(A, rec, lo, hi)
+        if t >= args.warmup:
+            vals.append(cb)
+    value = float(np.mean([v["value"] for v in vals]))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "3-D 7-point Laplacian 100^3, [0.20,0.60], 10 slices"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": vals[0]["sample"] + "; step count taken as 3x the DOS "
+                                                          "estimate of the slice"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

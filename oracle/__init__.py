@@ -57,6 +57,8 @@ def _load():
         _lib.orc_filter_build.restype = i32
         _lib.orc_filter_build.argtypes = [d, d, d, d, d, d, i32, i32, P, P, P, P, i32, P]
         _lib.orc_filter_apply.argtypes = [i64, P, P, P, d, d, i32, P, i32, P, P]
+        _lib.orc_reorth_cgs.restype = i32
+        _lib.orc_reorth_cgs.argtypes = [i64, P, P, i32]
         _lib.orc_cheblantr.restype = i32
         _lib.orc_cheblantr.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d,
                                        i32, i32, i32, d, d, u64, i32, P, P, P, P, P]
@@ -164,6 +166,13 @@ def filter_apply(A, lmin, lmax, coef, X: np.ndarray) -> np.ndarray:
     _load().orc_filter_apply(*_csr_args(A), lmin, lmax, len(coef) - 1, _p(coef), nvec,
                              _p(X), _p(Y))
     return Y
+
+
+def reorth(z: np.ndarray, B: np.ndarray) -> int:
+    """Full reorthogonalisation of z (in place) against the columns of B (n x k, Fortran
+    order): CGS with the DGKS test, at most two passes (Sec. 2.3).  Returns the passes."""
+    assert z.flags.c_contiguous and B.flags.f_contiguous and z.dtype == B.dtype == np.float64
+    return int(_load().orc_reorth_cgs(len(z), _p(z), _p(B), B.shape[1]))
 
 
 def cheblantr(A, a, b, pol, m=100, maxit=None, ncycle=10, tol=1e-8, tau1=1e-10, seed=0,

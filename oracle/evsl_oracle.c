@@ -263,6 +263,12 @@ static int orc_reorth(int64_t n, double *z, const double *B1, int nc1, const dou
     return passes;
 }
 
+/* Public form of one full reorthogonalisation of z against the ncol columns of B.           */
+int orc_reorth_cgs(int64_t n, double *z, const double *B, int ncol)
+{
+    return orc_reorth(n, z, B, ncol, NULL, 0);
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Spectral bounds (Sec. 2.2.1: "a few steps of the Lanczos algorithm"; LanTrbounds).
  * READING: `steps` Lanczos steps with full reorthogonalisation from the seeded start vector
@@ -590,7 +596,15 @@ void orc_filter_apply(int64_t n, const int64_t *rp, const int32_t *ci, const dou
  *   - a Lanczos breakdown (beta <= 1e-13 * ||y||) continues with a fresh seeded vector
  *     orthogonalised against [U, Q] and a zero coupling;
  *   - the TR set keeps at most m/2 vectors (those with the largest Ritz values), so that every
- *     cycle adds at least m/2 - 1 Lanczos steps and the basis never exceeds m+1 vectors.
+ *     cycle adds at least m/2 - 1 Lanczos steps and the basis never exceeds m+1 vectors;
+ *   - a check at which no Ritz value is >= bar counts as stable only if the previous check of
+ *     the cycle had none either and the cycle has taken max(2 Ncycle, m/4) steps (so a cycle
+ *     that finds nothing ends early, but not before a missed eigenvalue could emerge);
+ *   - stagnation: when two consecutive restarts lock nothing although candidates in the slice
+ *     remain, the locked set and those candidates are refined together by a Rayleigh-Ritz
+ *     projection with A (orc_refine), which separates Ritz vectors that mix nearly equal
+ *     eigenvalues on both sides of a slice end; the next cycle then starts from a fresh vector
+ *     as after a restart without candidates.  At most two refinements per call.
  * Y: n x cap column-major, lam/res: cap.  stats[0..3] = iterations, matvecs, restarts,
  * reorth passes.  Returns 0, -4 if maxit was exceeded, -5 if more than cap converged
  * (nev then holds the number found so far).                                               */
@@ -620,6 +634,60 @@ static void orc_fresh_vector(int64_t n, uint64_t seed, uint64_t index, double *q
     for (int64_t i = 0; i < n; i++) q[i] /= nr;
 }
 
+/* Rayleigh-Ritz refinement with A (READING, see orc_cheblantr): W = [U(:, :nlock), C] has
+ * orthonormal columns; G = W^T A W is eigendecomposed, G = Z diag(theta) Z^T, and the columns of
+ * W Z whose theta lies in the slice and whose residual ||A w - theta w|| <= tol ||A|| become the
+ * new locked set (in the order of Z's columns, i.e. ascending theta).  Returns the new count. */
+static int orc_refine(const orc_csr *A, double a, double b, int right_closed, double normA,
+                      double tol, double *U, int nlock, const double *C, int nc, int cap,
+                      double *lam, double *res)
+{
+    int64_t n = A->n;
+    int p = nlock + nc;
+    double *W = malloc(sizeof(double) * (size_t)n * p), *AW = malloc(sizeof(double) * (size_t)n * p);
+    double *G = malloc(sizeof(double) * (size_t)p * p), *th = malloc(sizeof(double) * p);
+    double *Z = malloc(sizeof(double) * (size_t)p * p);
+    double *w = malloc(sizeof(double) * n), *aw = malloc(sizeof(double) * n);
+    memcpy(W, U, sizeof(double) * (size_t)n * nlock);
+    memcpy(W + (size_t)n * nlock, C, sizeof(double) * (size_t)n * nc);
+    for (int j = 0; j < p; j++) orc_matvec(A, W + (size_t)j * n, AW + (size_t)j * n);
+    for (int j = 0; j < p; j++)
+        for (int i = 0; i < p; i++) AT(G, i, j, p) = orc_dot(n, W + (size_t)i * n, AW + (size_t)j * n);
+    for (int j = 0; j < p; j++)
+        for (int i = 0; i < j; i++) {
+            double s = 0.5 * (AT(G, i, j, p) + AT(G, j, i, p));
+            AT(G, i, j, p) = s;
+            AT(G, j, i, p) = s;
+        }
+    orc_syev(p, G, th, Z);
+    int kept = 0;
+    double *Unew = malloc(sizeof(double) * (size_t)n * (cap > 0 ? cap : 1));
+    for (int j = 0; j < p; j++) {
+        int inside = (th[j] >= a) && (right_closed ? (th[j] <= b) : (th[j] < b));
+        if (!inside) continue;
+        for (int64_t r = 0; r < n; r++) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int q = 0; q < p; q++) {
+                s1 += W[(size_t)q * n + r] * AT(Z, q, j, p);
+                s2 += AW[(size_t)q * n + r] * AT(Z, q, j, p);
+            }
+            w[r] = s1;
+            aw[r] = s2;
+        }
+        for (int64_t r = 0; r < n; r++) aw[r] -= th[j] * w[r];
+        double rj = orc_nrm2(n, aw) / normA;
+        if (rj <= tol && kept < cap) {
+            memcpy(Unew + (size_t)kept * n, w, sizeof(double) * n);
+            lam[kept] = th[j];
+            res[kept] = rj;
+            kept++;
+        }
+    }
+    memcpy(U, Unew, sizeof(double) * (size_t)n * kept);
+    free(W); free(AW); free(G); free(th); free(Z); free(w); free(aw); free(Unew);
+    return kept;
+}
+
 int orc_cheblantr(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                   double a, double b, int right_closed, double lmin, double lmax,
                   int deg, const double *coef, double bar,
@@ -642,7 +710,7 @@ int orc_cheblantr(int64_t n, const int64_t *rp, const int32_t *ci, const double 
     double *Tk = malloc(sizeof(double) * (m + 1) * (m + 1));
     double *trv = malloc(sizeof(double) * (size_t)n * (m + 1));
     double *trtheta = malloc(sizeof(double) * (m + 1)), *trs = malloc(sizeof(double) * (m + 1));
-    int nlock = 0, l = 0, its = 0, nrestart = 0, nocand = 0, status = 0;
+    int nlock = 0, l = 0, its = 0, nrestart = 0, nocand = 0, status = 0, stall = 0, nrefine = 0;
     long npass = 0;
     uint64_t fresh_index = 0;
 
@@ -685,7 +753,7 @@ int orc_cheblantr(int64_t n, const int64_t *rp, const int32_t *ci, const double 
         }
         int lstart = k;
         double t_old = 0.0;
-        int have_old = 0;
+        int have_old = 0, prev_nabove = 0;
         for (int i = k; i < m; i++) {
             its++;
             double *qi = Q + (size_t)i * n;
@@ -721,7 +789,10 @@ int orc_cheblantr(int64_t n, const int64_t *rp, const int32_t *ci, const double 
                     if (theta[jj] >= bar) { t_new += theta[jj]; nabove++; }
                 if (have_old && nabove > 0 && fabs(t_new - t_old) < tau1 * fmax(1.0, fabs(t_new)))
                     break;
+                int min_empty = (2 * ncycle > m / 4) ? 2 * ncycle : m / 4;
+                if (have_old && nabove == 0 && prev_nabove == 0 && k - lstart >= min_empty) break;
                 t_old = t_new;
+                prev_nabove = nabove;
                 have_old = 1;
             }
             if (its > maxit) break;
@@ -732,7 +803,7 @@ int orc_cheblantr(int64_t n, const int64_t *rp, const int32_t *ci, const double 
             for (int ii = 0; ii < k; ii++) AT(Tk, ii, jj, k) = AT(T, ii, jj, m + 1);
         orc_syev(k, Tk, theta, S);
         double betak = AT(T, k - 1, k, m + 1);
-        int ncand = 0, ntr = 0;
+        int ncand = 0, ntr = 0, nlock_before = nlock;
         for (int jj = k - 1; jj >= 0; jj--) {          /* candidates, largest theta first     */
             if (theta[jj] < bar) break;
             const double *s = S + (size_t)jj * k;
@@ -764,9 +835,18 @@ int orc_cheblantr(int64_t n, const int64_t *rp, const int32_t *ci, const double 
             }
         }
         if (ncand == 0) nocand++; else nocand = 0;
+        if (ncand > 0 && nlock == nlock_before) stall++; else stall = 0;
+        int refined = 0;
+        if (stall >= 2 && nrefine < 2 && ntr > 0 && nlock + ntr <= cap) {
+            nlock = orc_refine(&A, a, b, right_closed, normA, tol, U, nlock, trv, ntr, cap, lam, res);
+            nrefine++;
+            stall = 0;
+            nocand = 1;
+            refined = 1;
+        }
         if (nocand >= 2) break;
         if (its > maxit) { status = -4; break; }
-        if (ncand == 0) {
+        if (ncand == 0 || refined) {
             l = 0;
             orc_fresh_vector(n, seed, fresh_index++, Q, U, nlock, NULL, 0);
         } else {

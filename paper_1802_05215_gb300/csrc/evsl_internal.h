@@ -56,7 +56,7 @@ struct evsl_ctx {
 enum WsSlot {
     WS_PARTIAL = 0, WS_SCAL, WS_W0, WS_W1, WS_W2, WS_KPM_PART, WS_F32_X, WS_F32_Y,
     WS_LAN_U, WS_LAN_Q, WS_LAN_Y, WS_LAN_Z, WS_LAN_VEC, WS_LAN_T, WS_LAN_S, WS_LAN_IDX,
-    WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_COUNT
+    WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_COUNT
 };
 
 // ---- context helpers (capi.cu)
@@ -128,6 +128,9 @@ int scale_vec(evsl_ctx *c, int64_t n, double *x, double s, double *dst);
 int colscale_inv_sqrt(evsl_ctx *c, int64_t n, int k, double *Y, const double *nrm2);
 // C (n x l) = A (n x k, lda) * B (k x l, ldb)
 int gemm_nn(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t lda,
+            const double *B, int64_t ldb, double *C, int64_t ldc);
+// C (p x q, ldc) = A^T B, A: n x p (lda), B: n x q (ldb); split over rows, fixed-order sums
+int gemm_tn(evsl_ctx *c, int64_t n, int p, int q, const double *A, int64_t lda,
             const double *B, int64_t ldb, double *C, int64_t ldc);
 // dst[:, t] = src[:, idx[t]] (columns of length rows), idx device
 int gather_cols(evsl_ctx *c, int64_t rows, int k, const double *src, int64_t lds,

@@ -301,6 +301,71 @@ k_gemm_nn(int64_t n, int l, int k, const double *__restrict__ A, int64_t lda,
     }
 }
 
+// C = A^T B (A: n x p, B: n x q, column-major), split over row ranges: block (i, j, z)
+// accumulates the 64 x 64 tile (i, j) over rows [z*rows, (z+1)*rows) into part[z].
+__global__ void __launch_bounds__(256)
+k_gemm_tn(int64_t n, int p, int q, const double *__restrict__ A, int64_t lda,
+          const double *__restrict__ B, int64_t ldb, int64_t rows, double *__restrict__ part)
+{
+    __shared__ double As[GB_K][GB_M + 1];
+    __shared__ double Bs[GB_K][GB_N + 1];
+    int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    int i0 = blockIdx.x * GB_M, j0 = blockIdx.y * GB_N;
+    int64_t r_begin = (int64_t)blockIdx.z * rows, r_end = min(n, r_begin + rows);
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += GB_K) {
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            int e = threadIdx.x + 256 * t;  // 0..1023: 16 rows x 64 columns
+            int rr = e & 15, cc = e >> 4;
+            int64_t gr = r0 + rr;
+            As[rr][cc] = (gr < r_end && i0 + cc < p) ? A[(int64_t)(i0 + cc) * lda + gr] : 0.0;
+            Bs[rr][cc] = (gr < r_end && j0 + cc < q) ? B[(int64_t)(j0 + cc) * ldb + gr] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; kk++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+    double *out = part + (int64_t)blockIdx.z * p * q;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int gi = i0 + tx + 16 * i;
+        if (gi >= p) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int gj = j0 + ty + 16 * j;
+            if (gj < q) out[(int64_t)gj * p + gi] = acc[i][j];
+        }
+    }
+}
+
+// C[i + j*ldc] = sum_z part[z][i + j*p], fixed order
+__global__ void k_sum_splits(int p, int q, int nsplit, const double *__restrict__ part,
+                             double *__restrict__ C, int64_t ldc)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)p * q) return;
+    int i = (int)(t % p), j = (int)(t / p);
+    double s = 0.0;
+    for (int z = 0; z < nsplit; z++) s += part[(int64_t)z * p * q + t];
+    C[(int64_t)j * ldc + i] = s;
+}
+
 // ---------------------------------------------------------------- Jacobi eigensolver
 // Round-robin ("chess tournament") pairing of M (even) indices: round r in [0, M-1),
 // pair i in [0, M/2).  Every unordered pair occurs once per sweep of M-1 rounds.
@@ -593,6 +658,28 @@ int gemm_nn(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t lda, 
     k_gemm_nn<<<grid, 256, 0, c->stream>>>(n, l, k, A, lda, B, ldb, C, ldc);
     c->launches++;
     return check_launch(c, "gemm_nn");
+}
+
+int gemm_tn(evsl_ctx *c, int64_t n, int p, int q, const double *A, int64_t lda, const double *B,
+            int64_t ldb, double *C, int64_t ldc)
+{
+    if (p <= 0 || q <= 0) return EVSL_OK;
+    int tiles = ((p + GB_M - 1) / GB_M) * ((q + GB_N - 1) / GB_N);
+    int64_t nsplit = std::max<int64_t>(1, (4 * (int64_t)c->dev_sm_count + tiles - 1) / tiles);
+    nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, n / 1024));
+    int64_t rows = (n + nsplit - 1) / nsplit;
+    rows = (rows + GB_K - 1) / GB_K * GB_K;
+    nsplit = (n + rows - 1) / rows;
+    int st = EVSL_OK;
+    double *part = partials(c, nsplit * (int64_t)p * q, &st);
+    if (st) return st;
+    dim3 grid((unsigned)((p + GB_M - 1) / GB_M), (unsigned)((q + GB_N - 1) / GB_N), (unsigned)nsplit);
+    k_gemm_tn<<<grid, 256, 0, c->stream>>>(n, p, q, A, lda, B, ldb, rows, part);
+    c->launches++;
+    EVSL_TRY(check_launch(c, "gemm_tn"));
+    k_sum_splits<<<nblk((int64_t)p * q, 256), 256, 0, c->stream>>>(p, q, (int)nsplit, part, C, ldc);
+    c->launches++;
+    return check_launch(c, "gemm_tn reduce");
 }
 
 int gather_cols(evsl_ctx *c, int64_t rows, int k, const double *src, int64_t lds, const int *idx,

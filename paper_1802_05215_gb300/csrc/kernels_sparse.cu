@@ -75,10 +75,51 @@ __global__ void k_sell_fill(int64_t n, int64_t nslices, const int64_t *__restric
 //                        MODE 1: out = sc (A x - cc x) - xprev; y += cj out.
 //                        MODE 2: out = A x.
 template <typename T, int MODE>
+__device__ __forceinline__ void cheb_epilogue(int64_t o, T acc, T xr, const T *xprev, T *out, T *y,
+                                              T cc, T sc, T c0, T cj)
+{
+    if (MODE == 2) {
+        out[o] = acc;
+    } else {
+        T wv = (acc - cc * xr) * sc;
+        if (MODE == 1) wv -= xprev[o];
+        out[o] = wv;
+        if (MODE == 0)
+            y[o] = c0 * xr + cj * wv;
+        else
+            y[o] += cj * wv;
+    }
+}
+
+// Single vector: each nonzero is used once, so nothing is cached in registers; the loop is
+// unrolled so that several index loads and gathers are in flight per warp.
+template <typename T, int MODE>
 __global__ void __launch_bounds__(TPB)
-k_cheb_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
-            const int32_t *__restrict__ col, const T *__restrict__ val, int nvec,
-            const T *__restrict__ x, const T *xprev, T *out, T *y, T cc, T sc, T c0, T cj)
+k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
+             const int32_t *__restrict__ col, const T *__restrict__ val,
+             const T *__restrict__ x, const T *xprev, T *out, T *y, T cc, T sc, T c0, T cj)
+{
+    int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (s >= nslices) return;
+    int lane = threadIdx.x & 31;
+    int64_t b0 = sptr[s];
+    int w = (int)((sptr[s + 1] - b0) >> 5);
+    const T *vp = val + b0 + lane;
+    const int32_t *cp = col + b0 + lane;
+    T acc = T(0);
+#pragma unroll 4
+    for (int j = 0; j < w; j++) acc += vp[32 * j] * __ldg(x + cp[32 * j]);
+    int64_t r = s * 32 + lane;
+    if (r < n) cheb_epilogue<T, MODE>(r, acc, MODE == 2 ? T(0) : x[r], xprev, out, y, cc, sc, c0, cj);
+}
+
+// Block of nvec columns (column-major, ld = n): the slice's nonzeros stay in registers and
+// the columns are processed NC at a time so that NC * w gathers are in flight per warp.
+template <typename T, int MODE, int NC>
+__global__ void __launch_bounds__(TPB)
+k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
+             const int32_t *__restrict__ col, const T *__restrict__ val, int nvec,
+             const T *__restrict__ x, const T *xprev, T *out, T *y, T cc, T sc, T c0, T cj)
 {
     int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (s >= nslices) return;
@@ -89,20 +130,40 @@ k_cheb_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
     T v[WREG];
     int c[WREG];
     const bool inreg = (w <= WREG);
-    if (inreg) {
 #pragma unroll
-        for (int j = 0; j < WREG; j++) {
-            if (j < w) {
-                v[j] = val[base + 32 * j];
-                c[j] = col[base + 32 * j];
-            } else {
-                v[j] = T(0);
-                c[j] = 0;
+    for (int j = 0; j < WREG; j++) {
+        v[j] = (inreg && j < w) ? val[base + 32 * j] : T(0);
+        c[j] = (inreg && j < w) ? col[base + 32 * j] : 0;
+    }
+    int l0 = 0;
+    for (; l0 + NC <= nvec; l0 += NC) {
+        T acc[NC];
+#pragma unroll
+        for (int q = 0; q < NC; q++) acc[q] = T(0);
+        if (inreg) {
+#pragma unroll
+            for (int j = 0; j < WREG; j++)
+                if (j < w)
+#pragma unroll
+                    for (int q = 0; q < NC; q++) acc[q] += v[j] * __ldg(x + (int64_t)(l0 + q) * n + c[j]);
+        } else {
+            for (int j = 0; j < w; j++) {
+                T vj = val[base + 32 * j];
+                int cj_ = col[base + 32 * j];
+#pragma unroll
+                for (int q = 0; q < NC; q++) acc[q] += vj * __ldg(x + (int64_t)(l0 + q) * n + cj_);
+            }
+        }
+        if (r < n) {
+#pragma unroll
+            for (int q = 0; q < NC; q++) {
+                int64_t o = (int64_t)(l0 + q) * n + r;
+                cheb_epilogue<T, MODE>(o, acc[q], MODE == 2 ? T(0) : x[o], xprev, out, y, cc, sc, c0, cj);
             }
         }
     }
-    for (int l = 0; l < nvec; l++) {
-        const T *xl = x + (int64_t)l * n;
+    for (; l0 < nvec; l0++) {
+        const T *xl = x + (int64_t)l0 * n;
         T acc = T(0);
         if (inreg) {
 #pragma unroll
@@ -112,19 +173,8 @@ k_cheb_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
             for (int j = 0; j < w; j++) acc += val[base + 32 * j] * __ldg(xl + col[base + 32 * j]);
         }
         if (r < n) {
-            int64_t o = (int64_t)l * n + r;
-            if (MODE == 2) {
-                out[o] = acc;
-            } else {
-                T xr = xl[r];
-                T wv = (acc - cc * xr) * sc;
-                if (MODE == 1) wv -= xprev[o];
-                out[o] = wv;
-                if (MODE == 0)
-                    y[o] = c0 * xr + cj * wv;
-                else
-                    y[o] += cj * wv;
-            }
+            int64_t o = (int64_t)l0 * n + r;
+            cheb_epilogue<T, MODE>(o, acc, MODE == 2 ? T(0) : xl[r], xprev, out, y, cc, sc, c0, cj);
         }
     }
 }
@@ -133,7 +183,7 @@ k_cheb_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
 // sum_l sum_r v_l[r] out_l[r], with v_l[r] = +-1 read from the bit-packed probes
 // (bit `lane` of word bits[l * nslices + s] set <=> v = -1).  Grid-stride over slices with
 // a fixed grid so that the partials of one step fill exactly part[0..gridDim.x).
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(TPB)
 k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
            const int32_t *__restrict__ col, const T *__restrict__ val, int nvec,
@@ -152,37 +202,44 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
         T v[WREG];
         int c[WREG];
         const bool inreg = (w <= WREG);
-        if (inreg) {
 #pragma unroll
-            for (int j = 0; j < WREG; j++) {
-                if (j < w) {
-                    v[j] = val[base + 32 * j];
-                    c[j] = col[base + 32 * j];
-                } else {
-                    v[j] = T(0);
-                    c[j] = 0;
-                }
-            }
+        for (int j = 0; j < WREG; j++) {
+            v[j] = (inreg && j < w) ? val[base + 32 * j] : T(0);
+            c[j] = (inreg && j < w) ? col[base + 32 * j] : 0;
         }
         T rowmom = T(0);
-        for (int l = 0; l < nvec; l++) {
-            const T *xl = x + (int64_t)l * n;
-            T acc = T(0);
+        for (int l0 = 0; l0 < nvec; l0 += NC) {
+            T acc[NC];
+#pragma unroll
+            for (int q = 0; q < NC; q++) acc[q] = T(0);
             if (inreg) {
 #pragma unroll
                 for (int j = 0; j < WREG; j++)
-                    if (j < w) acc += v[j] * __ldg(xl + c[j]);
+                    if (j < w)
+#pragma unroll
+                        for (int q = 0; q < NC; q++)
+                            if (l0 + q < nvec) acc[q] += v[j] * __ldg(x + (int64_t)(l0 + q) * n + c[j]);
             } else {
-                for (int j = 0; j < w; j++)
-                    acc += val[base + 32 * j] * __ldg(xl + col[base + 32 * j]);
+                for (int j = 0; j < w; j++) {
+                    T vj = val[base + 32 * j];
+                    int cj_ = col[base + 32 * j];
+#pragma unroll
+                    for (int q = 0; q < NC; q++)
+                        if (l0 + q < nvec) acc[q] += vj * __ldg(x + (int64_t)(l0 + q) * n + cj_);
+                }
             }
-            uint32_t word = bits[(int64_t)l * nslices + s];
-            if (r < n) {
-                int64_t o = (int64_t)l * n + r;
-                T wv = (acc - cc * xl[r]) * sc;
-                if (mode == 1) wv -= xprev[o];
-                out[o] = wv;
-                rowmom += ((word >> lane) & 1u) ? -wv : wv;
+#pragma unroll
+            for (int q = 0; q < NC; q++) {
+                int l = l0 + q;
+                if (l >= nvec) break;
+                uint32_t word = bits[(int64_t)l * nslices + s];
+                if (r < n) {
+                    int64_t o = (int64_t)l * n + r;
+                    T wv = (acc[q] - cc * x[o]) * sc;
+                    if (mode == 1) wv -= xprev[o];
+                    out[o] = wv;
+                    rowmom += ((word >> lane) & 1u) ? -wv : wv;
+                }
             }
         }
         mom += (double)rowmom;
@@ -329,22 +386,32 @@ void sell_free(evsl_ctx *c)
     A = DevMatrix();
 }
 
+template <typename T, int MODE>
+static void launch_cheb(evsl_ctx *c, unsigned grid, int nvec, const T *val, const T *x, const T *xprev,
+                        T *out, T *y, T cc, T sc, T c0, T cj)
+{
+    const DevMatrix &A = c->A;
+    constexpr int NC = sizeof(T) == 8 ? 2 : 4;
+    if (nvec == 1)
+        k_cheb_step1<T, MODE><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, x, xprev,
+                                                          out, y, cc, sc, c0, cj);
+    else
+        k_cheb_stepN<T, MODE, NC><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec,
+                                                              x, xprev, out, y, cc, sc, c0, cj);
+}
+
 template <typename T>
 static int cheb_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xprev, T *out,
                        T *y, double cc, double sc, double c0, double cj, const T *val)
 {
-    const DevMatrix &A = c->A;
-    unsigned grid = blocks_for(A.nslices * 32, TPB);
+    unsigned grid = blocks_for(c->A.nslices * 32, TPB);
     T tcc = (T)cc, tsc = (T)sc, tc0 = (T)c0, tcj = (T)cj;
     if (mode == 0)
-        k_cheb_step<T, 0><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec, x,
-                                                      xprev, out, y, tcc, tsc, tc0, tcj);
+        launch_cheb<T, 0>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj);
     else if (mode == 1)
-        k_cheb_step<T, 1><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec, x,
-                                                      xprev, out, y, tcc, tsc, tc0, tcj);
+        launch_cheb<T, 1>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj);
     else
-        k_cheb_step<T, 2><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec, x,
-                                                      xprev, out, y, tcc, tsc, tc0, tcj);
+        launch_cheb<T, 2>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj);
     c->launches++;
     return check_launch(c, "cheb_step");
 }
@@ -402,7 +469,8 @@ static int kpm_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xpre
     uint32_t *bits = kpm_bits(c, nvec, &st);
     if (st) return st;
     const DevMatrix &A = c->A;
-    k_kpm_step<T><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, nvec, bits,
+    constexpr int NC = sizeof(T) == 8 ? 2 : 4;
+    k_kpm_step<T, NC><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, nvec, bits,
                                                x, xprev, out, (T)cc, (T)sc, part + (int64_t)k * nblk);
     c->launches++;
     return check_launch(c, "kpm_step");

@@ -4,6 +4,8 @@
 // context's stream; the host keeps only the small projected matrix and the control flow.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -277,6 +279,83 @@ int reorth(LanState &S, double *z, int nlock, int nq, double nrm_before2, double
     return EVSL_OK;
 }
 
+// Rayleigh-Ritz refinement with A over W = U[:, :p] (orthonormal columns): G = W^T A W =
+// Z diag(theta) Z^T; the columns of W Z with theta in the slice and ||A w - theta w|| <= tol ||A||
+// replace the locked set, in ascending theta.  lam/res are replaced accordingly.
+int refine_locked(LanState &S, double a, double b, bool right_closed, double normA, double tol,
+                  int p, std::vector<double> &lam, std::vector<double> &res, int *kept_out,
+                  bool verbose)
+{
+    evsl_ctx *c = S.c;
+    const int64_t n = S.n;
+    int st = EVSL_OK;
+    double *G = (double *)ctx_ws(c, WS_LAN_G, sizeof(double) * (size_t)p * p, &st);
+    if (st) return st;
+    const int zc = std::min(p, 128);
+    S.Z = (double *)ctx_ws(c, WS_LAN_Z, sizeof(double) * n * zc, &st);
+    if (st) return st;
+    for (int j0 = 0; j0 < p; j0 += zc) {
+        int nc = std::min(zc, p - j0);
+        EVSL_TRY(spmv_f64(c, nc, S.U + (int64_t)j0 * n, S.Z));
+        EVSL_TRY(gemm_tn(c, n, p, nc, S.U, n, S.Z, n, G + (int64_t)j0 * p, p));
+    }
+    std::vector<double> Gh((size_t)p * p), w(p);
+    EVSL_TRY(d2h(c, Gh.data(), G, sizeof(double) * Gh.size()));
+    for (int j = 0; j < p; j++)
+        for (int i = 0; i < j; i++) {
+            double v = 0.5 * (Gh[(size_t)j * p + i] + Gh[(size_t)i * p + j]);
+            Gh[(size_t)j * p + i] = v;
+            Gh[(size_t)i * p + j] = v;
+        }
+    int M = p + (p & 1);
+    S.Vj = (double *)ctx_ws(c, WS_LAN_T, sizeof(double) * (size_t)M * M, &st);
+    if (st) return st;
+    S.S = (double *)ctx_ws(c, WS_LAN_S, sizeof(double) * (size_t)M * M, &st);
+    if (st) return st;
+    int ldv = 0, sweeps = 0;
+    EVSL_TRY(jacobi_eig(c, p, Gh.data(), w.data(), S.Vj, &ldv, &sweeps));
+    std::vector<int> order(p);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] < w[y]; });
+    S.idxd = (int *)ctx_ws(c, WS_LAN_IDX, sizeof(int) * (size_t)(2 * p + 8), &st);
+    if (st) return st;
+    EVSL_TRY(h2d(c, S.idxd, order.data(), sizeof(int) * p));
+    EVSL_TRY(gather_cols(c, p, p, S.Vj, ldv, S.idxd, S.S, p));
+    S.Yt = (double *)ctx_ws(c, WS_LAN_Y, sizeof(double) * n * std::max(S.m, p), &st);
+    if (st) return st;
+    EVSL_TRY(gemm_nn(c, n, p, p, S.U, n, S.S, p, S.Yt, n));
+    std::vector<double> th(p), r2(p);
+    for (int j = 0; j < p; j++) th[j] = w[order[j]];
+    double *lamd = (double *)ctx_ws(c, WS_KPM_PART, sizeof(double) * 2 * (size_t)p, &st);
+    if (st) return st;
+    EVSL_TRY(h2d(c, lamd, th.data(), sizeof(double) * p));
+    for (int j0 = 0; j0 < p; j0 += zc) {
+        int nc = std::min(zc, p - j0);
+        EVSL_TRY(spmv_f64(c, nc, S.Yt + (int64_t)j0 * n, S.Z));
+        EVSL_TRY(colres2(c, n, nc, S.Z, S.Yt + (int64_t)j0 * n, n, lamd + j0, lamd + p + j0));
+    }
+    EVSL_TRY(d2h(c, r2.data(), lamd + p, sizeof(double) * p));
+    std::vector<int> keep;
+    lam.clear();
+    res.clear();
+    for (int j = 0; j < p; j++) {
+        bool inside = (th[j] >= a) && (right_closed ? (th[j] <= b) : (th[j] < b));
+        double rj = std::sqrt(std::max(0.0, r2[j])) / normA;
+        if (inside && rj <= tol && (int)keep.size() < S.cap) {
+            keep.push_back(j);
+            lam.push_back(th[j]);
+            res.push_back(rj);
+        }
+    }
+    if (!keep.empty()) {
+        EVSL_TRY(h2d(c, S.idxd + p, keep.data(), sizeof(int) * keep.size()));
+        EVSL_TRY(gather_cols(c, n, (int)keep.size(), S.Yt, n, S.idxd + p, S.U, n));
+    }
+    if (verbose) fprintf(stderr, "[evsl] refinement: p=%d kept=%zu sweeps=%d\n", p, keep.size(), sweeps);
+    *kept_out = (int)keep.size();
+    return EVSL_OK;
+}
+
 float ev_ms(cudaEvent_t a, cudaEvent_t b)
 {
     float ms = 0.f;
@@ -340,9 +419,11 @@ int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
     S.T.assign((size_t)(m + 1) * (m + 1), 0.0);
     std::vector<double> lam_l, res_l;  // locked pairs in locking order
     std::vector<double> trtheta, trs;
-    int nlock = 0, l = 0, its = 0, nrestart = 0, nocand = 0, status = EVSL_OK;
+    int nlock = 0, l = 0, its = 0, nrestart = 0, nocand = 0, status = EVSL_OK, stall = 0, nrefine = 0;
     uint64_t fresh_index = 0;
     const uint64_t seed = o->seed;
+    const char *venv = getenv("EVSL_VERBOSE");
+    const bool verbose = venv && venv[0] == '1';
 
     // one filtered Lanczos step on column i (0-based); the caller sets up T's coupling
     auto apply_filter = [&](const double *q) -> int {
@@ -398,6 +479,7 @@ int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
         const int lstart = k;
         double t_old = 0.0;
         bool have_old = false;
+        int prev_nabove = 0;
         for (int i = k; i < m; i++) {
             its++;
             double *qi = S.Q + (int64_t)i * n;
@@ -454,9 +536,15 @@ int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
                     EVSL_TRY(bisect_eigs(c, k, l, dd.data(), ee.data(), nbelow, k, lo, hi, w.data()));
                     for (double v : w) t_new += v;
                 }
+                if (verbose && (k - lstart) % (ncycle * 20) == 0)
+                    fprintf(stderr, "[evsl]   check its=%d k=%d nabove=%d t=%.12f\n", its, k, nabove, t_new);
                 if (have_old && nabove > 0 && std::fabs(t_new - t_old) < tau1 * std::max(1.0, std::fabs(t_new)))
                     break;
+                // a cycle with nothing above bar ends once it had time for a missed eigenvalue to emerge
+                if (have_old && nabove == 0 && prev_nabove == 0 && k - lstart >= std::max(2 * ncycle, m / 4))
+                    break;
                 t_old = t_new;
+                prev_nabove = nabove;
                 have_old = true;
             }
             if (its > maxit) break;
@@ -476,6 +564,7 @@ int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
         int ncand0 = 0;
         while (ncand0 < k && w[order[ncand0]] >= bar) ncand0++;
         int ncand = 0;
+        const int nlock_before = nlock;
         std::vector<int> lock_idx, tr_idx;
         std::vector<double> new_trtheta, new_trs;
         if (ncand0 > 0) {
@@ -532,7 +621,26 @@ int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
         }
         if (status == EVSL_ERR_CAPACITY) break;
         const int ntr = (int)tr_idx.size();
+        if (verbose)
+            fprintf(stderr, "[evsl] restart %d: its=%d k=%d l=%d jacobi_sweeps=%d cand>=bar=%d in_slice=%d "
+                            "locked+%d ntr=%d nlock=%d beta_k=%.3e\n",
+                    nrestart, its, k, l, sweeps, ncand0, ncand, (int)lock_idx.size(), ntr,
+                    nlock, betak);
         if (ncand == 0) nocand++; else nocand = 0;
+        if (ncand > 0 && nlock == nlock_before) stall++; else stall = 0;
+        bool refined = false;
+        if (stall >= 2 && nrefine < 2 && ntr > 0 && nlock + ntr <= cap) {
+            // stagnation: Rayleigh-Ritz with A over the locked set and the stuck candidates
+            EVSL_TRY(h2d(c, S.idxd, tr_idx.data(), sizeof(int) * ntr));
+            EVSL_TRY(gather_cols(c, n, ntr, S.Yt, n, S.idxd, S.U + (int64_t)nlock * n, n));
+            int kept = 0;
+            EVSL_TRY(refine_locked(S, a, b, o->right_closed != 0, normA, tol, nlock + ntr, lam_l, res_l, &kept, verbose));
+            nlock = kept;
+            nrefine++;
+            stall = 0;
+            nocand = 1;
+            refined = true;
+        }
         cudaEventRecord(S.e1, c->stream);
         cudaEventSynchronize(S.e1);
         S.t_restart += ev_ms(S.e0, S.e1) * 1e-3;
@@ -541,7 +649,7 @@ int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
             status = EVSL_ERR_NOCONV;
             break;
         }
-        if (ncand == 0) {
+        if (ncand == 0 || refined) {
             l = 0;
             EVSL_TRY(fresh_vector(S, seed, fresh_index++, S.Q, nlock, 0));
         } else {
