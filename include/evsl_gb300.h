@@ -131,6 +131,15 @@ int evsl_cheb_filter_build(double a, double b, double lmin, double lmax,
 int evsl_filter_apply(evsl_ctx *ctx, const evsl_polfilt *pol, int nvec, const double *X,
                       double *Y, evsl_precision prec);
 
+/* Multi-slice filter application: column t of X gets filter pols[t] (the slices of one
+ * interval are independent, Sec. 2.1 and 2.6, so their filters can share each pass over the
+ * matrix).  All filters must use the same [lmin, lmax].  Columns are processed in order of
+ * decreasing degree; at degree j one launch updates every column whose degree is >= j, so the
+ * matrix is read once per degree for all slices.  X, Y: DEVICE n x npol column-major FP64
+ * (non-overlapping); prec as in evsl_filter_apply. */
+int evsl_filter_apply_multi(evsl_ctx *ctx, int npol, const evsl_polfilt *pols, const double *X,
+                            double *Y, evsl_precision prec);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Filtered thick-restart Lanczos with locking (Sec. 2.5, Algorithm 2; ChebLanTr) on the slice
  * [a, b] with filter pol (built for the same slice).  Candidates are the Ritz values of
@@ -168,6 +177,47 @@ typedef struct {
 int evsl_chebLanTr(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol,
                    const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
                    double *res, evsl_stats *stats);
+
+/* Several slices of one matrix solved together (Sec. 2.6: slices are independent; here they
+ * share the GPU instead of separate processes).  Each job is one slice with its own filter,
+ * Krylov dimension and outputs; the slices advance in lockstep and every Lanczos step applies
+ * all their filters in one multi-slice pass per degree (as evsl_filter_apply_multi), while
+ * reorthogonalisation, restarts and locking stay per slice exactly as in evsl_chebLanTr.
+ * All filters must share [lmin, lmax].  opts supplies maxit (per slice), ncycle, tol, tau1,
+ * seed and prec; opts->m and opts->right_closed are taken from each job instead.  Device
+ * memory: each slice holds n x (cap + m + 1) doubles for its bases.  The call returns the first
+ * failing job's status (EVSL_OK if all succeeded); each job's own status is in job.status. */
+typedef struct {
+    double a, b;                /* the slice                                                */
+    const evsl_polfilt *pol;    /* its filter                                               */
+    int m;                      /* Krylov dimension for this slice                          */
+    int cap;                    /* capacity of lam, res and Y                               */
+    int right_closed;           /* 1: lambda in [a, b]; 0: lambda in [a, b)                 */
+    int *nev;                   /* out: number of pairs                                     */
+    double *lam, *res;          /* out: host arrays of cap entries                          */
+    double *Y;                  /* out: n x cap column-major, host or device memory         */
+    evsl_stats *stats;          /* out: may be NULL                                         */
+    int status;                 /* out: this slice's evsl_status                            */
+} evsl_slice_job;
+
+int evsl_chebLanTr_batch(evsl_ctx *ctx, int njobs, evsl_slice_job *jobs, const evsl_lan_opts *opts);
+
+/* Incremental form of evsl_chebLanTr_batch, for serving: jobs (slice solves on the context's
+ * matrix) join between steps and leave when finished, so requests that arrive while others run
+ * are admitted as soon as device memory allows (continuous batching).  evsl_batch_add allocates
+ * the job's bases (EVSL_ERR_NOMEM if the context's HBM budget would be exceeded; the job is then
+ * not admitted and the caller may retry later) and RETAINS the job pointer until the job
+ * finishes.  evsl_batch_step performs one Lanczos step of every active job (one multi-slice
+ * filter pass per degree, then each job's reorthogonalisation and, where a cycle ends, its
+ * restart); finished jobs get their outputs and status written, their device memory released,
+ * and are counted in *nfinished.  *nactive is the number of jobs still running.  Results of a
+ * job do not depend on which other jobs share its steps.  Destroying a batch discards the
+ * unfinished jobs without writing their outputs. */
+typedef struct evsl_batch evsl_batch;
+int evsl_batch_create(evsl_ctx *ctx, const evsl_lan_opts *opts, evsl_batch **batch);
+int evsl_batch_add(evsl_batch *batch, evsl_slice_job *job);
+int evsl_batch_step(evsl_batch *batch, int *nactive, int *nfinished);
+void evsl_batch_destroy(evsl_batch *batch);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Instrumentation (no counterpart in the paper).

@@ -238,6 +238,21 @@ int evsl_filter_apply(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doub
     return drv_filter_apply(c, pol, nvec, X, Y, prec);
 }
 
+int evsl_filter_apply_multi(evsl_ctx *c, int npol, const evsl_polfilt *pols, const double *X,
+                            double *Y, evsl_precision prec)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!pols || npol < 1 || !X || !Y || (prec != EVSL_FP64 && prec != EVSL_FP32))
+        return ctx_fail(c, EVSL_ERR_ARG, "filter_apply_multi: bad arguments");
+    for (int t = 0; t < npol; t++)
+        if (!pols[t].coef || pols[t].deg < 0)
+            return ctx_fail(c, EVSL_ERR_ARG, "filter_apply_multi: filter %d has no coefficients", t);
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "filter_apply_multi: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_filter_apply_multi(c, npol, pols, X, Y, prec);
+}
+
 int evsl_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
                    const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
                    double *res, evsl_stats *stats)
@@ -249,6 +264,63 @@ int evsl_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
     if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "chebLanTr: no matrix set");
     cudaSetDevice(c->device);
     return drv_chebLanTr(c, a, b, pol, opts, cap, nev, lam, Y, res, stats);
+}
+
+int evsl_chebLanTr_batch(evsl_ctx *c, int njobs, evsl_slice_job *jobs, const evsl_lan_opts *opts)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (njobs < 1 || !jobs || !opts) return ctx_fail(c, EVSL_ERR_ARG, "chebLanTr_batch: bad arguments");
+    for (int j = 0; j < njobs; j++) {
+        const evsl_slice_job &J = jobs[j];
+        if (!J.pol || !J.pol->coef || !J.nev || !J.lam || !J.res || J.cap < 1 || !(J.b > J.a) || J.m < 2)
+            return ctx_fail(c, EVSL_ERR_ARG, "chebLanTr_batch: job %d has bad arguments", j);
+        if (J.pol->lmin != jobs[0].pol->lmin || J.pol->lmax != jobs[0].pol->lmax)
+            return ctx_fail(c, EVSL_ERR_ARG, "chebLanTr_batch: job %d uses another [lmin, lmax]", j);
+        jobs[j].status = EVSL_OK;
+        *J.nev = 0;
+    }
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "chebLanTr_batch: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_chebLanTr_batch(c, njobs, jobs, opts);
+}
+
+int evsl_batch_create(evsl_ctx *c, const evsl_lan_opts *opts, evsl_batch **batch)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!opts || !batch) return ctx_fail(c, EVSL_ERR_ARG, "batch_create: bad arguments");
+    *batch = nullptr;
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "batch_create: no matrix set");
+    cudaSetDevice(c->device);
+    return batch_create(c, opts, batch);
+}
+
+int evsl_batch_add(evsl_batch *batch, evsl_slice_job *J)
+{
+    if (!batch) return EVSL_ERR_ARG;
+    evsl_ctx *c = batch_ctx(batch);
+    c->err.clear();
+    if (!J || !J->pol || !J->pol->coef || !J->nev || !J->lam || !J->res || J->cap < 1 || !(J->b > J->a) || J->m < 2)
+        return ctx_fail(c, EVSL_ERR_ARG, "batch_add: bad job");
+    cudaSetDevice(c->device);
+    return batch_add(batch, J);
+}
+
+int evsl_batch_step(evsl_batch *batch, int *nactive, int *nfinished)
+{
+    if (!batch) return EVSL_ERR_ARG;
+    evsl_ctx *c = batch_ctx(batch);
+    c->err.clear();
+    cudaSetDevice(c->device);
+    return batch_step(batch, nactive, nfinished);
+}
+
+void evsl_batch_destroy(evsl_batch *batch)
+{
+    if (!batch) return;
+    cudaSetDevice(batch_ctx(batch)->device);
+    batch_destroy(batch);
 }
 
 int64_t evsl_launch_count(const evsl_ctx *c) { return c ? c->launches : 0; }

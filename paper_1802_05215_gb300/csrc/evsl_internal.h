@@ -80,6 +80,13 @@ int cheb_step_f64(evsl_ctx *c, int mode, int nvec, const double *x, const double
                   double *out, double *y, double cc, double sc, double c0, double cj);
 int cheb_step_f32(evsl_ctx *c, int mode, int nvec, const float *x, const float *xprev,
                   float *out, float *y, double cc, double sc, double c0, double cj);
+// Multi-filter form: column l uses coefficient ctab[l] (and c0tab[l] in mode 0), device tables
+int cheb_step_multi_f64(evsl_ctx *c, int mode, int nvec, const double *x, const double *xprev,
+                        double *out, double *y, double cc, double sc, const double *ctab,
+                        const double *c0tab);
+int cheb_step_multi_f32(evsl_ctx *c, int mode, int nvec, const float *x, const float *xprev,
+                        float *out, float *y, double cc, double sc, const float *ctab,
+                        const float *c0tab);
 // Y = A X (FP64), nvec columns
 int spmv_f64(evsl_ctx *c, int nvec, const double *X, double *Y);
 // KPM: fill W0 with the probes, then steps
@@ -152,13 +159,25 @@ int host_slicer(const double *mu, int degree, int64_t n, double lmin, double lma
 // number of eigenvalues < sigma of the arrow + tridiagonal matrix (Sylvester inertia)
 int host_count_below(int k, int l, const double *d, const double *e, double sigma);
 
-// ---- drivers (lanczos.cu)
+// ---- drivers (lanczos.cu, tr_lanczos.cu)
+int filter_apply_dev(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const double *X, double *Y,
+                     evsl_precision prec, double *B0, double *B1, float *fbuf);
+int filter_apply_multi_dev(evsl_ctx *c, int npol, const evsl_polfilt *pols, const double *X,
+                           double *Y, evsl_precision prec);
+int drv_chebLanTr_batch(evsl_ctx *c, int njobs, evsl_slice_job *jobs, const evsl_lan_opts *o);
+int batch_create(evsl_ctx *c, const evsl_lan_opts *o, evsl_batch **out);
+void batch_destroy(evsl_batch *bt);
+int batch_add(evsl_batch *bt, evsl_slice_job *job);
+int batch_step(evsl_batch *bt, int *nactive, int *nfinished);
+evsl_ctx *batch_ctx(evsl_batch *bt);
 int drv_bounds(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax);
 int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
                   const evsl_lan_opts *o, int cap, int *nev, double *lam, double *Y,
                   double *res, evsl_stats *st);
 int drv_filter_apply(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const double *X,
                      double *Y, evsl_precision prec);
+int drv_filter_apply_multi(evsl_ctx *c, int npol, const evsl_polfilt *pols, const double *X,
+                           double *Y, evsl_precision prec);
 int drv_kpm(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax,
             evsl_precision prec, double *mu);
 

@@ -71,6 +71,7 @@ __global__ void k_sell_fill(int64_t n, int64_t nslices, const int64_t *__restric
     }
 }
 
+// [cheb_step1 begin] -- source region fingerprinted by the profile summaries
 // Fused Chebyshev step.  MODE 0: out = sc (A x - cc x); y = c0 x + cj out.
 //                        MODE 1: out = sc (A x - cc x) - xprev; y += cj out.
 //                        MODE 2: out = A x.
@@ -113,13 +114,18 @@ k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
     if (r < n) cheb_epilogue<T, MODE>(r, acc, MODE == 2 ? T(0) : x[r], xprev, out, y, cc, sc, c0, cj);
 }
 
+// [cheb_step1 end]
+
 // Block of nvec columns (column-major, ld = n): the slice's nonzeros stay in registers and
 // the columns are processed NC at a time so that NC * w gathers are in flight per warp.
+// ctab/c0tab (optional, device): per-column coefficient of this degree and, in MODE 0, of
+// degree 0 -- the multi-slice form, where every column carries its own filter.
 template <typename T, int MODE, int NC>
 __global__ void __launch_bounds__(TPB)
 k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
              const int32_t *__restrict__ col, const T *__restrict__ val, int nvec,
-             const T *__restrict__ x, const T *xprev, T *out, T *y, T cc, T sc, T c0, T cj)
+             const T *__restrict__ x, const T *xprev, T *out, T *y, T cc, T sc, T c0, T cj,
+             const T *__restrict__ ctab, const T *__restrict__ c0tab)
 {
     int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (s >= nslices) return;
@@ -158,7 +164,8 @@ k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
 #pragma unroll
             for (int q = 0; q < NC; q++) {
                 int64_t o = (int64_t)(l0 + q) * n + r;
-                cheb_epilogue<T, MODE>(o, acc[q], MODE == 2 ? T(0) : x[o], xprev, out, y, cc, sc, c0, cj);
+                T cjq = ctab ? ctab[l0 + q] : cj, c0q = c0tab ? c0tab[l0 + q] : c0;
+                cheb_epilogue<T, MODE>(o, acc[q], MODE == 2 ? T(0) : x[o], xprev, out, y, cc, sc, c0q, cjq);
             }
         }
     }
@@ -174,7 +181,8 @@ k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
         }
         if (r < n) {
             int64_t o = (int64_t)l0 * n + r;
-            cheb_epilogue<T, MODE>(o, acc, MODE == 2 ? T(0) : xl[r], xprev, out, y, cc, sc, c0, cj);
+            T cjq = ctab ? ctab[l0] : cj, c0q = c0tab ? c0tab[l0] : c0;
+            cheb_epilogue<T, MODE>(o, acc, MODE == 2 ? T(0) : xl[r], xprev, out, y, cc, sc, c0q, cjq);
         }
     }
 }
@@ -388,32 +396,47 @@ void sell_free(evsl_ctx *c)
 
 template <typename T, int MODE>
 static void launch_cheb(evsl_ctx *c, unsigned grid, int nvec, const T *val, const T *x, const T *xprev,
-                        T *out, T *y, T cc, T sc, T c0, T cj)
+                        T *out, T *y, T cc, T sc, T c0, T cj, const T *ctab, const T *c0tab)
 {
     const DevMatrix &A = c->A;
     constexpr int NC = sizeof(T) == 8 ? 2 : 4;
-    if (nvec == 1)
+    if (nvec == 1 && !ctab)
         k_cheb_step1<T, MODE><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, x, xprev,
                                                           out, y, cc, sc, c0, cj);
     else
         k_cheb_stepN<T, MODE, NC><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec,
-                                                              x, xprev, out, y, cc, sc, c0, cj);
+                                                              x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
 }
 
 template <typename T>
 static int cheb_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xprev, T *out,
-                       T *y, double cc, double sc, double c0, double cj, const T *val)
+                       T *y, double cc, double sc, double c0, double cj, const T *val,
+                       const T *ctab = nullptr, const T *c0tab = nullptr)
 {
     unsigned grid = blocks_for(c->A.nslices * 32, TPB);
     T tcc = (T)cc, tsc = (T)sc, tc0 = (T)c0, tcj = (T)cj;
     if (mode == 0)
-        launch_cheb<T, 0>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj);
+        launch_cheb<T, 0>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj, ctab, c0tab);
     else if (mode == 1)
-        launch_cheb<T, 1>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj);
+        launch_cheb<T, 1>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj, ctab, c0tab);
     else
-        launch_cheb<T, 2>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj);
+        launch_cheb<T, 2>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj, ctab, c0tab);
     c->launches++;
     return check_launch(c, "cheb_step");
+}
+
+int cheb_step_multi_f64(evsl_ctx *c, int mode, int nvec, const double *x, const double *xprev,
+                        double *out, double *y, double cc, double sc, const double *ctab,
+                        const double *c0tab)
+{
+    return cheb_step_t<double>(c, mode, nvec, x, xprev, out, y, cc, sc, 0.0, 0.0, c->A.val, ctab, c0tab);
+}
+
+int cheb_step_multi_f32(evsl_ctx *c, int mode, int nvec, const float *x, const float *xprev,
+                        float *out, float *y, double cc, double sc, const float *ctab,
+                        const float *c0tab)
+{
+    return cheb_step_t<float>(c, mode, nvec, x, xprev, out, y, cc, sc, 0.0, 0.0, c->A.val32, ctab, c0tab);
 }
 
 int cheb_step_f64(evsl_ctx *c, int mode, int nvec, const double *x, const double *xprev,

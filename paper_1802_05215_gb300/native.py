@@ -44,6 +44,13 @@ class LanOpts(C.Structure):
                 ("right_closed", C.c_int)]
 
 
+class SliceJob(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("pol", C.POINTER(PolFilt)),
+                ("m", C.c_int), ("cap", C.c_int), ("right_closed", C.c_int),
+                ("nev", C.POINTER(C.c_int)), ("lam", C.c_void_p), ("res", C.c_void_p),
+                ("Y", C.c_void_p), ("stats", C.c_void_p), ("status", C.c_int)]
+
+
 class Stats(C.Structure):
     _fields_ = [("niter", C.c_int64), ("nmv", C.c_int64), ("nrestart", C.c_int64),
                 ("npass", C.c_int64), ("t_filter", C.c_double), ("t_orth", C.c_double),
@@ -82,7 +89,13 @@ def load(build_if_missing: bool = True):
         "evsl_slice_by_dos": (i32, [P, i32, i64, d, d, d, d, i32, i32, P, P]),
         "evsl_cheb_filter_build": (i32, [d, d, d, d, P, P, P, i32]),
         "evsl_filter_apply": (i32, [P, P, i32, P, P, i32]),
+        "evsl_filter_apply_multi": (i32, [P, i32, P, P, P, i32]),
         "evsl_chebLanTr": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
+        "evsl_chebLanTr_batch": (i32, [P, i32, P, P]),
+        "evsl_batch_create": (i32, [P, P, C.POINTER(P)]),
+        "evsl_batch_add": (i32, [P, P]),
+        "evsl_batch_step": (i32, [P, P, P]),
+        "evsl_batch_destroy": (None, [P]),
         "evsl_launch_count": (i64, [P]),
         "evsl_profile": (i32, [P, i32]),
         "evsl_profile_get": (i32, [P, i32, P, P]),
@@ -211,6 +224,12 @@ class Context:
         self._check(self.lib.evsl_filter_apply(self.h, C.byref(filt.pol), nvec, _addr(X),
                                                _addr(Y), prec), "filter_apply")
 
+    def filter_apply_multi(self, filters, X, Y, prec=FP64):
+        """Column t of the device block X (n x len(filters)) is filtered by filters[t]."""
+        arr = (PolFilt * len(filters))(*[f.pol for f in filters])
+        self._check(self.lib.evsl_filter_apply_multi(self.h, len(filters), arr, _addr(X), _addr(Y),
+                                                     prec), "filter_apply_multi")
+
     def chebLanTr(self, a, b, filt: Filter, m=100, maxit=0, ncycle=10, tol=1e-8, tau1=1e-10,
                   seed=0, prec=FP64, right_closed=True, cap=None, Y=None, allow_partial=False):
         """Filtered thick-restart Lanczos on [a, b].  Y: None (host numpy result) or a
@@ -232,6 +251,34 @@ class Context:
         return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
                     stats=stats.as_dict())
 
+    def chebLanTr_batch(self, slices, filters, ms, caps=None, maxit=0, ncycle=10, tol=1e-8,
+                        tau1=1e-10, seed=0, prec=FP64, right_closed=None, Ys=None,
+                        allow_partial=False):
+        """Several slices [a_j, b_j] of the current matrix solved in lockstep with batched
+        filters.  Returns one result dict per slice (as chebLanTr)."""
+        nj = len(slices)
+        caps = caps or [m + 64 for m in ms]
+        right_closed = right_closed if right_closed is not None else [True] * nj
+        opts = LanOpts(0, maxit, ncycle, tol, tau1, seed, prec, 1)
+        keep, jobs = [], (SliceJob * nj)()
+        for j, ((a, b), f, m, cap) in enumerate(zip(slices, filters, ms, caps)):
+            nev = C.c_int()
+            lam, res = np.zeros(cap), np.zeros(cap)
+            Y = Ys[j] if Ys is not None else np.zeros((cap, self.n))
+            st = Stats()
+            keep.append((nev, lam, res, Y, st))
+            jobs[j] = SliceJob(a, b, C.pointer(f.pol), m, cap, int(right_closed[j]), C.pointer(nev),
+                               _ptr(lam), _ptr(res), _ptr(Y), C.addressof(st), 0)
+        rc = self.lib.evsl_chebLanTr_batch(self.h, nj, jobs, C.byref(opts))
+        if rc != EVSL_OK and not (allow_partial and rc in (-4, -5)):
+            self._check(rc, "chebLanTr_batch")
+        out = []
+        for j, (nev, lam, res, Y, st) in enumerate(keep):
+            k = nev.value
+            out.append(dict(status=jobs[j].status, nev=k, lam=lam[:k].copy(), res=res[:k].copy(),
+                            Y=Y, stats=st.as_dict()))
+        return out
+
     def launch_count(self) -> int:
         return int(self.lib.evsl_launch_count(self.h))
 
@@ -244,3 +291,76 @@ class Context:
         self._check(self.lib.evsl_profile_get(self.h, kernel, C.byref(n), C.byref(ms)),
                     "profile_get")
         return n.value, ms.value
+
+
+class Job:
+    """One slice solve submitted to a Batch; holds the buffers the library writes into."""
+
+    def __init__(self, a, b, filt: Filter, m, cap, right_closed, n, Y=None, tag=None):
+        self.filt = filt
+        self.nev_c = C.c_int()
+        self.lam = np.zeros(cap)
+        self.res = np.zeros(cap)
+        self.Y = Y if Y is not None else np.zeros((cap, n))
+        self.stats_c = Stats()
+        self.tag = tag
+        self.struct = SliceJob(a, b, C.pointer(filt.pol), m, cap, int(right_closed),
+                               C.pointer(self.nev_c), _ptr(self.lam), _ptr(self.res), _ptr(self.Y),
+                               C.addressof(self.stats_c), 0)
+        self.done = False
+
+    def result(self):
+        k = self.nev_c.value
+        return dict(status=self.struct.status, nev=k, lam=self.lam[:k].copy(),
+                    res=self.res[:k].copy(), Y=self.Y, stats=self.stats_c.as_dict(), tag=self.tag)
+
+
+class Batch:
+    """Continuous batching of slice solves on one context (evsl_batch_*): jobs join between
+    steps and leave when finished; each step applies every active job's filter in one pass."""
+
+    def __init__(self, ctx: Context, maxit=0, ncycle=10, tol=1e-8, tau1=1e-10, seed=0, prec=FP64):
+        self.ctx = ctx
+        self.opts = LanOpts(0, maxit, ncycle, tol, tau1, seed, prec, 1)
+        h = C.c_void_p()
+        ctx._check(ctx.lib.evsl_batch_create(ctx.h, C.byref(self.opts), C.byref(h)), "batch_create")
+        self.h = h
+        self.active: list[Job] = []
+
+    def add(self, a, b, filt: Filter, m, cap=None, right_closed=True, Y=None, tag=None) -> Job:
+        """Admit a job; raises EvslError with code -2 when the HBM budget has no room for it."""
+        job = Job(a, b, filt, m, cap or (m + 64), right_closed, self.ctx.n, Y, tag)
+        self.ctx._check(self.ctx.lib.evsl_batch_add(self.h, C.byref(job.struct)), "batch_add")
+        self.active.append(job)
+        return job
+
+    def step(self):
+        """One lockstep Lanczos step; returns the jobs that finished in it."""
+        na, nf = C.c_int(), C.c_int()
+        self.ctx._check(self.ctx.lib.evsl_batch_step(self.h, C.byref(na), C.byref(nf)), "batch_step")
+        done = []
+        if nf.value:
+            # a finished job has its status and outputs written; the library drops it from the batch
+            still = []
+            for j in self.active:
+                (done if self._finished(j) else still).append(j)
+            self.active = still
+        return done
+
+    def _finished(self, job):
+        # outputs are written once; a finished job has its stats filled in (t_total > 0)
+        if job.stats_c.t_total > 0 and not job.done:
+            job.done = True
+            return True
+        return False
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.evsl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

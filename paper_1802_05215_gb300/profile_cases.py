@@ -1,0 +1,74 @@
+"""Small fixed workloads for profiling single kernels with ncu (a few launches, < 1 GB).
+
+    python -m paper_1802_05215_gb300.profile_cases cheb      # filter step: FP64 then FP32
+    python -m paper_1802_05215_gb300.profile_cases gemv      # Gram-Schmidt GEMV-T / GEMV-N
+    python -m paper_1802_05215_gb300.profile_cases kpm       # KPM moment step, FP64 then FP32
+    python -m paper_1802_05215_gb300.profile_cases multi     # 16-slice batched filter step, FP32
+
+Each case runs on the 100^3 7-point Laplacian (n = 1e6, nnz = 6.94e6) and prints the number of
+kernels the library launched.
+"""
+from __future__ import annotations
+
+import sys
+
+
+def _ctx():
+    from . import inputs, native
+    A = inputs.laplacian_3d(100)
+    ctx = native.Context(0)
+    ctx.set_csr(A)
+    return native, A, ctx
+
+
+def cheb():
+    """Six-degree filter on one vector: 6 launches of the fused step in FP64, then 6 in FP32."""
+    import torch
+    native, A, ctx = _ctx()
+    f = native.cheb_filter_build(0.40, 0.428, 0.0, 12.0)
+    f.pol.deg = 6
+    X = torch.randn(1, A.n, dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    ctx.filter_apply(f, X, Y, prec=native.FP64)
+    ctx.filter_apply(f, X, Y, prec=native.FP32)
+    torch.cuda.synchronize()
+    return ctx
+
+
+def gemv():
+    """400 bounds-Lanczos steps: the last projections run against ~400 basis columns (3.2 GB)."""
+    native, A, ctx = _ctx()
+    ctx.bounds(400, 0)
+    return ctx
+
+
+def kpm():
+    """KPM degree 4 with 40 probes, FP64 then FP32."""
+    native, A, ctx = _ctx()
+    ctx.kpm_dos(4, 40, 0, 0.0, 12.0, prec=native.FP64)
+    ctx.kpm_dos(4, 40, 0, 0.0, 12.0, prec=native.FP32)
+    return ctx
+
+
+def multi():
+    """16 slice filters of [0.2, 0.6] batched (one block launch per degree), FP32."""
+    import numpy as np
+    import torch
+    native, A, ctx = _ctx()
+    cuts = np.linspace(0.2, 0.6, 17)
+    fs = [native.cheb_filter_build(cuts[i], cuts[i + 1], 0.0, 12.0) for i in range(16)]
+    for f in fs:
+        f.pol.deg = min(f.pol.deg, 6)
+    X = torch.randn(16, A.n, dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    ctx.filter_apply_multi(fs, X, Y, prec=native.FP32)
+    torch.cuda.synchronize()
+    return ctx
+
+
+CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi}
+
+if __name__ == "__main__":
+    name = sys.argv[1] if len(sys.argv) > 1 else "cheb"
+    ctx = CASES[name]()
+    print(f"{name}: ok, launches={ctx.launch_count()}")

@@ -267,3 +267,144 @@ def test_launch_counter_and_profile(ctx, nat):
     ctx.profile(False)
     assert launches == 30 and ms > 0
     assert ctx.launch_count() - n0 >= 31
+
+
+# ------------------------------------------------------------------------------ multi-slice filter
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-5)])
+def test_filter_apply_multi_matches_oracle(ctx, nat, oracle_mod, prec, tol):
+    # one column per slice, each with its own degree and coefficients, one launch per degree
+    import torch
+    A = I.anderson_3d(15, 4.0, 3)              # n = 3375: ragged last slice
+    ctx.set_csr(A)
+    lo, hi = oracle_mod.bounds(A, 60, 0)
+    cuts = [-1.0, 0.5, 1.4, 2.0, 2.3, 3.5]
+    filters = [nat.cheb_filter_build(cuts[i], cuts[i + 1], lo, hi) for i in range(5)]
+    degs = [f.deg for f in filters]
+    assert len(set(degs)) > 2
+    X = np.random.default_rng(2).standard_normal((5, A.n))
+    Xd = torch.tensor(X, device="cuda")
+    Yd = torch.empty_like(Xd)
+    ctx.filter_apply_multi(filters, Xd, Yd, prec=prec)
+    Y = Yd.cpu().numpy()
+    for t, f in enumerate(filters):
+        Yo = oracle_mod.filter_apply(A, lo, hi, f.coef, X[t].copy())[:, 0]
+        scale = np.abs(f.coef).sum() * np.abs(X[t]).max()
+        assert np.max(np.abs(Y[t] - Yo)) <= tol * scale, (t, degs[t])
+
+
+def test_filter_apply_multi_single_and_degree_zero(ctx, nat, oracle_mod):
+    import torch
+    A = I.laplacian_2d(40)
+    ctx.set_csr(A)
+    f1 = nat.cheb_filter_build(1.0, 1.2, 0.0, 8.0)
+    f0 = nat.cheb_filter_build(2.0, 2.5, 0.0, 8.0)
+    f0.coef = np.array([0.3])
+    f0.pol.deg = 0
+    f0.pol.coef = f0.coef.ctypes.data_as(nat.C.POINTER(nat.C.c_double))
+    X = np.random.default_rng(4).standard_normal((2, A.n))
+    Xd = torch.tensor(X, device="cuda")
+    Yd = torch.empty_like(Xd)
+    ctx.filter_apply_multi([f0, f1], Xd, Yd)
+    Y = Yd.cpu().numpy()
+    assert np.max(np.abs(Y[0] - 0.3 * X[0])) <= 1e-15
+    Yref = torch.empty_like(Xd[1:2])
+    ctx.filter_apply(f1, Xd[1:2].contiguous(), Yref)
+    assert np.max(np.abs(Y[1] - Yref.cpu().numpy()[0])) <= 1e-12 * np.abs(f1.coef).sum() * np.abs(X[1]).max()
+
+
+# ------------------------------------------------------------------------------ multi-slice Lanczos
+def test_cheblantr_batch_equals_per_slice_runs(ctx, nat, oracle_mod):
+    # the lockstep multi-slice driver performs, per slice, the same operations in the same order
+    # as the single-slice one (the block filter kernel does each column's arithmetic exactly like
+    # the one-vector kernel), so results agree bitwise
+    A = I.laplacian_3d(14)
+    e = lap_eigs(3, 14)
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(80, 0)
+    cuts = [0.0, 0.9, 1.35, 1.7]
+    slices = [(cuts[i], cuts[i + 1]) for i in range(3)]
+    filters = [nat.cheb_filter_build(a, b, lo, hi) for a, b in slices]
+    counts = [int(np.count_nonzero((e >= a) & (e < b))) for a, b in slices]
+    ms = [max(2 * c + 40, 100) for c in counts]
+    rc = [False, False, True]
+    batch = ctx.chebLanTr_batch(slices, filters, ms, right_closed=rc)
+    for j, ((a, b), f, m) in enumerate(zip(slices, filters, ms)):
+        single = ctx.chebLanTr(a, b, f, m=m, right_closed=rc[j])
+        assert batch[j]["status"] == 0
+        assert batch[j]["nev"] == single["nev"] == counts[j] + (j == 2) * int(np.count_nonzero(e == cuts[3]))
+        assert np.array_equal(batch[j]["lam"], single["lam"])
+        k = single["nev"]
+        assert np.array_equal(batch[j]["Y"][:k], single["Y"][:k])
+        assert batch[j]["stats"]["niter"] == single["stats"]["niter"]
+
+
+def test_cheblantr_batch_fp32_filter_anderson(ctx, nat, oracle_mod):
+    # FP32 filter vectors, FP64 reorthogonalisation and Ritz step: the eigenpairs still meet the
+    # FP64 tolerances (exact count vs dense eigensolve, residual <= 1e-8 ||A||)
+    A = I.anderson_3d(8, 4.0, 0)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(80, 0)
+    cuts = [-1.0, 0.0, 1.0]
+    slices = [(cuts[0], cuts[1]), (cuts[1], cuts[2])]
+    filters = [nat.cheb_filter_build(a, b, lo, hi) for a, b in slices]
+    counts = [int(np.count_nonzero((ev >= a) & (ev < b))) for a, b in slices]
+    ms = [max(2 * c + 40, 100) for c in counts]
+    out = ctx.chebLanTr_batch(slices, filters, ms, prec=nat.FP32, right_closed=[False, True])
+    for j, (a, b) in enumerate(slices):
+        ex = ev[(ev >= a) & ((ev < b) if j == 0 else (ev <= b))]
+        assert out[j]["nev"] == len(ex)
+        assert np.all(np.abs(out[j]["lam"] - ex) <= 1e-9 * np.maximum(1, np.abs(ex)))
+        Y = out[j]["Y"][:len(ex)].T
+        assert np.max(_dense_residuals(A, out[j]["lam"], Y)) <= 1e-8
+
+
+# ------------------------------------------------------------------------------ continuous batching
+def test_batch_continuous_admission_same_results_alone_and_in_mix(ctx, nat):
+    # jobs join a running batch at different steps and leave when done; each result equals the
+    # job solved alone (bitwise: per-column arithmetic does not depend on the batch)
+    A = I.laplacian_2d(40)
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(80, 0)
+    e = lap_eigs(2, 40)
+    slices = [(0.5, 0.8), (1.1, 1.3), (2.0, 2.2), (3.0, 3.1)]
+    filters = [nat.cheb_filter_build(a, b, lo, hi) for a, b in slices]
+    ms = [max(2 * int(np.count_nonzero((e >= a) & (e <= b))) + 40, 100) for a, b in slices]
+    alone = [ctx.chebLanTr(a, b, f, m=m) for (a, b), f, m in zip(slices, filters, ms)]
+    bt = nat.Batch(ctx)
+    jobs, results, step = {}, {}, 0
+    arrive = {0: [0, 1], 7: [2], 30: [3]}        # job index -> step at which it is admitted
+    while len(results) < len(slices):
+        for j in arrive.get(step, []):
+            jobs[j] = bt.add(slices[j][0], slices[j][1], filters[j], ms[j], tag=j)
+        for job in bt.step():
+            results[job.tag] = job.result()
+        step += 1
+        assert step < 100000
+    bt.close()
+    for j in range(len(slices)):
+        r, s = results[j], alone[j]
+        assert r["status"] == 0 and r["nev"] == s["nev"] > 0
+        assert np.array_equal(r["lam"], s["lam"])
+        assert np.array_equal(r["Y"][:r["nev"]], s["Y"][:s["nev"]])
+
+
+def test_batch_admission_respects_hbm_budget(nat):
+    A = I.laplacian_2d(60)
+    n = A.n
+    per_job = 8 * n * (64 + 100 + 1 + 64)        # U (cap) + Q (m+1) + scalars, roughly
+    with nat.Context(0, hbm_budget=int(2.5 * per_job) + 64 * 1024 * 1024) as c:
+        c.set_csr(A)
+        lo, hi = 0.0, 8.0
+        f = nat.cheb_filter_build(1.0, 1.1, lo, hi)
+        bt = nat.Batch(c)
+        admitted, refused = 0, 0
+        for _ in range(6):
+            try:
+                bt.add(1.0, 1.1, f, 100, cap=64)
+                admitted += 1
+            except nat.EvslError as err:
+                assert err.code == -2
+                refused += 1
+        assert admitted >= 1 and refused >= 1
+        bt.close()
