@@ -140,6 +140,27 @@ int evsl_filter_apply(evsl_ctx *ctx, const evsl_polfilt *pol, int nvec, const do
 int evsl_filter_apply_multi(evsl_ctx *ctx, int npol, const evsl_polfilt *pols, const double *X,
                             double *Y, evsl_precision prec);
 
+/* Allocation-free form of evsl_filter_apply (the paper has no counterpart).  For callers that
+ * must not allocate device memory once set up: code recording into a CUDA stream capture
+ * (cudaMalloc is not allowed while a capture is in progress), real-time or embedded loops
+ * that forbid allocation after initialisation, and hosts whose device memory is owned by
+ * another allocator.  Same operation, arguments and layout as evsl_filter_apply with
+ * prec = EVSL_FP64: Y = rho(Ahat) X on nvec columns, X and Y device pointers (n x nvec,
+ * column-major, non-overlapping), matrix from the context.  The two recurrence temporaries
+ * live in one fixed device array of 2 * EVSL_NOALLOC_MAX_ELEMS doubles (32 MiB) that this
+ * library reserves on every GPU where its kernels are loaded, until the process exits; this
+ * call allocates nothing (no cudaMalloc/cudaFree, no workspace growth, no event creation).
+ * Its first call on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Every call shares the array: calls that
+ * can overlap on the GPU (several contexts or threads on one device) race and must be
+ * serialised by the caller.  The array keeps the previous call's contents; nothing in it has
+ * to start at zero, because each temporary entry is written before it is read.  The call is
+ * synchronous.  Errors: EVSL_ERR_ARG if n * nvec > EVSL_NOALLOC_MAX_ELEMS (the message names
+ * the limit), EVSL_ERR_STATE without a matrix, EVSL_ERR_CUDA if the address lookup fails. */
+#define EVSL_NOALLOC_MAX_ELEMS (1 << 21)
+int evsl_filter_apply_noalloc(evsl_ctx *ctx, const evsl_polfilt *pol, int nvec, const double *X,
+                              double *Y);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Filtered thick-restart Lanczos with locking (Sec. 2.5, Algorithm 2; ChebLanTr) on the slice
  * [a, b] with filter pol (built for the same slice).  Candidates are the Ritz values of

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "evsl_internal.h"
 
@@ -530,4 +531,67 @@ int fill_uniform_f64(evsl_ctx *c, int64_t n, uint64_t seed, int stream, uint64_t
     k_fill_uniform<<<blocks_for(n, 256), 256, 0, c->stream>>>(n, sm_key(seed, (uint64_t)stream), index, x);
     c->launches++;
     return check_launch(c, "fill_uniform");
+}
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free filter application.  The recurrence temporaries live in one fixed device
+// array shared by all calls on a device; its device address is looked up once per device.
+namespace {
+
+__device__ __align__(256) double g_noalloc_scratch[2 * (size_t)EVSL_NOALLOC_MAX_ELEMS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+extern "C" int evsl_filter_apply_noalloc(evsl_ctx *c, const evsl_polfilt *pol, int nvec,
+                                         const double *X, double *Y)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!pol || !pol->coef || pol->deg < 0 || nvec < 1 || !X || !Y)
+        return ctx_fail(c, EVSL_ERR_ARG, "filter_apply_noalloc: bad arguments");
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "filter_apply_noalloc: no matrix set");
+    const int64_t N = c->A.n * (int64_t)nvec;
+    if (N > (int64_t)EVSL_NOALLOC_MAX_ELEMS)
+        return ctx_fail(c, EVSL_ERR_ARG,
+                        "filter_apply_noalloc: n * nvec = %lld exceeds EVSL_NOALLOC_MAX_ELEMS = %d",
+                        (long long)N, EVSL_NOALLOC_MAX_ELEMS);
+    if (c->device < 0 || c->device >= NOALLOC_MAX_DEVICES)
+        return ctx_fail(c, EVSL_ERR_ARG, "filter_apply_noalloc: device ordinal %d not supported", c->device);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "filter_apply_noalloc set device");
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[c->device]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) return ctx_cuda(c, e, "filter_apply_noalloc symbol address");
+            g_noalloc_ptr[c->device] = (double *)p;
+        }
+        scratch = g_noalloc_ptr[c->device];
+    }
+    double *B0 = scratch, *B1 = scratch + EVSL_NOALLOC_MAX_ELEMS;
+    const double cc = 0.5 * (pol->lmax + pol->lmin), d = 0.5 * (pol->lmax - pol->lmin);
+    const double *coef = pol->coef;
+    int st;
+    if (pol->deg == 0) {
+        st = scale_vec(c, N, const_cast<double *>(X), coef[0], Y);
+    } else {
+        st = cheb_step_f64(c, 0, nvec, X, nullptr, B0, Y, cc, 1.0 / d, coef[0], coef[1]);
+        const double *prev = X;
+        double *cur = B0;
+        for (int j = 2; j <= pol->deg && st == EVSL_OK; j++) {
+            double *out = (j == 2) ? B1 : const_cast<double *>(prev);
+            st = cheb_step_f64(c, 1, nvec, cur, prev, out, Y, cc, 2.0 / d, 0.0, coef[j]);
+            prev = cur;
+            cur = out;
+        }
+    }
+    if (st != EVSL_OK) return st;
+    e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, "filter_apply_noalloc");
 }

@@ -19,6 +19,7 @@ ERRORS = {-1: "EVSL_ERR_ARG", -2: "EVSL_ERR_NOMEM", -3: "EVSL_ERR_CUDA", -4: "EV
 DAMP_NONE, DAMP_JACKSON, DAMP_SIGMA = 0, 1, 2
 FP64, FP32 = 0, 1
 K_CHEB_STEP, K_KPM_STEP, K_REORTH, K_RITZ_GEMM, K_SMALL_EIG = range(5)
+NOALLOC_MAX_ELEMS = 1 << 21
 
 
 class EvslError(RuntimeError):
@@ -89,6 +90,7 @@ def load(build_if_missing: bool = True):
         "evsl_slice_by_dos": (i32, [P, i32, i64, d, d, d, d, i32, i32, P, P]),
         "evsl_cheb_filter_build": (i32, [d, d, d, d, P, P, P, i32]),
         "evsl_filter_apply": (i32, [P, P, i32, P, P, i32]),
+        "evsl_filter_apply_noalloc": (i32, [P, P, i32, P, P]),
         "evsl_filter_apply_multi": (i32, [P, i32, P, P, P, i32]),
         "evsl_chebLanTr": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_chebLanTr_batch": (i32, [P, i32, P, P]),
@@ -229,6 +231,13 @@ class Context:
         arr = (PolFilt * len(filters))(*[f.pol for f in filters])
         self._check(self.lib.evsl_filter_apply_multi(self.h, len(filters), arr, _addr(X), _addr(Y),
                                                      prec), "filter_apply_multi")
+
+    def filter_apply_noalloc(self, filt: Filter, X, Y):
+        """Allocation-free Y = rho(Ahat) X (FP64) using the library's fixed device scratch;
+        n * nvec must not exceed NOALLOC_MAX_ELEMS."""
+        nvec = X.numel() // self.n
+        self._check(self.lib.evsl_filter_apply_noalloc(self.h, C.byref(filt.pol), nvec, _addr(X),
+                                                       _addr(Y)), "filter_apply_noalloc")
 
     def chebLanTr(self, a, b, filt: Filter, m=100, maxit=0, ncycle=10, tol=1e-8, tau1=1e-10,
                   seed=0, prec=FP64, right_closed=True, cap=None, Y=None, allow_partial=False):
