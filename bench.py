@@ -449,9 +449,122 @@ def run_serving(args):
     return line
 
 
+def run_anderson_batched(args):
+    """Anderson 80^3 (W = 4, seed 0), [-1, 1] in 16 DOS slices: the same slices solved by
+    lockstep-batched FP32-filter Lanczos (one multi-slice filter pass per degree) and by plain
+    FP64 per-slice Lanczos, one after the other on the same GPU."""
+    import torch
+
+    from paper_1802_05215_gb300 import native
+    A = inputs.workload("anderson3d_80")["matrix"]()
+    n = A.n
+    with native.Context(0) as ctx:
+        ctx.set_csr(A)
+        lo, hi = ctx.bounds(BOUNDS_STEPS, SEED)
+        mu = ctx.kpm_dos(KPM_DEG, KPM_NVEC, SEED, lo, hi)
+        sli, est = native.slice_by_dos(mu, n, lo, hi, -1.0, 1.0, 16)
+        pick = list(range(16)) if args.slices <= 0 else list(range(min(16, args.slices)))
+        slices = [(float(sli[i]), float(sli[i + 1])) for i in pick]
+        filters = [native.cheb_filter_build(a, b, lo, hi) for a, b in slices]
+        ms = [lanczos_m(est[i]) for i in pick]
+        caps = [int(1.3 * est[i] + 50) for i in pick]
+        rc = [i == 15 for i in pick]
+        Ys = [torch.empty(c * n, dtype=torch.float64, device="cuda") for c in caps]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch = ctx.chebLanTr_batch(slices, filters, ms, caps=caps, prec=native.FP32, right_closed=rc,
+                                    Ys=Ys, tol=TOL)
+        t_batch = time.perf_counter() - t0
+        plain, t_plain = [], 0.0
+        for j, ((a, b), f, m, cap) in enumerate(zip(slices, filters, ms, caps)):
+            t0 = time.perf_counter()
+            plain.append(ctx.chebLanTr(a, b, f, m=m, cap=cap, tol=TOL, right_closed=rc[j], Y=Ys[j]))
+            t_plain += time.perf_counter() - t0
+    nb = sum(r["nev"] for r in batch)
+    npl = sum(r["nev"] for r in plain)
+    line = {"metric": "eigenpairs/s at resid<=1e-8, batched FP32-filter vs plain FP64",
+            "value": nb / t_batch, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32 filter, f64 reorth/Ritz", "data": "synthetic",
+            "config": {"workload": "Anderson 80^3 W=4 seed 0, [-1,1] in 16 KPM-DOS slices",
+                       "slices_run": pick},
+            "batched_fp32": {"eigenpairs": nb, "seconds": t_batch,
+                             "max_res": max(float(r["res"].max()) for r in batch if r["nev"])},
+            "plain_fp64": {"eigenpairs": npl, "seconds": t_plain, "eigenpairs_per_s": npl / t_plain,
+                           "max_res": max(float(r["res"].max()) for r in plain if r["nev"])},
+            "counts_batched": [r["nev"] for r in batch], "counts_plain": [r["nev"] for r in plain],
+            "dos_estimates": [float(est[i]) for i in pick],
+            "degrees": [f.deg for f in filters],
+            "speedup": (nb / t_batch) / (npl / t_plain)}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_kpm_200(args):
+    """KPM density of the Anderson 200^3 model (W = 2, n = 8e6, nnz = 5.576e7): degree 300 with
+    64 Rademacher probes in one block, FP64 and FP32; the FP64 moments of the first probe are
+    checked against the oracle, the FP32 ones against FP64, and the DOS L1 error is reported."""
+    from paper_1802_05215_gb300 import native
+    A = inputs.workload("anderson3d_200")["matrix"]()
+    M, nv = 300, 64
+    out = {}
+    with native.Context(0) as ctx:
+        ctx.set_csr(A)
+        lo, hi = ctx.bounds(BOUNDS_STEPS, SEED)
+        for prec, name in [(native.FP64, "fp64"), (native.FP32, "fp32")]:
+            ctx.kpm_dos(M, nv, SEED, lo, hi, prec=prec)                  # warm-up
+            ctx.profile(True)
+            t0 = time.perf_counter()
+            mu = ctx.kpm_dos(M, nv, SEED, lo, hi, prec=prec)
+            wall = time.perf_counter() - t0
+            nl, ms = ctx.profile_get(native.K_KPM_STEP)
+            ctx.profile(False)
+            b = 8 if prec == native.FP64 else 4
+            alg = A.nnz * (b + 4) + 8 * (A.n + 1) + 3 * nv * A.n * b + A.n * nv / 8
+            per = ms / nl * 1e-3
+            out[name] = {"mu": mu, "seconds": wall, "step_us": per * 1e6, "GBs": alg / per / 1e9,
+                         "frac_of_hbm": alg / per / 1e9 / peaks()[0]}
+        mu1 = ctx.kpm_dos(M, 1, SEED, lo, hi, prec=native.FP64)
+    err32 = float(np.max(np.abs(out["fp32"]["mu"] - out["fp64"]["mu"])) / A.n)
+    check = {}
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        mo1 = oracle.kpm_moments(A, M, 1, SEED, lo, hi)
+        check = {"oracle_probe0_max_rel_err": float(np.max(np.abs(mu1 - mo1)) / A.n),
+                 "oracle_seconds": time.perf_counter() - t0}
+    # DOS L1 error of the FP32 density against the FP64 one, on 4001 points
+    ts = np.linspace(lo, hi, 4001)
+    c, d = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    th = np.arccos(np.clip((ts - c) / d, -1, 1))
+    a = np.pi / (M + 2)
+    k = np.arange(M + 1)
+    g = ((M - k + 2) * np.cos(k * a) + np.sin(k * a) / np.tan(a)) / (M + 2)
+
+    def density(mu):
+        s = g[0] * mu[0] + 2 * np.sum((g[1:] * mu[1:])[:, None] * np.cos(k[1:, None] * th[None, :]), axis=0)
+        return s / (np.pi * np.sqrt(np.maximum(1e-300, 1 - ((ts - c) / d) ** 2)) * d * A.n)
+
+    f64, f32 = density(out["fp64"]["mu"]), density(out["fp32"]["mu"])
+    inner = slice(1, -1)
+    trap = getattr(np, "trapezoid", None) or np.trapz
+    l1 = float(trap(np.abs(f32 - f64)[inner], ts[inner]))
+    line = {"metric": "KPM moments, Anderson 200^3 (n=8e6), degree 300, 64 probes",
+            "value": out["fp32"]["GBs"], "unit": "GB/s (FP32 KPM step)", "n_gpus": 1,
+            "dtype": "f32 and f64", "data": "synthetic",
+            "fp64": {k2: v for k2, v in out["fp64"].items() if k2 != "mu"},
+            "fp32": {k2: v for k2, v in out["fp32"].items() if k2 != "mu"},
+            "fp32_vs_fp64_max_moment_err_rel_n": err32, "dos_l1_fp32_vs_fp64": l1, **check}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["lap3d_100", "serving"], default="lap3d_100")
+    ap.add_argument("--workload", choices=["lap3d_100", "serving", "anderson3d_80", "kpm_200"],
+                    default="lap3d_100")
+    ap.add_argument("--slices", type=int, default=4,
+                    help="anderson3d_80: how many of the 16 slices to solve (<= 0: all)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
@@ -462,6 +575,10 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.workload == "serving":
         run_serving(args)
+    elif args.workload == "anderson3d_80":
+        run_anderson_batched(args)
+    elif args.workload == "kpm_200":
+        run_kpm_200(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -51,6 +51,8 @@ typedef enum { EVSL_FP64 = 0, EVSL_FP32 = 1 } evsl_precision;
  * device: CUDA ordinal.  hbm_budget_bytes: cap on the device memory the context may hold
  * (0 = no cap); allocations beyond it fail with EVSL_ERR_NOMEM.  *ctx is set to NULL on error. */
 int evsl_create(evsl_ctx **ctx, int device, size_t hbm_budget_bytes);
+/* Frees everything the context holds, including batches created on it that were not destroyed
+ * (their unfinished jobs are discarded; the batch handles become invalid). */
 void evsl_destroy(evsl_ctx *ctx);
 /* Message of the last failed call on ctx (empty string if none); valid until the next call. */
 const char *evsl_last_error(const evsl_ctx *ctx);

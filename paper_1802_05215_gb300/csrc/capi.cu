@@ -163,6 +163,7 @@ void evsl_destroy(evsl_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    while (!c->batches.empty()) batch_destroy(c->batches.back());  // unfinished jobs are discarded
     cudaStreamSynchronize(c->stream);
     prof_resolve(c);
     sell_free(c);

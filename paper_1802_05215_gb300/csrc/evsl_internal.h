@@ -25,6 +25,12 @@ struct DevMatrix {
     int32_t *col = nullptr;      // nstored
     double *val = nullptr;       // nstored
     float *val32 = nullptr;      // nstored
+    int32_t *rlen = nullptr;     // n: stored (non-padding) entries of each row
+    bool has_diag = false;       // every row stores its diagonal entry
+    // mapped copy (2/d)(A - c I) of the values for the filter recurrence, for one (c, d)
+    double *vhat = nullptr;
+    float *vhat32 = nullptr;
+    double hat_c = 0.0, hat_d = 0.0;
 };
 
 struct ProfGroup {
@@ -51,12 +57,14 @@ struct evsl_ctx {
     int64_t prof_launches[EVSL_K_COUNT] = {0};
     double prof_ms[EVSL_K_COUNT] = {0};
     int dev_sm_count = 0;
+    std::vector<evsl_batch *> batches;  // live batches, destroyed with the context
 };
 
 enum WsSlot {
     WS_PARTIAL = 0, WS_SCAL, WS_W0, WS_W1, WS_W2, WS_KPM_PART, WS_F32_X, WS_F32_Y,
     WS_LAN_U, WS_LAN_Q, WS_LAN_Y, WS_LAN_Z, WS_LAN_VEC, WS_LAN_T, WS_LAN_S, WS_LAN_IDX,
-    WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_COUNT
+    WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_POL_V, WS_POL_W, WS_POL_B, WS_POL_S, WS_POL_Y, WS_POL_R,
+    WS_COUNT
 };
 
 // ---- context helpers (capi.cu)
@@ -76,17 +84,22 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *c
 void sell_free(evsl_ctx *c);
 // One fused Chebyshev step on nvec columns (ld = n).  mode 0: out = sc (A x - cc x),
 // y = c0 x + cj out.  mode 1: out = sc (A x - cc x) - xprev, y += cj out.  out may alias xprev.
+// hat = true uses the mapped values made current by ensure_mapped(c, cc, d) (same result up to
+// rounding, two FP64 operations fewer per row).
 int cheb_step_f64(evsl_ctx *c, int mode, int nvec, const double *x, const double *xprev,
-                  double *out, double *y, double cc, double sc, double c0, double cj);
+                  double *out, double *y, double cc, double sc, double c0, double cj, bool hat);
 int cheb_step_f32(evsl_ctx *c, int mode, int nvec, const float *x, const float *xprev,
-                  float *out, float *y, double cc, double sc, double c0, double cj);
+                  float *out, float *y, double cc, double sc, double c0, double cj, bool hat);
 // Multi-filter form: column l uses coefficient ctab[l] (and c0tab[l] in mode 0), device tables
 int cheb_step_multi_f64(evsl_ctx *c, int mode, int nvec, const double *x, const double *xprev,
                         double *out, double *y, double cc, double sc, const double *ctab,
-                        const double *c0tab);
+                        const double *c0tab, bool hat);
 int cheb_step_multi_f32(evsl_ctx *c, int mode, int nvec, const float *x, const float *xprev,
                         float *out, float *y, double cc, double sc, const float *ctab,
-                        const float *c0tab);
+                        const float *c0tab, bool hat);
+// Make the mapped values (2/d)(A - cc I) current; returns false when the matrix lacks stored
+// diagonal entries (the unscaled kernels are used then).
+bool ensure_mapped(evsl_ctx *c, double cc, double d, int *status);
 // Y = A X (FP64), nvec columns
 int spmv_f64(evsl_ctx *c, int nvec, const double *X, double *Y);
 // KPM: fill W0 with the probes, then steps
@@ -96,10 +109,10 @@ int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0);
 // index k, per-block partial sums of sum_l sum_i v_l[i] out_l[i] into part + k*nblk.
 int kpm_step_f64(evsl_ctx *c, int mode, int nvec, uint64_t seed, const double *x,
                  const double *xprev, double *out, double cc, double sc, double *part, int k,
-                 int nblk);
+                 int nblk, bool hat);
 int kpm_step_f32(evsl_ctx *c, int mode, int nvec, uint64_t seed, const float *x,
                  const float *xprev, float *out, double cc, double sc, double *part, int k,
-                 int nblk);
+                 int nblk, bool hat);
 int kpm_nblocks(evsl_ctx *c);
 int convert_f64_to_f32(evsl_ctx *c, int64_t count, const double *x, float *y);
 int convert_f32_to_f64(evsl_ctx *c, int64_t count, const float *x, double *y);
@@ -136,6 +149,14 @@ int colscale_inv_sqrt(evsl_ctx *c, int64_t n, int k, double *Y, const double *nr
 // C (n x l) = A (n x k, lda) * B (k x l, ldb)
 int gemm_nn(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t lda,
             const double *B, int64_t ldb, double *C, int64_t ldc);
+// C -= A B (same shapes as gemm_nn)
+int gemm_nn_sub(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t lda,
+                const double *B, int64_t ldb, double *C, int64_t ldc);
+// Out[:, j] = Z[:, j] + coef[j] X[:, j], coef device (Out may alias X)
+int axpy_cols(evsl_ctx *c, int64_t n, int k, const double *coef, const double *X, const double *Z,
+              double *Out);
+// Y[:, j] *= scale[j] (rows x k, ld rows), scale device
+int colscale(evsl_ctx *c, int64_t rows, int k, double *Y, const double *scale);
 // C (p x q, ldc) = A^T B, A: n x p (lda), B: n x q (ldb); split over rows, fixed-order sums
 int gemm_tn(evsl_ctx *c, int64_t n, int p, int q, const double *A, int64_t lda,
             const double *B, int64_t ldb, double *C, int64_t ldc);

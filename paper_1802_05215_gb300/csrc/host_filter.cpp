@@ -228,11 +228,24 @@ int host_count_below(int k, int l, const double *d, const double *e, double sigm
         neg += p < 0.0;
         schur += e[i] * e[i] / p;
     }
-    double p = 0.0;
-    for (int i = l; i < k; ++i) {
-        p = (i == l) ? d[i] - sigma - schur : d[i] - sigma - e[i - 1] * e[i - 1] / p;
-        if (std::fabs(p) < pmin) p = -pmin;
-        neg += p < 0.0;
+    if (l >= k) return neg;
+    double pm = 1.0, p = d[l] - sigma - schur;
+    if (std::fabs(p) < pmin) p = -pmin;
+    neg += p < 0.0;
+    for (int i = l + 1; i < k; ++i) {
+        double pn = (d[i] - sigma) * p - e[i - 1] * e[i - 1] * pm;
+        if (pn == 0.0) pn = -pmin * p;  // a zero pivot counts as negative
+        neg += (pn < 0.0) != (p < 0.0);
+        pm = p;
+        p = pn;
+        const double ap = std::fabs(p);
+        if (ap > 0x1p+600) {
+            p *= 0x1p-600;
+            pm *= 0x1p-600;
+        } else if (ap < 0x1p-600) {
+            p *= 0x1p+600;
+            pm *= 0x1p+600;
+        }
     }
     return neg;
 }

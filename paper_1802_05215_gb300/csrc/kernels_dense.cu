@@ -237,6 +237,23 @@ __global__ void k_colscale(int64_t n, int k, double *__restrict__ Y, const doubl
     if (i < n && j < k) Y[(int64_t)j * n + i] *= 1.0 / sqrt(nrm2[j]);
 }
 
+// Out[:, j] = Z[:, j] + coef[j] X[:, j] (Out may alias X)
+__global__ void k_axpy_cols(int64_t n, const double *__restrict__ coef, const double *X,
+                            const double *__restrict__ Z, double *Out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i < n) Out[(int64_t)j * n + i] = Z[(int64_t)j * n + i] + coef[j] * X[(int64_t)j * n + i];
+}
+
+// Y[:, j] *= scale[j] (columns of length rows)
+__global__ void k_colscale_by(int64_t rows, double *__restrict__ Y, const double *__restrict__ scale)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i < rows) Y[(int64_t)j * rows + i] *= scale[j];
+}
+
 __global__ void k_gather(int64_t rows, int k, const double *__restrict__ src, int64_t lds,
                          const int *__restrict__ idx, double *__restrict__ dst, int64_t ldd)
 {
@@ -248,6 +265,8 @@ __global__ void k_gather(int64_t rows, int k, const double *__restrict__ src, in
 // C = A B, FP64, 64 x 64 tiles, 16-deep k panels, 4 x 4 outputs per thread.
 constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
 
+// SUB = true: C -= A B instead of C = A B
+template <bool SUB>
 __global__ void __launch_bounds__(256)
 k_gemm_nn(int64_t n, int l, int k, const double *__restrict__ A, int64_t lda,
           const double *__restrict__ B, int64_t ldb, double *__restrict__ C, int64_t ldc)
@@ -296,7 +315,12 @@ k_gemm_nn(int64_t n, int l, int k, const double *__restrict__ A, int64_t lda,
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             int gc = col0 + ty + 16 * j;
-            if (gc < l) C[(int64_t)gc * ldc + gr] = acc[i][j];
+            if (gc < l) {
+                if (SUB)
+                    C[(int64_t)gc * ldc + gr] -= acc[i][j];
+                else
+                    C[(int64_t)gc * ldc + gr] = acc[i][j];
+            }
         }
     }
 }
@@ -482,8 +506,13 @@ __global__ void k_diag(int m, int M, const double *__restrict__ Amat, double *__
 }
 
 // ---------------------------------------------------------------- bisection
-// number of eigenvalues < sigma of the arrow + tridiagonal matrix via the signs of the
-// pivots of an LDL^T factorisation of T - sigma I (Sylvester's law of inertia).
+// Number of eigenvalues < sigma of the arrow + tridiagonal matrix (Sylvester's law of inertia).
+// Arrow rows i < l: pivots d_i - sigma (independent, so their divisions pipeline) and their
+// Schur complement sum_i e_i^2 / (d_i - sigma) folded into row l.  Rows i >= l: the leading
+// minors p_i = (d_i - sigma) p_{i-1} - e_{i-1}^2 p_{i-2} (p_{l-1} = 1, p_l = pivot of row l)
+// without divisions; a sign change between consecutive minors is a negative pivot.  The pair
+// (p_{i-1}, p_i) is rescaled by 2^-600 / 2^600 when it grows or shrinks too far (exact scaling,
+// signs unchanged); a zero minor becomes -pmin times the previous one (a negative pivot).
 __device__ int dev_count_below(int k, int l, const double *__restrict__ d, const double *__restrict__ e,
                                double sigma, double pmin)
 {
@@ -492,21 +521,34 @@ __device__ int dev_count_below(int k, int l, const double *__restrict__ d, const
     for (int i = 0; i < l; i++) {
         double piv = d[i] - sigma;
         if (fabs(piv) < pmin) piv = -pmin;
-        if (piv < 0.0) cnt++;
+        cnt += piv < 0.0;
         sum += e[i] * e[i] / piv;
     }
-    double piv = 0.0;
-    for (int i = l; i < k; i++) {
-        if (i == l)
-            piv = d[i] - sigma - sum;
-        else
-            piv = d[i] - sigma - e[i - 1] * e[i - 1] / piv;
-        if (fabs(piv) < pmin) piv = -pmin;
-        if (piv < 0.0) cnt++;
+    if (l >= k) return cnt;
+    double pm = 1.0;                      // p_{i-1}
+    double p = d[l] - sigma - sum;        // p_l (pivot of row l times p_{l-1} = 1)
+    if (fabs(p) < pmin) p = -pmin;
+    cnt += p < 0.0;
+    for (int i = l + 1; i < k; i++) {
+        double e2 = e[i - 1] * e[i - 1];
+        double pn = (d[i] - sigma) * p - e2 * pm;
+        if (pn == 0.0) pn = -pmin * p;  // a zero pivot counts as negative
+        cnt += (pn < 0.0) != (p < 0.0);
+        pm = p;
+        p = pn;
+        double ap = fabs(p);
+        if (ap > 0x1p+600) {
+            p *= 0x1p-600;
+            pm *= 0x1p-600;
+        } else if (ap < 0x1p-600) {
+            p *= 0x1p+600;
+            pm *= 0x1p+600;
+        }
     }
     return cnt;
 }
 
+// one eigenvalue per thread, few threads per block so that the work spreads over all SMs
 __global__ void k_bisect(int k, int l, const double *__restrict__ d, const double *__restrict__ e,
                          int k0, int k1, double lo0, double hi0, double pmin, double *__restrict__ w)
 {
@@ -655,9 +697,36 @@ int gemm_nn(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t lda, 
 {
     if (n <= 0 || l <= 0) return EVSL_OK;
     dim3 grid((unsigned)((n + GB_M - 1) / GB_M), (unsigned)((l + GB_N - 1) / GB_N));
-    k_gemm_nn<<<grid, 256, 0, c->stream>>>(n, l, k, A, lda, B, ldb, C, ldc);
+    k_gemm_nn<false><<<grid, 256, 0, c->stream>>>(n, l, k, A, lda, B, ldb, C, ldc);
     c->launches++;
     return check_launch(c, "gemm_nn");
+}
+
+int gemm_nn_sub(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t lda, const double *B,
+                int64_t ldb, double *C, int64_t ldc)
+{
+    if (n <= 0 || l <= 0 || k <= 0) return EVSL_OK;
+    dim3 grid((unsigned)((n + GB_M - 1) / GB_M), (unsigned)((l + GB_N - 1) / GB_N));
+    k_gemm_nn<true><<<grid, 256, 0, c->stream>>>(n, l, k, A, lda, B, ldb, C, ldc);
+    c->launches++;
+    return check_launch(c, "gemm_nn_sub");
+}
+
+int axpy_cols(evsl_ctx *c, int64_t n, int k, const double *coef, const double *X, const double *Z,
+              double *Out)
+{
+    if (k <= 0) return EVSL_OK;
+    k_axpy_cols<<<dim3(nblk(n, 256), k), 256, 0, c->stream>>>(n, coef, X, Z, Out);
+    c->launches++;
+    return check_launch(c, "axpy_cols");
+}
+
+int colscale(evsl_ctx *c, int64_t rows, int k, double *Y, const double *scale)
+{
+    if (k <= 0) return EVSL_OK;
+    k_colscale_by<<<dim3(nblk(rows, 256), k), 256, 0, c->stream>>>(rows, Y, scale);
+    c->launches++;
+    return check_launch(c, "colscale");
 }
 
 int gemm_tn(evsl_ctx *c, int64_t n, int p, int q, const double *A, int64_t lda, const double *B,
@@ -779,7 +848,8 @@ int bisect_eigs(evsl_ctx *c, int k, int l, const double *d_host, const double *e
     double pmin = 1e-290 * emax;
     ProfGroup g;
     prof_begin(c, EVSL_K_SMALL_EIG, &g);
-    k_bisect<<<nblk(cnt, 64), 64, 0, c->stream>>>(k, l, dd, ee, k0, k1, lo, hi, pmin, ww);
+    const int tpb = std::max(1, std::min(32, (cnt + 4 * c->dev_sm_count - 1) / (4 * c->dev_sm_count)));
+    k_bisect<<<nblk(cnt, tpb), tpb, 0, c->stream>>>(k, l, dd, ee, k0, k1, lo, hi, pmin, ww);
     c->launches++;
     prof_end(c, &g, 1);
     EVSL_TRY(check_launch(c, "bisect"));

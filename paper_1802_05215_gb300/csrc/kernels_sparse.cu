@@ -76,26 +76,45 @@ __global__ void k_sell_fill(int64_t n, int64_t nslices, const int64_t *__restric
 // Fused Chebyshev step.  MODE 0: out = sc (A x - cc x); y = c0 x + cj out.
 //                        MODE 1: out = sc (A x - cc x) - xprev; y += cj out.
 //                        MODE 2: out = A x.
-template <typename T, int MODE>
+// Explicitly rounded arithmetic, so that every kernel variant (one vector, block, multi-slice)
+// produces bitwise the same numbers for a column whatever the compiler's contraction choices.
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mul_r(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_r(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double sub_r(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_r(float a, float b) { return __fsub_rn(a, b); }
+
+// HAT: the values are the mapped (2/d)(A - c I), so acc is already 2 Ahat x.
+template <typename T, int MODE, bool HAT>
 __device__ __forceinline__ void cheb_epilogue(int64_t o, T acc, T xr, const T *xprev, T *out, T *y,
                                               T cc, T sc, T c0, T cj)
 {
     if (MODE == 2) {
         out[o] = acc;
     } else {
-        T wv = (acc - cc * xr) * sc;
-        if (MODE == 1) wv -= xprev[o];
+        T wv;
+        if (HAT)
+            wv = (MODE == 0) ? mul_r(T(0.5), acc) : sub_r(acc, xprev[o]);
+        else {
+            wv = mul_r(fma_r(-cc, xr, acc), sc);
+            if (MODE == 1) wv = sub_r(wv, xprev[o]);
+        }
         out[o] = wv;
         if (MODE == 0)
-            y[o] = c0 * xr + cj * wv;
+            y[o] = fma_r(cj, wv, mul_r(c0, xr));
         else
-            y[o] += cj * wv;
+            y[o] = fma_r(cj, wv, y[o]);
     }
 }
 
+// x[r] is needed by the unscaled recurrence and by the first step's y = c0 x + c1 w_1
+template <int MODE, bool HAT>
+constexpr bool needs_xr() { return MODE == 0 || (MODE == 1 && !HAT); }
+
 // Single vector: each nonzero is used once, so nothing is cached in registers; the loop is
 // unrolled so that several index loads and gathers are in flight per warp.
-template <typename T, int MODE>
+template <typename T, int MODE, bool HAT>
 __global__ void __launch_bounds__(TPB)
 k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
              const int32_t *__restrict__ col, const T *__restrict__ val,
@@ -110,26 +129,35 @@ k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
     const int32_t *cp = col + b0 + lane;
     T acc = T(0);
 #pragma unroll 4
-    for (int j = 0; j < w; j++) acc += vp[32 * j] * __ldg(x + cp[32 * j]);
+    for (int j = 0; j < w; j++) acc = fma_r(vp[32 * j], __ldg(x + cp[32 * j]), acc);
     int64_t r = s * 32 + lane;
-    if (r < n) cheb_epilogue<T, MODE>(r, acc, MODE == 2 ? T(0) : x[r], xprev, out, y, cc, sc, c0, cj);
+    if (r < n)
+        cheb_epilogue<T, MODE, HAT>(r, acc, needs_xr<MODE, HAT>() ? x[r] : T(0), xprev, out, y, cc, sc, c0, cj);
 }
 
 // [cheb_step1 end]
 
 // Block of nvec columns (column-major, ld = n): the slice's nonzeros stay in registers and
 // the columns are processed NC at a time so that NC * w gathers are in flight per warp.
+// Warps are (slice, column group) pairs: with few slices the columns are split into ngroups
+// contiguous groups of NC-column packs, so that enough warps run; each column's arithmetic
+// is the same whatever the grouping.
 // ctab/c0tab (optional, device): per-column coefficient of this degree and, in MODE 0, of
 // degree 0 -- the multi-slice form, where every column carries its own filter.
-template <typename T, int MODE, int NC>
+template <typename T, int MODE, int NC, bool HAT>
 __global__ void __launch_bounds__(TPB)
 k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
-             const int32_t *__restrict__ col, const T *__restrict__ val, int nvec,
+             const int32_t *__restrict__ col, const T *__restrict__ val, int nvec, int ngroups,
              const T *__restrict__ x, const T *xprev, T *out, T *y, T cc, T sc, T c0, T cj,
              const T *__restrict__ ctab, const T *__restrict__ c0tab)
 {
-    int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (s >= nslices) return;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= nslices * ngroups) return;
+    const int64_t s = wid % nslices;
+    const int grp = (int)(wid / nslices);
+    const int npack = (nvec + NC - 1) / NC;
+    const int lb = (int)((int64_t)grp * npack / ngroups) * NC;
+    const int le = min((int)((int64_t)(grp + 1) * npack / ngroups) * NC, nvec);
     int lane = threadIdx.x & 31;
     int64_t base = sptr[s] + lane;
     int w = (int)((sptr[s + 1] - sptr[s]) >> 5);
@@ -142,8 +170,8 @@ k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
         v[j] = (inreg && j < w) ? val[base + 32 * j] : T(0);
         c[j] = (inreg && j < w) ? col[base + 32 * j] : 0;
     }
-    int l0 = 0;
-    for (; l0 + NC <= nvec; l0 += NC) {
+    int l0 = lb;
+    for (; l0 + NC <= le; l0 += NC) {
         T acc[NC];
 #pragma unroll
         for (int q = 0; q < NC; q++) acc[q] = T(0);
@@ -152,13 +180,13 @@ k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
             for (int j = 0; j < WREG; j++)
                 if (j < w)
 #pragma unroll
-                    for (int q = 0; q < NC; q++) acc[q] += v[j] * __ldg(x + (int64_t)(l0 + q) * n + c[j]);
+                    for (int q = 0; q < NC; q++) acc[q] = fma_r(v[j], __ldg(x + (int64_t)(l0 + q) * n + c[j]), acc[q]);
         } else {
             for (int j = 0; j < w; j++) {
                 T vj = val[base + 32 * j];
                 int cj_ = col[base + 32 * j];
 #pragma unroll
-                for (int q = 0; q < NC; q++) acc[q] += vj * __ldg(x + (int64_t)(l0 + q) * n + cj_);
+                for (int q = 0; q < NC; q++) acc[q] = fma_r(vj, __ldg(x + (int64_t)(l0 + q) * n + cj_), acc[q]);
             }
         }
         if (r < n) {
@@ -166,24 +194,26 @@ k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
             for (int q = 0; q < NC; q++) {
                 int64_t o = (int64_t)(l0 + q) * n + r;
                 T cjq = ctab ? ctab[l0 + q] : cj, c0q = c0tab ? c0tab[l0 + q] : c0;
-                cheb_epilogue<T, MODE>(o, acc[q], MODE == 2 ? T(0) : x[o], xprev, out, y, cc, sc, c0q, cjq);
+                cheb_epilogue<T, MODE, HAT>(o, acc[q], needs_xr<MODE, HAT>() ? x[o] : T(0), xprev, out, y, cc,
+                                            sc, c0q, cjq);
             }
         }
     }
-    for (; l0 < nvec; l0++) {
+    for (; l0 < le; l0++) {
         const T *xl = x + (int64_t)l0 * n;
         T acc = T(0);
         if (inreg) {
 #pragma unroll
             for (int j = 0; j < WREG; j++)
-                if (j < w) acc += v[j] * __ldg(xl + c[j]);
+                if (j < w) acc = fma_r(v[j], __ldg(xl + c[j]), acc);
         } else {
-            for (int j = 0; j < w; j++) acc += val[base + 32 * j] * __ldg(xl + col[base + 32 * j]);
+            for (int j = 0; j < w; j++) acc = fma_r(val[base + 32 * j], __ldg(xl + col[base + 32 * j]), acc);
         }
         if (r < n) {
             int64_t o = (int64_t)l0 * n + r;
             T cjq = ctab ? ctab[l0] : cj, c0q = c0tab ? c0tab[l0] : c0;
-            cheb_epilogue<T, MODE>(o, acc, MODE == 2 ? T(0) : xl[r], xprev, out, y, cc, sc, c0q, cjq);
+            cheb_epilogue<T, MODE, HAT>(o, acc, needs_xr<MODE, HAT>() ? xl[r] : T(0), xprev, out, y, cc, sc,
+                                        c0q, cjq);
         }
     }
 }
@@ -192,7 +222,7 @@ k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
 // sum_l sum_r v_l[r] out_l[r], with v_l[r] = +-1 read from the bit-packed probes
 // (bit `lane` of word bits[l * nslices + s] set <=> v = -1).  Grid-stride over slices with
 // a fixed grid so that the partials of one step fill exactly part[0..gridDim.x).
-template <typename T, int NC>
+template <typename T, int NC, bool HAT>
 __global__ void __launch_bounds__(TPB)
 k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
            const int32_t *__restrict__ col, const T *__restrict__ val, int nvec,
@@ -244,8 +274,13 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                 uint32_t word = bits[(int64_t)l * nslices + s];
                 if (r < n) {
                     int64_t o = (int64_t)l * n + r;
-                    T wv = (acc[q] - cc * x[o]) * sc;
-                    if (mode == 1) wv -= xprev[o];
+                    T wv;
+                    if (HAT)
+                        wv = (mode == 1) ? acc[q] - xprev[o] : T(0.5) * acc[q];
+                    else {
+                        wv = (acc[q] - cc * x[o]) * sc;
+                        if (mode == 1) wv -= xprev[o];
+                    }
                     out[o] = wv;
                     rowmom += ((word >> lane) & 1u) ? -wv : wv;
                 }
@@ -335,6 +370,14 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, co
     for (int64_t p = 0; p < nnz; p++)
         if (ci[p] < 0 || ci[p] >= n)
             return ctx_fail(c, EVSL_ERR_ARG, "set_csr: column index %d out of range at %lld", ci[p], (long long)p);
+    std::vector<int32_t> rlen(n);
+    bool has_diag = true;
+    for (int64_t r = 0; r < n; r++) {
+        rlen[r] = (int32_t)(rp[r + 1] - rp[r]);
+        bool found = false;
+        for (int64_t p = rp[r]; p < rp[r + 1] && !found; p++) found = (ci[p] == r);
+        has_diag = has_diag && found;
+    }
     sell_free(c);
     DevMatrix &A = c->A;
     int64_t ns = sptr[nslices];
@@ -345,10 +388,12 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, co
     if ((st = ctx_alloc(c, (void **)&A.sptr, sizeof(int64_t) * (nslices + 1))) ||
         (st = ctx_alloc(c, (void **)&A.col, sizeof(int32_t) * ns)) ||
         (st = ctx_alloc(c, (void **)&A.val, sizeof(double) * ns)) ||
-        (st = ctx_alloc(c, (void **)&A.val32, sizeof(float) * ns))) {
+        (st = ctx_alloc(c, (void **)&A.val32, sizeof(float) * ns)) ||
+        (st = ctx_alloc(c, (void **)&A.rlen, sizeof(int32_t) * n))) {
         sell_free(c);
         return st;
     }
+    A.has_diag = has_diag;
     A.n = n;
     A.nnz = nnz;
     A.nslices = nslices;
@@ -368,6 +413,7 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, co
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ci, ci, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_cv, cv, sizeof(double) * nnz, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A.rlen, rlen.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         k_sell_fill<double><<<blocks_for(nslices * 32, 256), 256, 0, s>>>(n, nslices, d_rp, d_ci, d_cv,
                                                                           A.sptr, A.col, A.val, A.val32);
@@ -392,69 +438,151 @@ void sell_free(evsl_ctx *c)
     ctx_free(c, A.col, sizeof(int32_t) * A.nstored);
     ctx_free(c, A.val, sizeof(double) * A.nstored);
     ctx_free(c, A.val32, sizeof(float) * A.nstored);
+    ctx_free(c, A.rlen, sizeof(int32_t) * A.n);
+    ctx_free(c, A.vhat, sizeof(double) * A.nstored);
+    ctx_free(c, A.vhat32, sizeof(float) * A.nstored);
     A = DevMatrix();
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool HAT>
 static void launch_cheb(evsl_ctx *c, unsigned grid, int nvec, const T *val, const T *x, const T *xprev,
                         T *out, T *y, T cc, T sc, T c0, T cj, const T *ctab, const T *c0tab)
 {
     const DevMatrix &A = c->A;
     constexpr int NC = sizeof(T) == 8 ? 2 : 4;
     if (nvec == 1 && !ctab)
-        k_cheb_step1<T, MODE><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, x, xprev,
-                                                          out, y, cc, sc, c0, cj);
-    else
-        k_cheb_stepN<T, MODE, NC><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec,
-                                                              x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+        k_cheb_step1<T, MODE, HAT><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, x, xprev,
+                                                               out, y, cc, sc, c0, cj);
+    else {
+        // enough (slice, column group) warps to fill the GPU: 64 warps per SM
+        const int npack = (nvec + NC - 1) / NC;
+        const int64_t want = (int64_t)c->dev_sm_count * 64;
+        const int ngroups = (int)std::max<int64_t>(1, std::min<int64_t>(npack, (want + A.nslices - 1) / A.nslices));
+        const unsigned g2 = blocks_for(A.nslices * 32 * (int64_t)ngroups, TPB);
+        k_cheb_stepN<T, MODE, NC, HAT><<<g2, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec,
+                                                                 ngroups, x, xprev, out, y, cc, sc, c0, cj,
+                                                                 ctab, c0tab);
+    }
 }
 
+template <typename T, bool HAT>
+static void launch_cheb_mode(evsl_ctx *c, int mode, unsigned grid, int nvec, const T *val, const T *x,
+                             const T *xprev, T *out, T *y, T cc, T sc, T c0, T cj, const T *ctab,
+                             const T *c0tab)
+{
+    if (mode == 0)
+        launch_cheb<T, 0, HAT>(c, grid, nvec, val, x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+    else if (mode == 1)
+        launch_cheb<T, 1, HAT>(c, grid, nvec, val, x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+    else
+        launch_cheb<T, 2, HAT>(c, grid, nvec, val, x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+}
+
+// hat: use the mapped values (2/d)(A - cc I), made current by the caller with ensure_mapped
 template <typename T>
 static int cheb_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xprev, T *out,
-                       T *y, double cc, double sc, double c0, double cj, const T *val,
+                       T *y, double cc, double sc, double c0, double cj, const T *val, bool hat,
                        const T *ctab = nullptr, const T *c0tab = nullptr)
 {
-    unsigned grid = blocks_for(c->A.nslices * 32, TPB);
+    const DevMatrix &A = c->A;
+    unsigned grid = blocks_for(A.nslices * 32, TPB);
     T tcc = (T)cc, tsc = (T)sc, tc0 = (T)c0, tcj = (T)cj;
-    if (mode == 0)
-        launch_cheb<T, 0>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj, ctab, c0tab);
-    else if (mode == 1)
-        launch_cheb<T, 1>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj, ctab, c0tab);
-    else
-        launch_cheb<T, 2>(c, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj, ctab, c0tab);
+    hat = hat && mode != 2 && A.vhat;
+    if (hat) {
+        const T *hv = sizeof(T) == 8 ? (const T *)A.vhat : (const T *)A.vhat32;
+        launch_cheb_mode<T, true>(c, mode, grid, nvec, hv, x, xprev, out, y, tcc, tsc, tc0, tcj, ctab, c0tab);
+    } else {
+        launch_cheb_mode<T, false>(c, mode, grid, nvec, val, x, xprev, out, y, tcc, tsc, tc0, tcj, ctab, c0tab);
+    }
     c->launches++;
     return check_launch(c, "cheb_step");
 }
 
 int cheb_step_multi_f64(evsl_ctx *c, int mode, int nvec, const double *x, const double *xprev,
                         double *out, double *y, double cc, double sc, const double *ctab,
-                        const double *c0tab)
+                        const double *c0tab, bool hat)
 {
-    return cheb_step_t<double>(c, mode, nvec, x, xprev, out, y, cc, sc, 0.0, 0.0, c->A.val, ctab, c0tab);
+    return cheb_step_t<double>(c, mode, nvec, x, xprev, out, y, cc, sc, 0.0, 0.0, c->A.val, hat, ctab, c0tab);
 }
 
 int cheb_step_multi_f32(evsl_ctx *c, int mode, int nvec, const float *x, const float *xprev,
                         float *out, float *y, double cc, double sc, const float *ctab,
-                        const float *c0tab)
+                        const float *c0tab, bool hat)
 {
-    return cheb_step_t<float>(c, mode, nvec, x, xprev, out, y, cc, sc, 0.0, 0.0, c->A.val32, ctab, c0tab);
+    return cheb_step_t<float>(c, mode, nvec, x, xprev, out, y, cc, sc, 0.0, 0.0, c->A.val32, hat, ctab, c0tab);
+}
+
+// mapped values (2/d)(A - cc I): padding entries stay zero
+__global__ void k_make_mapped(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
+                              const int32_t *__restrict__ col, const double *__restrict__ val,
+                              const int32_t *__restrict__ rlen, double cc, double sc, double *__restrict__ vhat,
+                              float *__restrict__ vhat32)
+{
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t s = r >> 5;
+    if (s >= nslices) return;
+    int lane = (int)(r & 31);
+    int64_t base = sptr[s] + lane;
+    int w = (int)((sptr[s + 1] - sptr[s]) >> 5);
+    int len = (r < n) ? rlen[r] : 0;
+    for (int j = 0; j < w; j++) {
+        int64_t e = base + 32 * (int64_t)j;
+        double v = 0.0;
+        if (j < len) {
+            v = val[e];
+            if (col[e] == r) v -= cc;
+            v *= sc;
+        }
+        vhat[e] = v;
+        vhat32[e] = (float)v;
+    }
+}
+
+bool ensure_mapped(evsl_ctx *c, double cc, double d, int *status)
+{
+    DevMatrix &A = c->A;
+    if (!A.has_diag || A.n == 0) return false;
+    if (A.vhat && A.hat_c == cc && A.hat_d == d) return true;
+    if (!A.vhat) {
+        int st = ctx_alloc(c, (void **)&A.vhat, sizeof(double) * A.nstored);
+        if (st == EVSL_OK) st = ctx_alloc(c, (void **)&A.vhat32, sizeof(float) * A.nstored);
+        if (st != EVSL_OK) {
+            // not enough room for the mapped copy: the unscaled kernels still work
+            ctx_free(c, A.vhat, sizeof(double) * A.nstored);
+            A.vhat = nullptr;
+            A.vhat32 = nullptr;
+            c->err.clear();
+            return false;
+        }
+    }
+    k_make_mapped<<<blocks_for(A.nslices * 32, 256), 256, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, A.val,
+                                                                         A.rlen, cc, 2.0 / d, A.vhat, A.vhat32);
+    c->launches++;
+    int st = check_launch(c, "make_mapped");
+    if (st != EVSL_OK) {
+        *status = st;
+        return false;
+    }
+    A.hat_c = cc;
+    A.hat_d = d;
+    return true;
 }
 
 int cheb_step_f64(evsl_ctx *c, int mode, int nvec, const double *x, const double *xprev,
-                  double *out, double *y, double cc, double sc, double c0, double cj)
+                  double *out, double *y, double cc, double sc, double c0, double cj, bool hat)
 {
-    return cheb_step_t<double>(c, mode, nvec, x, xprev, out, y, cc, sc, c0, cj, c->A.val);
+    return cheb_step_t<double>(c, mode, nvec, x, xprev, out, y, cc, sc, c0, cj, c->A.val, hat);
 }
 
 int cheb_step_f32(evsl_ctx *c, int mode, int nvec, const float *x, const float *xprev,
-                  float *out, float *y, double cc, double sc, double c0, double cj)
+                  float *out, float *y, double cc, double sc, double c0, double cj, bool hat)
 {
-    return cheb_step_t<float>(c, mode, nvec, x, xprev, out, y, cc, sc, c0, cj, c->A.val32);
+    return cheb_step_t<float>(c, mode, nvec, x, xprev, out, y, cc, sc, c0, cj, c->A.val32, hat);
 }
 
 int spmv_f64(evsl_ctx *c, int nvec, const double *X, double *Y)
 {
-    return cheb_step_t<double>(c, 2, nvec, X, nullptr, Y, nullptr, 0.0, 1.0, 0.0, 0.0, c->A.val);
+    return cheb_step_t<double>(c, 2, nvec, X, nullptr, Y, nullptr, 0.0, 1.0, 0.0, 0.0, c->A.val, false);
 }
 
 int kpm_nblocks(evsl_ctx *c)
@@ -487,29 +615,37 @@ int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0) { return kpm_i
 
 template <typename T>
 static int kpm_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xprev, T *out,
-                      double cc, double sc, double *part, int k, int nblk, const T *val)
+                      double cc, double sc, double *part, int k, int nblk, const T *val, bool hat)
 {
     int st = EVSL_OK;
     uint32_t *bits = kpm_bits(c, nvec, &st);
     if (st) return st;
     const DevMatrix &A = c->A;
     constexpr int NC = sizeof(T) == 8 ? 2 : 4;
-    k_kpm_step<T, NC><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, nvec, bits,
-                                               x, xprev, out, (T)cc, (T)sc, part + (int64_t)k * nblk);
+    if (hat && A.vhat) {
+        const T *hv = sizeof(T) == 8 ? (const T *)A.vhat : (const T *)A.vhat32;
+        k_kpm_step<T, NC, true><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, hv, nvec,
+                                                             bits, x, xprev, out, (T)cc, (T)sc,
+                                                             part + (int64_t)k * nblk);
+    } else {
+        k_kpm_step<T, NC, false><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, nvec,
+                                                              bits, x, xprev, out, (T)cc, (T)sc,
+                                                              part + (int64_t)k * nblk);
+    }
     c->launches++;
     return check_launch(c, "kpm_step");
 }
 
 int kpm_step_f64(evsl_ctx *c, int mode, int nvec, uint64_t, const double *x, const double *xprev,
-                 double *out, double cc, double sc, double *part, int k, int nblk)
+                 double *out, double cc, double sc, double *part, int k, int nblk, bool hat)
 {
-    return kpm_step_t<double>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val);
+    return kpm_step_t<double>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val, hat);
 }
 
 int kpm_step_f32(evsl_ctx *c, int mode, int nvec, uint64_t, const float *x, const float *xprev,
-                 float *out, double cc, double sc, double *part, int k, int nblk)
+                 float *out, double cc, double sc, double *part, int k, int nblk, bool hat)
 {
-    return kpm_step_t<float>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val32);
+    return kpm_step_t<float>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val32, hat);
 }
 
 int convert_f64_to_f32(evsl_ctx *c, int64_t count, const double *x, float *y)
@@ -581,12 +717,13 @@ extern "C" int evsl_filter_apply_noalloc(evsl_ctx *c, const evsl_polfilt *pol, i
     if (pol->deg == 0) {
         st = scale_vec(c, N, const_cast<double *>(X), coef[0], Y);
     } else {
-        st = cheb_step_f64(c, 0, nvec, X, nullptr, B0, Y, cc, 1.0 / d, coef[0], coef[1]);
+        const bool hat = c->A.vhat && c->A.hat_c == cc && c->A.hat_d == d;
+        st = cheb_step_f64(c, 0, nvec, X, nullptr, B0, Y, cc, 1.0 / d, coef[0], coef[1], hat);
         const double *prev = X;
         double *cur = B0;
         for (int j = 2; j <= pol->deg && st == EVSL_OK; j++) {
             double *out = (j == 2) ? B1 : const_cast<double *>(prev);
-            st = cheb_step_f64(c, 1, nvec, cur, prev, out, Y, cc, 2.0 / d, 0.0, coef[j]);
+            st = cheb_step_f64(c, 1, nvec, cur, prev, out, Y, cc, 2.0 / d, 0.0, coef[j], hat);
             prev = cur;
             cur = out;
         }

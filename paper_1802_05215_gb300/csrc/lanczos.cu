@@ -45,15 +45,18 @@ int filter_apply_dev(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doubl
     const double *coef = pol->coef;
     const int deg = pol->deg;
     if (deg == 0) return scale_vec(c, N, const_cast<double *>(X), coef[0], Y);
+    int st = EVSL_OK;
+    const bool hat = ensure_mapped(c, cc, d, &st);
+    if (st) return st;
     ProfGroup g;
     if (prec == EVSL_FP64) {
         prof_begin(c, EVSL_K_CHEB_STEP, &g);
-        EVSL_TRY(cheb_step_f64(c, 0, nvec, X, nullptr, B0, Y, cc, 1.0 / d, coef[0], coef[1]));
+        EVSL_TRY(cheb_step_f64(c, 0, nvec, X, nullptr, B0, Y, cc, 1.0 / d, coef[0], coef[1], hat));
         const double *prev = X;
         double *cur = B0;
         for (int j = 2; j <= deg; j++) {
             double *out = (j == 2) ? B1 : const_cast<double *>(prev);
-            EVSL_TRY(cheb_step_f64(c, 1, nvec, cur, prev, out, Y, cc, 2.0 / d, 0.0, coef[j]));
+            EVSL_TRY(cheb_step_f64(c, 1, nvec, cur, prev, out, Y, cc, 2.0 / d, 0.0, coef[j], hat));
             prev = cur;
             cur = out;
         }
@@ -63,12 +66,12 @@ int filter_apply_dev(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doubl
     float *fx = fbuf, *f0 = fbuf + N, *f1 = fbuf + 2 * N, *fy = fbuf + 3 * N;
     EVSL_TRY(convert_f64_to_f32(c, N, X, fx));
     prof_begin(c, EVSL_K_CHEB_STEP, &g);
-    EVSL_TRY(cheb_step_f32(c, 0, nvec, fx, nullptr, f0, fy, cc, 1.0 / d, coef[0], coef[1]));
+    EVSL_TRY(cheb_step_f32(c, 0, nvec, fx, nullptr, f0, fy, cc, 1.0 / d, coef[0], coef[1], hat));
     const float *prev = fx;
     float *cur = f0;
     for (int j = 2; j <= deg; j++) {
         float *out = (j == 2) ? f1 : const_cast<float *>(prev);
-        EVSL_TRY(cheb_step_f32(c, 1, nvec, cur, prev, out, fy, cc, 2.0 / d, 0.0, coef[j]));
+        EVSL_TRY(cheb_step_f32(c, 1, nvec, cur, prev, out, fy, cc, 2.0 / d, 0.0, coef[j], hat));
         prev = cur;
         cur = out;
     }
@@ -149,6 +152,8 @@ int filter_apply_multi_dev(evsl_ctx *c, int npol, const evsl_polfilt *pols, cons
     double *Ys = Xs + N;
     EVSL_TRY(gather_cols(c, n, npol, X, n, dperm, Xs, n));
     const double cc = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+    const bool hat = ensure_mapped(c, cc, d, &st);
+    if (st) return st;
     ProfGroup g;
     if (maxdeg == 0) {
         for (int t = 0; t < npol; t++)
@@ -160,13 +165,13 @@ int filter_apply_multi_dev(evsl_ctx *c, int npol, const evsl_polfilt *pols, cons
         if (st) return st;
         const double *t64 = (const double *)dtab;
         prof_begin(c, EVSL_K_CHEB_STEP, &g);
-        EVSL_TRY(cheb_step_multi_f64(c, 0, npol, Xs, nullptr, B0, Ys, cc, 1.0 / d, t64 + npol, t64));
+        EVSL_TRY(cheb_step_multi_f64(c, 0, npol, Xs, nullptr, B0, Ys, cc, 1.0 / d, t64 + npol, t64, hat));
         const double *prev = Xs;
         double *cur = B0;
         for (int j = 2; j <= maxdeg; j++) {
             double *out = (j == 2) ? B1 : const_cast<double *>(prev);
             EVSL_TRY(cheb_step_multi_f64(c, 1, active[j], cur, prev, out, Ys, cc, 2.0 / d,
-                                         t64 + (size_t)j * npol, nullptr));
+                                         t64 + (size_t)j * npol, nullptr, hat));
             prev = cur;
             cur = out;
         }
@@ -178,13 +183,13 @@ int filter_apply_multi_dev(evsl_ctx *c, int npol, const evsl_polfilt *pols, cons
         const float *t32 = (const float *)dtab;
         EVSL_TRY(convert_f64_to_f32(c, N, Xs, fx));
         prof_begin(c, EVSL_K_CHEB_STEP, &g);
-        EVSL_TRY(cheb_step_multi_f32(c, 0, npol, fx, nullptr, f0, fy, cc, 1.0 / d, t32 + npol, t32));
+        EVSL_TRY(cheb_step_multi_f32(c, 0, npol, fx, nullptr, f0, fy, cc, 1.0 / d, t32 + npol, t32, hat));
         const float *prev = fx;
         float *cur = f0;
         for (int j = 2; j <= maxdeg; j++) {
             float *out = (j == 2) ? f1 : const_cast<float *>(prev);
             EVSL_TRY(cheb_step_multi_f32(c, 1, active[j], cur, prev, out, fy, cc, 2.0 / d,
-                                         t32 + (size_t)j * npol, nullptr));
+                                         t32 + (size_t)j * npol, nullptr, hat));
             prev = cur;
             cur = out;
         }
@@ -222,6 +227,8 @@ static int kpm_run(evsl_ctx *c, int M, int nvec, uint64_t seed, double lmin, dou
     if (st) return st;
     double *dmu = (double *)ctx_ws(c, WS_SCAL, sizeof(double) * (M + 1 + 16), &st);
     if (st) return st;
+    const bool hat = ensure_mapped(c, cc, d, &st);
+    if (st) return st;
     if constexpr (sizeof(T) == 8)
         EVSL_TRY(kpm_init_f64(c, nvec, seed, (double *)W0));
     else
@@ -233,14 +240,14 @@ static int kpm_run(evsl_ctx *c, int M, int nvec, uint64_t seed, double lmin, dou
         // k = 1: cur = Ahat W0 ; k >= 2: prev <- 2 Ahat cur - prev, then swap
         if constexpr (sizeof(T) == 8) {
             if (k == 1)
-                EVSL_TRY(kpm_step_f64(c, 0, nvec, seed, (double *)W0, nullptr, (double *)W1, cc, 1.0 / d, part, 1, nb));
+                EVSL_TRY(kpm_step_f64(c, 0, nvec, seed, (double *)W0, nullptr, (double *)W1, cc, 1.0 / d, part, 1, nb, hat));
             else
-                EVSL_TRY(kpm_step_f64(c, 1, nvec, seed, (double *)cur, (double *)prev, (double *)prev, cc, 2.0 / d, part, k, nb));
+                EVSL_TRY(kpm_step_f64(c, 1, nvec, seed, (double *)cur, (double *)prev, (double *)prev, cc, 2.0 / d, part, k, nb, hat));
         } else {
             if (k == 1)
-                EVSL_TRY(kpm_step_f32(c, 0, nvec, seed, (float *)W0, nullptr, (float *)W1, cc, 1.0 / d, part, 1, nb));
+                EVSL_TRY(kpm_step_f32(c, 0, nvec, seed, (float *)W0, nullptr, (float *)W1, cc, 1.0 / d, part, 1, nb, hat));
             else
-                EVSL_TRY(kpm_step_f32(c, 1, nvec, seed, (float *)cur, (float *)prev, (float *)prev, cc, 2.0 / d, part, k, nb));
+                EVSL_TRY(kpm_step_f32(c, 1, nvec, seed, (float *)cur, (float *)prev, (float *)prev, cc, 2.0 / d, part, k, nb, hat));
         }
         if (k >= 2) std::swap(prev, cur);
     }

@@ -23,6 +23,11 @@
 namespace {
 
 constexpr double DGKS_ETA2 = 0.5;  // (1/sqrt(2))^2: second Gram-Schmidt pass when ||z'||^2 < 0.5 ||z||^2
+constexpr int POLISH_BLOCKS = 3;            // Krylov blocks per polish cycle after an FP32 run
+constexpr int POLISH_CYCLES = 4;            // polish cycles at most
+constexpr double POLISH_SELECT = 0.9;       // Ritz values of rho kept for the A projection: mu >= 0.9 bar
+constexpr double POLISH_RHO_RES = 1e-3;     // ... whose vectors have ||rho y - mu y|| <= 1e-3 |mu|
+constexpr double MIXED_TOL_LOCK_MAX = 1e-4; // loosest locking level of the FP32 phase
 
 enum Scal { ALPHA = 0, NRM_BEFORE = 1, NRM_AFTER = 2, NRM_Y = 3, TMP = 4, H = 16 };
 
@@ -68,6 +73,11 @@ public:
         tau1_ = o.tau1 > 0 ? o.tau1 : 1e-10;
         bar_ = pol->bar;
         normA_ = std::max(std::fabs(pol->lmin), std::fabs(pol->lmax));
+        // FP32 filter: phase 1 locks at the FP32-reachable level in a slice widened by the
+        // corresponding eigenvalue error; the FP64 polish at the end decides membership and tol
+        mixed_ = (o.prec == EVSL_FP32);
+        tol_lock_ = mixed_ ? std::max(tol_, 1e-6) : tol_;
+        widen_ = mixed_ ? tol_lock_ * normA_ : 0.0;
         const char *venv = getenv("EVSL_VERBOSE");
         verbose_ = venv && venv[0] == '1';
     }
@@ -131,6 +141,13 @@ public:
 
     int finish(int *nev, double *lam, double *res, double *Y, evsl_stats *st, double t_total)
     {
+        if (mixed_ && nlock_ > 0) {
+            cudaEventRecord(e0_, c_->stream);
+            EVSL_TRY(polish());
+            cudaEventRecord(e1_, c_->stream);
+            cudaEventSynchronize(e1_);
+            t_restart_ += ev_ms(e0_, e1_) * 1e-3;
+        }
         std::vector<int> perm(nlock_);
         std::iota(perm.begin(), perm.end(), 0);
         std::sort(perm.begin(), perm.end(), [&](int x, int y) { return lam_l_[x] < lam_l_[y]; });
@@ -352,6 +369,7 @@ private:
     {
         cudaEventRecord(e0_, c_->stream);
         const int k = k_;
+        last_k_ = k;
         nrestart_++;
         int st = EVSL_OK;
         const int zcols = std::min(m_, 128);
@@ -387,7 +405,7 @@ private:
         int ncand = 0;
         const int nlock_before = nlock_;
         std::vector<int> lock_idx, tr_idx;
-        std::vector<double> new_trtheta, new_trs;
+        std::vector<double> new_trtheta, new_trs, tr_res;
         if (ncand0 > 0) {
             EVSL_TRY(h2d(c_, idx, order.data(), sizeof(int) * ncand0));
             EVSL_TRY(gather_cols(c_, k, ncand0, Vj, ldv, idx, Sd, k));
@@ -414,11 +432,11 @@ private:
             }
             for (int cnd = 0; cnd < ncand0; cnd++) {
                 double lj = lamh[cnd];
-                bool inside = (lj >= a_) && (right_closed_ ? (lj <= b_) : (lj < b_));
+                bool inside = (lj >= a_ - widen_) && ((right_closed_ || widen_ > 0) ? (lj <= b_ + widen_) : (lj < b_));
                 if (!inside) continue;
                 ncand++;
                 double rj = std::sqrt(std::max(0.0, resh[cnd])) / normA_;
-                if (rj <= tol_) {
+                if (rj <= tol_lock_) {
                     if (nlock_ + (int)lock_idx.size() >= cap_) {
                         status_ = EVSL_ERR_CAPACITY;
                         break;
@@ -428,6 +446,7 @@ private:
                     res_l_.push_back(rj);
                 } else if ((int)tr_idx.size() < m_ / 2) {
                     // thick-restart set, largest Ritz values first, at most m/2 vectors
+                    tr_res.push_back(rj);
                     tr_idx.push_back(cnd);
                     new_trtheta.push_back(w[order[cnd]]);
                     new_trs.push_back(betak * slast[cnd]);
@@ -441,12 +460,23 @@ private:
         }
         if (status_ == EVSL_ERR_CAPACITY) return finish_run();
         const int ntr = (int)tr_idx.size();
-        if (verbose_)
+        if (verbose_) {
+            double rmin = 1e300;
+            for (double r : tr_res) rmin = std::min(rmin, r);
             fprintf(stderr, "[evsl] restart %d: its=%d k=%d l=%d jacobi_sweeps=%d cand>=bar=%d in_slice=%d "
-                            "locked+%d ntr=%d nlock=%d beta_k=%.3e\n",
-                    nrestart_, its_, k, l_, sweeps, ncand0, ncand, (int)lock_idx.size(), ntr, nlock_, betak);
+                            "locked+%d ntr=%d nlock=%d beta_k=%.3e min_unconverged_res=%.3e\n",
+                    nrestart_, its_, k, l_, sweeps, ncand0, ncand, (int)lock_idx.size(), ntr, nlock_, betak,
+                    tr_res.empty() ? 0.0 : rmin);
+        }
         if (ncand == 0) nocand_++; else nocand_ = 0;
         if (ncand > 0 && nlock_ == nlock_before) stall_++; else stall_ = 0;
+        if (mixed_ && stall_ >= 2 && tol_lock_ < MIXED_TOL_LOCK_MAX) {
+            // candidates in the slice that no longer improve: the FP32 filter's accuracy floor
+            // lies above the locking level, so relax it (the FP64 polish restores tol)
+            tol_lock_ = std::min(MIXED_TOL_LOCK_MAX, 10.0 * tol_lock_);
+            widen_ = tol_lock_ * normA_;
+            stall_ = 0;
+        }
         bool refined = false;
         if (stall_ >= 2 && nrefine_ < 2 && ntr > 0 && nlock_ + ntr <= cap_) {
             // stagnation: Rayleigh-Ritz with A over the locked set and the stuck candidates
@@ -500,71 +530,330 @@ private:
         return EVSL_OK;
     }
 
-    // Rayleigh-Ritz refinement with A over W = U[:, :p] (orthonormal columns): G = W^T A W =
-    // Z diag(theta) Z^T; the columns of W Z with theta in the slice and ||A w - theta w|| <=
-    // tol ||A|| replace the locked set, in ascending theta.
-    int refine_locked(int p, int *kept_out)
+    bool in_slice(double t) const { return t >= a_ && (right_closed_ ? t <= b_ : t < b_); }
+
+    // FP64 recovery after an FP32-filter run: restarted block Krylov iteration with the FP64
+    // filter.  The start block V0 = orth[U, G] holds the pairs the FP32 phase locked and g guard
+    // vectors (the leading vectors of its last Krylov basis: orthogonal to U and dominated by
+    // the largest rho below bar, i.e. the eigenvectors just outside the slice).  Each cycle
+    // builds Q = [V0, V1, V2] with V_{j+1} = orth((I - Q Q^T) rho(Ahat) V_j) and keeps
+    // R = rho(Ahat) Q.  H = Q^T R gives the Ritz values mu of rho on span(Q); the Ritz vectors
+    // with mu >= 0.9 bar and ||rho y - mu y|| <= 1e-3 |mu| (from R^T R) span a nearly invariant
+    // subspace, and a Rayleigh-Ritz step with A on it gives the eigenpair estimates; directions
+    // that have not converged stay out of that projection, where they would make spurious
+    // Ritz values inside the slice.  The next cycle starts from the k0 Ritz vectors of rho with
+    // the largest mu.  The error of an in-slice eigenvector along the eigenvectors just outside
+    // the slice, where rho is close to bar on both sides, falls much faster in the Krylov space
+    // than under plain subspace iteration.  The cycles stop when every estimate in the slice
+    // meets tol and no Ritz value >= bar is left unconverged; the converged in-slice pairs are
+    // the result (EVSL_ERR_NOCONV if some never met tol, EVSL_ERR_CAPACITY if more than cap did).
+    int polish()
     {
+        const int p = nlock_;
+        if (p == 0) return EVSL_OK;
+        const int g = std::min(std::max(16, p / 4), 256);
+        const int k0 = (int)std::min<int64_t>(p + g, n_);
+        const int nb = POLISH_BLOCKS;
+        const int64_t kmax = std::min<int64_t>((int64_t)nb * k0, n_);
+        const int nc = std::min(k0, 64);
         int st = EVSL_OK;
-        const int zc = std::min(p, 128);
-        double *Z = (double *)ctx_ws(c_, WS_LAN_Z, sizeof(double) * n_ * zc, &st);
+        double *Q = (double *)ctx_ws(c_, WS_POL_V, sizeof(double) * n_ * kmax, &st);
         if (st) return st;
-        double *G = (double *)ctx_ws(c_, WS_LAN_G, sizeof(double) * (size_t)p * p, &st);
+        double *R = (double *)ctx_ws(c_, WS_POL_W, sizeof(double) * n_ * kmax, &st);
         if (st) return st;
-        for (int j0 = 0; j0 < p; j0 += zc) {
-            int nc = std::min(zc, p - j0);
-            EVSL_TRY(spmv_f64(c_, nc, U_ + (int64_t)j0 * n_, Z));
-            EVSL_TRY(gemm_tn(c_, n_, p, nc, U_, n_, Z, n_, G + (int64_t)j0 * p, p));
-        }
-        std::vector<double> Gh((size_t)p * p), w(p);
-        EVSL_TRY(d2h(c_, Gh.data(), G, sizeof(double) * Gh.size()));
-        for (int j = 0; j < p; j++)
-            for (int i = 0; i < j; i++) {
-                double v = 0.5 * (Gh[(size_t)j * p + i] + Gh[(size_t)i * p + j]);
-                Gh[(size_t)j * p + i] = v;
-                Gh[(size_t)i * p + j] = v;
+        double *Ys = (double *)ctx_ws(c_, WS_POL_Y, sizeof(double) * n_ * k0, &st);
+        if (st) return st;
+        double *Out = (double *)ctx_ws(c_, WS_LAN_Y, sizeof(double) * n_ * std::max(m_, k0), &st);
+        if (st) return st;
+        double *B = (double *)ctx_ws(c_, WS_POL_B, sizeof(double) * n_ * 2 * nc, &st);
+        if (st) return st;
+        const int kq = std::min(last_k_, k0 - p);
+        EVSL_TRY(d2d(c_, Q, U_, sizeof(double) * n_ * p));
+        if (kq > 0) EVSL_TRY(d2d(c_, Q + (int64_t)p * n_, Q_, sizeof(double) * n_ * kq));
+        for (int j = p + kq; j < k0; j++)
+            EVSL_TRY(fill_uniform_f64(c_, n_, o_.seed, SM_STREAM_LANCZOS, fresh_index_++, Q + (int64_t)j * n_));
+        int kb0 = 0;
+        EVSL_TRY(orthonormalize(Q, k0, Ys, &kb0));
+        std::vector<double> th, r2;
+        for (int cyc = 0; cyc < POLISH_CYCLES && kb0 > 0; cyc++) {
+            // block Krylov basis Q[:, :Kt] and R = rho(Ahat) Q
+            int off = 0, kb = kb0, Kt = 0;
+            for (int j = 0; j < nb; j++) {
+                for (int j0 = 0; j0 < kb; j0 += nc) {
+                    const int m = std::min(nc, kb - j0);
+                    const int64_t o = (int64_t)(off + j0) * n_;
+                    EVSL_TRY(filter_apply_dev(c_, pol_, m, Q + o, R + o, EVSL_FP64, B, B + (int64_t)m * n_, nullptr));
+                }
+                Kt = off + kb;
+                if (j + 1 == nb) break;
+                const int kn = (int)std::min<int64_t>(kb, kmax - Kt);
+                if (kn <= 0) break;
+                double *Nb = Q + (int64_t)Kt * n_;
+                EVSL_TRY(d2d(c_, Nb, R + (int64_t)off * n_, sizeof(double) * n_ * kn));
+                double *G = (double *)ctx_ws(c_, WS_LAN_G, sizeof(double) * (size_t)Kt * kn, &st);
+                if (st) return st;
+                for (int pass = 0; pass < 2; pass++) {
+                    EVSL_TRY(gemm_tn(c_, n_, Kt, kn, Q, n_, Nb, n_, G, Kt));
+                    EVSL_TRY(gemm_nn_sub(c_, n_, kn, Kt, Q, n_, G, Kt, Nb, n_));
+                }
+                int knew = 0;
+                EVSL_TRY(orthonormalize(Nb, kn, Ys, &knew));
+                if (knew == 0) break;
+                off = Kt;
+                kb = knew;
             }
-        const int M = p + (p & 1);
-        double *Vj = (double *)ctx_ws(c_, WS_LAN_T, sizeof(double) * (size_t)M * M, &st);
-        if (st) return st;
-        int ldv = 0, sweeps = 0;
-        EVSL_TRY(jacobi_eig(c_, p, Gh.data(), w.data(), Vj, &ldv, &sweeps));
-        double *Sd = (double *)ctx_ws(c_, WS_LAN_S, sizeof(double) * (size_t)M * M, &st);
-        if (st) return st;
-        std::vector<int> order(p);
-        std::iota(order.begin(), order.end(), 0);
-        std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] < w[y]; });
-        int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * (size_t)(2 * p + 8), &st);
-        if (st) return st;
-        EVSL_TRY(h2d(c_, idx, order.data(), sizeof(int) * p));
-        EVSL_TRY(gather_cols(c_, p, p, Vj, ldv, idx, Sd, p));
-        double *Yt = (double *)ctx_ws(c_, WS_LAN_Y, sizeof(double) * n_ * std::max(m_, p), &st);
-        if (st) return st;
-        EVSL_TRY(gemm_nn(c_, n_, p, p, U_, n_, Sd, p, Yt, n_));
-        std::vector<double> th(p), r2(p);
-        for (int j = 0; j < p; j++) th[j] = w[order[j]];
-        double *lamd = (double *)ctx_ws(c_, WS_KPM_PART, sizeof(double) * 2 * (size_t)p, &st);
-        if (st) return st;
-        EVSL_TRY(h2d(c_, lamd, th.data(), sizeof(double) * p));
-        for (int j0 = 0; j0 < p; j0 += zc) {
-            int nc = std::min(zc, p - j0);
-            EVSL_TRY(spmv_f64(c_, nc, Yt + (int64_t)j0 * n_, Z));
-            EVSL_TRY(colres2(c_, n_, nc, Z, Yt + (int64_t)j0 * n_, n_, lamd + j0, lamd + p + j0));
+            // Ritz values of rho on span(Q): H = Q^T R; residuals in rho from R^T R
+            double *G = (double *)ctx_ws(c_, WS_LAN_G, sizeof(double) * (size_t)Kt * Kt, &st);
+            if (st) return st;
+            EVSL_TRY(gemm_tn(c_, n_, Kt, Kt, Q, n_, R, n_, G, Kt));
+            std::vector<double> Gh((size_t)Kt * Kt), mu(Kt);
+            EVSL_TRY(d2h(c_, Gh.data(), G, sizeof(double) * Gh.size()));
+            symmetrize(Gh, Kt);
+            const int M = std::max(2, Kt + (Kt & 1));
+            double *Vj = (double *)ctx_ws(c_, WS_LAN_T, sizeof(double) * (size_t)M * M, &st);
+            if (st) return st;
+            int ldv = 0, sweeps = 0;
+            EVSL_TRY(jacobi_eig(c_, Kt, Gh.data(), mu.data(), Vj, &ldv, &sweeps));
+            EVSL_TRY(gemm_tn(c_, n_, Kt, Kt, R, n_, R, n_, G, Kt));
+            std::vector<int> order(Kt);
+            std::iota(order.begin(), order.end(), 0);
+            std::sort(order.begin(), order.end(), [&](int x, int y) { return mu[x] > mu[y]; });
+            int ncand = 0;
+            while (ncand < Kt && mu[order[ncand]] >= POLISH_SELECT * bar_) ncand++;
+            std::vector<int> sel;
+            bool pending = false;  // a Ritz value >= bar whose vector has not converged yet
+            double *Sd = (double *)ctx_ws(c_, WS_LAN_S, sizeof(double) * (size_t)M * M, &st);
+            if (st) return st;
+            int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * ((size_t)Kt + 8), &st);
+            if (st) return st;
+            // the restart block's coefficients (the Rayleigh-Ritz step below reuses Vj's memory)
+            const int kr = std::min(k0, Kt);
+            double *Stop = (double *)ctx_ws(c_, WS_POL_R, sizeof(double) * (size_t)Kt * kr, &st);
+            if (st) return st;
+            EVSL_TRY(h2d(c_, idx, order.data(), sizeof(int) * kr));
+            EVSL_TRY(gather_cols(c_, Kt, kr, Vj, ldv, idx, Stop, Kt));
+            if (ncand > 0) {
+                double *T = (double *)ctx_ws(c_, WS_POL_S, sizeof(double) * ((size_t)Kt * ncand + ncand + 8), &st);
+                if (st) return st;
+                double *qd = T + (size_t)Kt * ncand;
+                EVSL_TRY(h2d(c_, idx, order.data(), sizeof(int) * ncand));
+                EVSL_TRY(gather_cols(c_, Kt, ncand, Vj, ldv, idx, Sd, Kt));
+                EVSL_TRY(gemm_nn(c_, Kt, ncand, Kt, G, Kt, Sd, Kt, T, Kt));
+                EVSL_TRY(coldot(c_, Kt, ncand, Sd, Kt, T, Kt, qd));
+                std::vector<double> q(ncand);
+                EVSL_TRY(d2h(c_, q.data(), qd, sizeof(double) * ncand));
+                for (int t = 0; t < ncand; t++) {
+                    const double mj = mu[order[t]];
+                    const double rr = std::sqrt(std::max(0.0, q[t] - mj * mj));
+                    if (rr <= POLISH_RHO_RES * std::fabs(mj) && (int)sel.size() < k0) sel.push_back(order[t]);
+                    else if (mj >= bar_) pending = true;
+                }
+            }
+            const int ks = (int)sel.size();
+            th.clear();
+            r2.clear();
+            bool ok = !pending;
+            int nin = 0;
+            double rmax = 0.0;
+            if (ks > 0) {
+                EVSL_TRY(h2d(c_, idx, sel.data(), sizeof(int) * ks));
+                EVSL_TRY(gather_cols(c_, Kt, ks, Vj, ldv, idx, Sd, Kt));
+                EVSL_TRY(gemm_nn(c_, n_, ks, Kt, Q, n_, Sd, Kt, Ys, n_));
+                int sw2 = 0;
+                EVSL_TRY(rayleigh_ritz(Ys, ks, Out, th, r2, &sw2));
+                for (int j = 0; j < ks; j++)
+                    if (in_slice(th[j])) {
+                        const double rj = std::sqrt(std::max(0.0, r2[j])) / normA_;
+                        nin++;
+                        rmax = std::max(rmax, rj);
+                        if (rj > tol_) ok = false;
+                    }
+            }
+            if (verbose_)
+                fprintf(stderr, "[evsl] polish cycle %d: basis=%d selected=%d pending=%d in_slice=%d max_res=%.3e\n",
+                        cyc, Kt, ks, (int)pending, nin, rmax);
+            if (ok || cyc + 1 == POLISH_CYCLES) break;
+            // restart from the k0 Ritz vectors of rho with the largest mu
+            kb0 = kr;
+            EVSL_TRY(gemm_nn(c_, n_, kb0, Kt, Q, n_, Stop, Kt, Ys, n_));
+            EVSL_TRY(d2d(c_, Q, Ys, sizeof(double) * n_ * kb0));
         }
-        EVSL_TRY(d2h(c_, r2.data(), lamd + p, sizeof(double) * p));
         std::vector<int> keep;
         lam_l_.clear();
         res_l_.clear();
-        for (int j = 0; j < p; j++) {
-            bool inside = (th[j] >= a_) && (right_closed_ ? (th[j] <= b_) : (th[j] < b_));
-            double rj = std::sqrt(std::max(0.0, r2[j])) / normA_;
-            if (inside && rj <= tol_ && (int)keep.size() < cap_) {
+        bool all = true;
+        int nconv = 0;
+        for (int j = 0; j < (int)th.size(); j++) {
+            if (!in_slice(th[j])) continue;
+            const double rj = std::sqrt(std::max(0.0, r2[j])) / normA_;
+            if (rj > tol_) {
+                all = false;
+                continue;
+            }
+            nconv++;
+            if ((int)keep.size() < cap_) {
                 keep.push_back(j);
                 lam_l_.push_back(th[j]);
                 res_l_.push_back(rj);
             }
         }
         if (!keep.empty()) {
+            int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * (keep.size() + 8), &st);
+            if (st) return st;
+            EVSL_TRY(h2d(c_, idx, keep.data(), sizeof(int) * keep.size()));
+            EVSL_TRY(gather_cols(c_, n_, (int)keep.size(), Out, n_, idx, U_, n_));
+        }
+        nlock_ = (int)keep.size();
+        if (nconv > cap_) status_ = EVSL_ERR_CAPACITY;
+        else if (!all && status_ == EVSL_OK) status_ = EVSL_ERR_NOCONV;
+        return EVSL_OK;
+    }
+
+    // In place: the k columns of W become an orthonormal basis of their span (*kr columns).
+    // Columns are scaled to unit norm, then two passes of W <- W S diag(s)^(-1/2) with
+    // W^T W = S diag(s) S^T; the first pass drops directions with s <= 1e-12 max(s), i.e.
+    // columns that are (to about 1e-6) combinations of the others.  Tmp: n x k scratch.
+    int orthonormalize(double *W, int k, double *Tmp, int *kr)
+    {
+        int st = EVSL_OK;
+        double *sd = (double *)ctx_ws(c_, WS_POL_S, sizeof(double) * ((size_t)k + 8), &st);
+        if (st) return st;
+        std::vector<double> nr(k), scl;
+        EVSL_TRY(coldot(c_, n_, k, W, n_, W, n_, sd));
+        EVSL_TRY(d2h(c_, nr.data(), sd, sizeof(double) * k));
+        for (int j = 0; j < k; j++) nr[j] = nr[j] > 0.0 ? 1.0 / std::sqrt(nr[j]) : 0.0;
+        EVSL_TRY(h2d(c_, sd, nr.data(), sizeof(double) * k));
+        EVSL_TRY(colscale(c_, n_, k, W, sd));
+        int kk = k;
+        for (int pass = 0; pass < 2 && kk > 0; pass++) {
+            double *G = (double *)ctx_ws(c_, WS_LAN_G, sizeof(double) * (size_t)kk * kk, &st);
+            if (st) return st;
+            EVSL_TRY(gemm_tn(c_, n_, kk, kk, W, n_, W, n_, G, kk));
+            std::vector<double> Gh((size_t)kk * kk), sv(kk);
+            EVSL_TRY(d2h(c_, Gh.data(), G, sizeof(double) * Gh.size()));
+            symmetrize(Gh, kk);
+            const int M = std::max(2, kk + (kk & 1));
+            double *Vj = (double *)ctx_ws(c_, WS_LAN_T, sizeof(double) * (size_t)M * M, &st);
+            if (st) return st;
+            int ldv = 0, sweeps = 0;
+            EVSL_TRY(jacobi_eig(c_, kk, Gh.data(), sv.data(), Vj, &ldv, &sweeps));
+            double smax = 0.0;
+            for (double v : sv) smax = std::max(smax, v);
+            std::vector<int> kd;
+            scl.clear();
+            for (int j = 0; j < kk; j++)
+                if (sv[j] > 1e-12 * smax) {
+                    kd.push_back(j);
+                    scl.push_back(1.0 / std::sqrt(sv[j]));
+                }
+            const int nk = (int)kd.size();
+            if (nk == 0) {
+                kk = 0;
+                break;
+            }
+            double *Sd = (double *)ctx_ws(c_, WS_LAN_S, sizeof(double) * (size_t)M * M, &st);
+            if (st) return st;
+            int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * ((size_t)nk + 8), &st);
+            if (st) return st;
+            EVSL_TRY(h2d(c_, idx, kd.data(), sizeof(int) * nk));
+            EVSL_TRY(gather_cols(c_, kk, nk, Vj, ldv, idx, Sd, kk));
+            EVSL_TRY(h2d(c_, sd, scl.data(), sizeof(double) * nk));
+            EVSL_TRY(colscale(c_, kk, nk, Sd, sd));
+            EVSL_TRY(gemm_nn(c_, n_, nk, kk, W, n_, Sd, kk, Tmp, n_));
+            EVSL_TRY(d2d(c_, W, Tmp, sizeof(double) * n_ * nk));
+            kk = nk;
+        }
+        *kr = kk;
+        return EVSL_OK;
+    }
+
+    static void symmetrize(std::vector<double> &Gh, int k)
+    {
+        for (int j = 0; j < k; j++)
+            for (int i = 0; i < j; i++) {
+                double v = 0.5 * (Gh[(size_t)j * k + i] + Gh[(size_t)i * k + j]);
+                Gh[(size_t)j * k + i] = v;
+                Gh[(size_t)i * k + j] = v;
+            }
+    }
+
+    // Rayleigh-Ritz with A over the k orthonormal columns of Wb: Wb^T A Wb = S diag(th) S^T
+    // with th ascending, Out = Wb S (Out must not alias Wb), r2[j] = ||A out_j - th_j out_j||^2.
+    int rayleigh_ritz(const double *Wb, int k, double *Out, std::vector<double> &th,
+                      std::vector<double> &r2, int *sweeps_out)
+    {
+        int st = EVSL_OK;
+        const int zc = std::min(k, 128);
+        double *Z = (double *)ctx_ws(c_, WS_LAN_Z, sizeof(double) * n_ * zc, &st);
+        if (st) return st;
+        double *G = (double *)ctx_ws(c_, WS_LAN_G, sizeof(double) * (size_t)k * k, &st);
+        if (st) return st;
+        for (int j0 = 0; j0 < k; j0 += zc) {
+            int nc = std::min(zc, k - j0);
+            EVSL_TRY(spmv_f64(c_, nc, Wb + (int64_t)j0 * n_, Z));
+            EVSL_TRY(gemm_tn(c_, n_, k, nc, Wb, n_, Z, n_, G + (int64_t)j0 * k, k));
+        }
+        std::vector<double> Gh((size_t)k * k), w(k);
+        EVSL_TRY(d2h(c_, Gh.data(), G, sizeof(double) * Gh.size()));
+        symmetrize(Gh, k);
+        const int M = std::max(2, k + (k & 1));
+        double *Vj = (double *)ctx_ws(c_, WS_LAN_T, sizeof(double) * (size_t)M * M, &st);
+        if (st) return st;
+        int ldv = 0, sweeps = 0;
+        EVSL_TRY(jacobi_eig(c_, k, Gh.data(), w.data(), Vj, &ldv, &sweeps));
+        double *Sd = (double *)ctx_ws(c_, WS_LAN_S, sizeof(double) * (size_t)M * M, &st);
+        if (st) return st;
+        std::vector<int> order(k);
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] < w[y]; });
+        int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * (size_t)(2 * k + 8), &st);
+        if (st) return st;
+        EVSL_TRY(h2d(c_, idx, order.data(), sizeof(int) * k));
+        EVSL_TRY(gather_cols(c_, k, k, Vj, ldv, idx, Sd, k));
+        EVSL_TRY(gemm_nn(c_, n_, k, k, Wb, n_, Sd, k, Out, n_));
+        th.assign(k, 0.0);
+        r2.assign(k, 0.0);
+        for (int j = 0; j < k; j++) th[j] = w[order[j]];
+        double *lamd = (double *)ctx_ws(c_, WS_KPM_PART, sizeof(double) * 2 * (size_t)k, &st);
+        if (st) return st;
+        EVSL_TRY(h2d(c_, lamd, th.data(), sizeof(double) * k));
+        for (int j0 = 0; j0 < k; j0 += zc) {
+            int nc = std::min(zc, k - j0);
+            EVSL_TRY(spmv_f64(c_, nc, Out + (int64_t)j0 * n_, Z));
+            EVSL_TRY(colres2(c_, n_, nc, Z, Out + (int64_t)j0 * n_, n_, lamd + j0, lamd + k + j0));
+        }
+        EVSL_TRY(d2h(c_, r2.data(), lamd + k, sizeof(double) * k));
+        *sweeps_out = sweeps;
+        return EVSL_OK;
+    }
+
+    // Rayleigh-Ritz refinement with A over W = U[:, :p] (orthonormal columns): the Ritz
+    // vectors with theta in the (possibly widened) slice and ||A w - theta w|| <= tol_lock ||A||
+    // replace the locked set, in ascending theta.
+    int refine_locked(int p, int *kept_out)
+    {
+        int st = EVSL_OK;
+        double *Yt = (double *)ctx_ws(c_, WS_LAN_Y, sizeof(double) * n_ * std::max(m_, p), &st);
+        if (st) return st;
+        std::vector<double> th, r2;
+        int sweeps = 0;
+        EVSL_TRY(rayleigh_ritz(U_, p, Yt, th, r2, &sweeps));
+        std::vector<int> keep;
+        lam_l_.clear();
+        res_l_.clear();
+        for (int j = 0; j < p; j++) {
+            bool inside = (th[j] >= a_ - widen_) &&
+                          ((right_closed_ || widen_ > 0) ? (th[j] <= b_ + widen_) : (th[j] < b_));
+            double rj = std::sqrt(std::max(0.0, r2[j])) / normA_;
+            if (inside && rj <= tol_lock_ && (int)keep.size() < cap_) {
+                keep.push_back(j);
+                lam_l_.push_back(th[j]);
+                res_l_.push_back(rj);
+            }
+        }
+        if (!keep.empty()) {
+            int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * (size_t)(2 * p + 8), &st);
+            if (st) return st;
             EVSL_TRY(h2d(c_, idx + p, keep.data(), sizeof(int) * keep.size()));
             EVSL_TRY(gather_cols(c_, n_, (int)keep.size(), Yt, n_, idx + p, U_, n_));
         }
@@ -579,13 +868,13 @@ private:
     const evsl_polfilt *pol_;
     evsl_lan_opts o_;
     int m_ = 0, cap_ = 0, maxit_ = 0, ncycle_ = 10;
-    bool right_closed_ = true, verbose_ = false;
-    double tol_ = 1e-8, tau1_ = 1e-10, bar_ = 0.0, normA_ = 1.0;
+    bool right_closed_ = true, verbose_ = false, mixed_ = false;
+    double tol_ = 1e-8, tau1_ = 1e-10, bar_ = 0.0, normA_ = 1.0, tol_lock_ = 1e-8, widen_ = 0.0;
     double *U_ = nullptr, *Q_ = nullptr, *sc_ = nullptr, *h_ = nullptr;
     size_t nsc_ = 0;
     std::vector<double> T_, trtheta_, trs_, lam_l_, res_l_;
     int nlock_ = 0, l_ = 0, k_ = 0, i_ = 0, lstart_ = 0, its_ = 0, nrestart_ = 0, nocand_ = 0;
-    int stall_ = 0, nrefine_ = 0, prev_nabove_ = 0;
+    int stall_ = 0, nrefine_ = 0, prev_nabove_ = 0, last_k_ = 0;
     bool tr_pending_ = false, have_old_ = false, done_ = false;
     double t_old_ = 0.0;
     uint64_t fresh_index_ = 0;
@@ -676,6 +965,7 @@ int batch_create(evsl_ctx *c, const evsl_lan_opts *o, evsl_batch **out)
     bt->o = *o;
     cudaEventCreate(&bt->fa);
     cudaEventCreate(&bt->fb);
+    c->batches.push_back(bt);
     *out = bt;
     return EVSL_OK;
 }
@@ -683,6 +973,8 @@ int batch_create(evsl_ctx *c, const evsl_lan_opts *o, evsl_batch **out)
 void batch_destroy(evsl_batch *bt)
 {
     if (!bt) return;
+    auto &v = bt->c->batches;
+    v.erase(std::remove(v.begin(), v.end(), bt), v.end());
     cudaStreamSynchronize(bt->c->stream);
     bt->solvers.clear();
     if (bt->fa) cudaEventDestroy(bt->fa);
@@ -690,11 +982,49 @@ void batch_destroy(evsl_batch *bt)
     delete bt;
 }
 
+// Device bytes the shared workspaces still have to grow by so that a step (batched filter) and
+// a restart / refinement of any active job fit: admission reserves them before accepting a job.
+static size_t workspace_growth(evsl_ctx *c, const evsl_batch *bt, const evsl_slice_job *job)
+{
+    const size_t n = (size_t)c->A.n;
+    size_t na = bt->solvers.size() + 1;
+    int mmax = job->m, capmax = job->cap, degmax = job->pol->deg;
+    for (const evsl_slice_job *J : bt->jobs) {
+        mmax = std::max(mmax, J->m);
+        capmax = std::max(capmax, J->cap);
+        degmax = std::max(degmax, J->pol->deg);
+    }
+    const size_t big = std::max<size_t>(mmax, 2 * (size_t)capmax);
+    size_t need = 0;
+    auto want = [&](int slot, size_t bytes) {
+        size_t have = (c->ws_bytes.size() > (size_t)slot) ? c->ws_bytes[slot] : 0;
+        if (bytes > have) need += bytes - have;
+    };
+    want(WS_LAN_VEC, sizeof(double) * 2 * n * na);
+    want(WS_W2, sizeof(double) * 2 * n * na);
+    want(WS_W0, sizeof(double) * std::max<size_t>(n * na, 2 * n * 128));
+    want(WS_W1, sizeof(double) * n * na);
+    if (bt->o.prec == EVSL_FP32) want(WS_F32_X, sizeof(float) * 4 * n * na);
+    want(WS_KPM_PART, sizeof(double) * ((size_t)(degmax + 1) * na + 2 * big + 64));
+    want(WS_LAN_Y, sizeof(double) * n * big);
+    want(WS_LAN_Z, sizeof(double) * n * 128);
+    want(WS_LAN_T, sizeof(double) * (big + 2) * (big + 2));
+    want(WS_LAN_S, sizeof(double) * (big + 2) * (big + 2));
+    want(WS_LAN_G, sizeof(double) * big * big);
+    want(WS_PARTIAL, sizeof(double) * ((n + 2047) / 2048 + 1) * (size_t)(capmax + mmax + 1 + 64));
+    return need;
+}
+
 int batch_add(evsl_batch *bt, evsl_slice_job *job)
 {
     evsl_ctx *c = bt->c;
     job->status = EVSL_OK;
     *job->nev = 0;
+    const size_t need = workspace_growth(c, bt, job);
+    const size_t bases = sizeof(double) * (size_t)c->A.n * ((size_t)job->cap + job->m + 1);
+    if (c->budget && c->used + need + bases > c->budget)
+        return ctx_fail(c, EVSL_ERR_NOMEM, "batch_add: HBM budget has no room for the job (%zu + %zu + %zu > %zu bytes)",
+                        c->used, bases, need, c->budget);
     std::unique_ptr<SliceSolver> s(new SliceSolver(c, job->a, job->b, job->pol, bt->o, job->m, job->cap,
                                                    job->right_closed != 0));
     int rc = s->init();

@@ -180,6 +180,11 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
+            # the library destroys this context's batches with it: invalidate their handles first
+            for b in getattr(self, "_batches", []):
+                bt = b()
+                if bt is not None:
+                    bt.h = None
             self.lib.evsl_destroy(self.h)
             self.h = None
 
@@ -335,6 +340,10 @@ class Batch:
         ctx._check(ctx.lib.evsl_batch_create(ctx.h, C.byref(self.opts), C.byref(h)), "batch_create")
         self.h = h
         self.active: list[Job] = []
+        import weakref
+        if not hasattr(ctx, "_batches"):
+            ctx._batches = []
+        ctx._batches.append(weakref.ref(self))
 
     def add(self, a, b, filt: Filter, m, cap=None, right_closed=True, Y=None, tag=None) -> Job:
         """Admit a job; raises EvslError with code -2 when the HBM budget has no room for it."""
@@ -364,9 +373,9 @@ class Batch:
         return False
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self.ctx, "h", None):
             self.ctx.lib.evsl_batch_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
