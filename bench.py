@@ -377,22 +377,23 @@ def run_reference(args):
 
 
 def serving_workload(seed: int = 0, nreq: int = 24):
-    """Mixed serving stream: 2-D and 3-D Laplacians and Anderson models of several sizes; each
-    request one slice holding 20..120 eigenvalues.  Laplacian intervals are cut midway between
-    closed-form eigenvalues (exact counts); Anderson intervals are DOS slices of the spectrum."""
+    """Mixed serving stream: 2-D and 3-D Laplacians and Anderson models (n = 1.0e4 .. 2.3e4);
+    each request one slice holding 20..120 eigenvalues.  Laplacian intervals are cut midway
+    between distinct closed-form eigenvalues (exact counts); Anderson intervals are DOS slices
+    of the spectrum.  Arrivals are Poisson with a mean gap of 0.25 s."""
     from paper_1802_05215_gb300 import native
-    mats = {"lap2d_200": inputs.laplacian_2d(200), "lap2d_300": inputs.laplacian_2d(300),
-            "lap3d_40": inputs.laplacian_3d(40), "lap3d_50": inputs.laplacian_3d(50),
-            "anderson_40_W3": inputs.anderson_3d(40, 3.0, 1),
-            "anderson_40_W6": inputs.anderson_3d(40, 6.0, 2)}
+    mats = {"lap2d_100": inputs.laplacian_2d(100), "lap2d_150": inputs.laplacian_2d(150),
+            "lap3d_22": inputs.laplacian_3d(22), "lap3d_28": inputs.laplacian_3d(28),
+            "anderson_24_W3": inputs.anderson_3d(24, 3.0, 1),
+            "anderson_24_W6": inputs.anderson_3d(24, 6.0, 2)}
 
     def lap_spectrum(dims, nx):
         f = 2.0 - 2.0 * np.cos(np.arange(1, nx + 1) * np.pi / (nx + 1))
         e = f[:, None] + f[None, :] if dims == 2 else f[:, None, None] + f[None, :, None] + f[None, None, :]
         return np.sort(e.ravel())
 
-    spectra = {"lap2d_200": lap_spectrum(2, 200), "lap2d_300": lap_spectrum(2, 300),
-               "lap3d_40": lap_spectrum(3, 40), "lap3d_50": lap_spectrum(3, 50)}
+    spectra = {"lap2d_100": lap_spectrum(2, 100), "lap2d_150": lap_spectrum(2, 150),
+               "lap3d_22": lap_spectrum(3, 22), "lap3d_28": lap_spectrum(3, 28)}
     rng = np.random.default_rng(seed)
     reqs, t = [], 0.0
     from paper_1802_05215_gb300.serve import Request
@@ -403,8 +404,14 @@ def serving_workload(seed: int = 0, nreq: int = 24):
         c = int(rng.integers(20, 121))
         if key in spectra:
             ev = spectra[key]
+            gap = 1e-9 * max(1.0, float(ev[-1]))
             i0 = int(rng.integers(1, len(ev) - c - 1))
-            a, b = 0.5 * (ev[i0 - 1] + ev[i0]), 0.5 * (ev[i0 + c - 1] + ev[i0 + c])
+            while ev[i0] - ev[i0 - 1] <= gap:                 # cut between distinct eigenvalues
+                i0 += 1
+            i1 = i0 + c
+            while i1 < len(ev) - 1 and ev[i1] - ev[i1 - 1] <= gap:
+                i1 += 1
+            a, b = 0.5 * (ev[i0 - 1] + ev[i0]), 0.5 * (ev[i1 - 1] + ev[i1])
             est = float(np.count_nonzero((ev >= a) & (ev <= b)))
         else:
             if key not in dos:
@@ -426,10 +433,12 @@ def run_serving(args):
     from paper_1802_05215_gb300 import native, serve
     mats, reqs = serving_workload()
     server = serve.Server(mats, prec=native.FP32)
+    server.run(reqs[:2], batched=True)                     # warm-up (module load, workspaces)
     out = {}
-    for mode, batched in [("plain_fp64_fifo", False), ("batched_fp32", True)]:
+    for mode, batched, prec in [("plain_fp64_fifo", False, native.FP64), ("batched_fp64", True, native.FP64),
+                                ("batched_fp32", True, native.FP32)]:
         t0 = time.perf_counter()
-        res = server.run(reqs, batched=batched)
+        res = server.run(reqs, batched=batched, prec=prec)
         wall = time.perf_counter() - t0
         out[mode] = serve.summarize(res, wall)
         out[mode]["nev_by_request"] = [o.nev for o in res]
@@ -440,10 +449,13 @@ def run_serving(args):
             "value": b["eigenpairs_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32 filter, f64 reorth/Ritz", "data": "synthetic",
             "config": {"workload": f"{len(reqs)} Poisson-arriving slice requests (20..120 eigenvalues) "
-                                   "over 2-D/3-D Laplacians and Anderson models, n = 40k..125k"},
+                                   "over 2-D/3-D Laplacians and Anderson models, n = 1.0e4..2.3e4"},
             "p50_latency_s": b["p50_latency_s"], "p99_latency_s": b["p99_latency_s"],
             "plain_fp64": {k: v for k, v in out["plain_fp64_fifo"].items() if k != "nev_by_request"},
+            "batched_fp64": {k: v for k, v in out["batched_fp64"].items() if k != "nev_by_request"},
             "batched": {k: v for k, v in b.items() if k != "nev_by_request"},
+            "nev_by_request": {k: v["nev_by_request"] for k, v in out.items()},
+            "expected_by_request": [r.est for r in reqs],
             "same_counts_plain_vs_batched": same}
     print(json.dumps(line), flush=True)
     return line
@@ -473,12 +485,13 @@ def run_anderson_batched(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         batch = ctx.chebLanTr_batch(slices, filters, ms, caps=caps, prec=native.FP32, right_closed=rc,
-                                    Ys=Ys, tol=TOL)
+                                    Ys=Ys, tol=TOL, allow_partial=True)
         t_batch = time.perf_counter() - t0
         plain, t_plain = [], 0.0
         for j, ((a, b), f, m, cap) in enumerate(zip(slices, filters, ms, caps)):
             t0 = time.perf_counter()
-            plain.append(ctx.chebLanTr(a, b, f, m=m, cap=cap, tol=TOL, right_closed=rc[j], Y=Ys[j]))
+            plain.append(ctx.chebLanTr(a, b, f, m=m, cap=cap, tol=TOL, right_closed=rc[j], Y=Ys[j],
+                                       allow_partial=True))
             t_plain += time.perf_counter() - t0
     nb = sum(r["nev"] for r in batch)
     npl = sum(r["nev"] for r in plain)
@@ -492,6 +505,11 @@ def run_anderson_batched(args):
             "plain_fp64": {"eigenpairs": npl, "seconds": t_plain, "eigenpairs_per_s": npl / t_plain,
                            "max_res": max(float(r["res"].max()) for r in plain if r["nev"])},
             "counts_batched": [r["nev"] for r in batch], "counts_plain": [r["nev"] for r in plain],
+            "status_batched": [int(r["status"]) for r in batch], "status_plain": [int(r["status"]) for r in plain],
+            "stats_batched": [{k: r["stats"][k] for k in ("niter", "t_filter", "t_orth", "t_restart", "t_total")}
+                              for r in batch],
+            "stats_plain": [{k: r["stats"][k] for k in ("niter", "t_filter", "t_orth", "t_restart", "t_total")}
+                            for r in plain],
             "dos_estimates": [float(est[i]) for i in pick],
             "degrees": [f.deg for f in filters],
             "speedup": (nb / t_batch) / (npl / t_plain)}

@@ -24,7 +24,7 @@ namespace {
 
 constexpr double DGKS_ETA2 = 0.5;  // (1/sqrt(2))^2: second Gram-Schmidt pass when ||z'||^2 < 0.5 ||z||^2
 constexpr int POLISH_BLOCKS = 3;            // Krylov blocks per polish cycle after an FP32 run
-constexpr int POLISH_CYCLES = 4;            // polish cycles at most
+constexpr int POLISH_CYCLES = 6;            // polish cycles at most
 constexpr double POLISH_SELECT = 0.9;       // Ritz values of rho kept for the A projection: mu >= 0.9 bar
 constexpr double POLISH_RHO_RES = 1e-3;     // ... whose vectors have ||rho y - mu y|| <= 1e-3 |mu|
 constexpr double MIXED_TOL_LOCK_MAX = 1e-4; // loosest locking level of the FP32 phase
@@ -887,7 +887,9 @@ private:
 int status_message(evsl_ctx *c, int st, int cap, int maxit)
 {
     if (st == EVSL_ERR_CAPACITY) return ctx_fail(c, st, "more than cap=%d eigenpairs converged", cap);
-    if (st == EVSL_ERR_NOCONV) return ctx_fail(c, st, "maxit=%d Lanczos steps reached", maxit);
+    if (st == EVSL_ERR_NOCONV)
+        return ctx_fail(c, st, "some eigenpairs of the slice did not reach tol (maxit=%d Lanczos steps, or "
+                               "the FP64 polish cycles after an FP32 filter ran out)", maxit);
     return st;
 }
 

@@ -81,8 +81,10 @@ class Server:
         for m in self.mats.values():
             m.close()
 
-    def run(self, requests: list[Request], batched: bool = True) -> list[Outcome]:
-        """Serve the requests against the wall clock; returns one outcome per request."""
+    def run(self, requests: list[Request], batched: bool = True, prec=None) -> list[Outcome]:
+        """Serve the requests against the wall clock; returns one outcome per request.
+        prec: filter precision of the batched mode (default: the server's)."""
+        prec = self.prec if prec is None else prec
         pending = sorted(requests, key=lambda r: r.arrival)
         queue: list[Request] = []
         out: dict[int, Outcome] = {}
@@ -103,7 +105,7 @@ class Server:
                                      float(res["res"].max()) if res["nev"] else 0.0, res["lam"])
             return [out[r.rid] for r in requests]
         for M in self.mats.values():
-            M.batch = native.Batch(M.ctx, tol=self.tol, prec=self.prec)
+            M.batch = native.Batch(M.ctx, tol=self.tol, prec=prec)
         while len(out) < len(requests):
             t = now()
             while i < len(pending) and pending[i].arrival <= t:
