@@ -103,6 +103,8 @@ bool ensure_mapped(evsl_ctx *c, double cc, double d, int *status);
 // Y = A X (FP64), nvec columns
 int spmv_f64(evsl_ctx *c, int nvec, const double *X, double *Y);
 // KPM: fill W0 with the probes, then steps
+// KPM probe blocks are row-major with leading dimension kpm_ld(nvec) (nvec rounded up to even)
+int kpm_ld(int nvec);
 int kpm_init_f64(evsl_ctx *c, int nvec, uint64_t seed, double *W0);
 int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0);
 // mode 0: out = (A x - cc x) sc; mode 1: out = (A x - cc x) sc - xprev.  Writes, for moment

@@ -566,6 +566,40 @@ __global__ void k_bisect(int k, int l, const double *__restrict__ d, const doubl
     w[j - k0] = 0.5 * (lo + hi);
 }
 
+// Multisection: one warp per eigenvalue j (ascending index); each round the 32 lanes count
+// the eigenvalues below 32 interior points of [lo, hi] (33 equal parts) at once and the
+// bracket shrinks to the part where the count passes j, so a round does the work of five
+// bisection steps with the same sequential depth as one.  d and e are staged in shared memory.
+// Same stopping rule as k_bisect.
+__global__ void k_multisect(int k, int l, const double *__restrict__ dg, const double *__restrict__ eg,
+                            int k0, int k1, double lo0, double hi0, double pmin, double *__restrict__ w)
+{
+    extern __shared__ double sh[];
+    double *d = sh, *e = sh + k;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        d[i] = dg[i];
+        e[i] = eg[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int j = k0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (j >= k1) return;  // whole warps leave together
+    double lo = lo0, hi = hi0;
+    for (int it = 0; it < 64; it++) {
+        if (hi - lo <= 4.5e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
+        const double h = (hi - lo) * (1.0 / 33.0);
+        const double x = lo + h * (double)(lane + 1);
+        const bool above = dev_count_below(k, l, d, e, x, pmin) > j;  // lambda_j < x
+        const unsigned b = __ballot_sync(0xffffffffu, above);
+        const double nlo = (b == 0u) ? lo + h * 32.0 : (__ffs(b) == 1 ? lo : lo + h * (double)(__ffs(b) - 1));
+        const double nhi = (b == 0u) ? hi : lo + h * (double)__ffs(b);
+        if (!(nlo > lo) && !(nhi < hi)) break;  // the points no longer split the bracket
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0) w[j - k0] = 0.5 * (lo + hi);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -848,8 +882,18 @@ int bisect_eigs(evsl_ctx *c, int k, int l, const double *d_host, const double *e
     double pmin = 1e-290 * emax;
     ProfGroup g;
     prof_begin(c, EVSL_K_SMALL_EIG, &g);
-    const int tpb = std::max(1, std::min(32, (cnt + 4 * c->dev_sm_count - 1) / (4 * c->dev_sm_count)));
-    k_bisect<<<nblk(cnt, tpb), tpb, 0, c->stream>>>(k, l, dd, ee, k0, k1, lo, hi, pmin, ww);
+    const size_t smem = sizeof(double) * 2 * (size_t)k;
+    if (smem <= 200 * 1024) {
+        // one warp per eigenvalue, four per block
+        if (smem > 48 * 1024) {
+            cudaError_t ea = cudaFuncSetAttribute(k_multisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (ea != cudaSuccess) return ctx_cuda(c, ea, "multisect smem");
+        }
+        k_multisect<<<(unsigned)((cnt + 3) / 4), 128, smem, c->stream>>>(k, l, dd, ee, k0, k1, lo, hi, pmin, ww);
+    } else {
+        const int tpb = std::max(1, std::min(32, (cnt + 4 * c->dev_sm_count - 1) / (4 * c->dev_sm_count)));
+        k_bisect<<<nblk(cnt, tpb), tpb, 0, c->stream>>>(k, l, dd, ee, k0, k1, lo, hi, pmin, ww);
+    }
     c->launches++;
     prof_end(c, &g, 1);
     EVSL_TRY(check_launch(c, "bisect"));

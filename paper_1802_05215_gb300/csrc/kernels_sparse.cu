@@ -218,75 +218,101 @@ k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
     }
 }
 
+// KPM block layout: row-major, row r holding its probe values contiguously with leading
+// dimension ld = nvec rounded up to even (the padding probe stays zero); the bit-packed signs
+// are row-major too, bit (l % 32) of word bits[r * nw + l / 32] set <=> v_l[r] = -1.
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
 // KPM step: the same recurrence without y, plus the moment partial sums
-// sum_l sum_r v_l[r] out_l[r], with v_l[r] = +-1 read from the bit-packed probes
-// (bit `lane` of word bits[l * nslices + s] set <=> v = -1).  Grid-stride over slices with
-// a fixed grid so that the partials of one step fill exactly part[0..gridDim.x).
-template <typename T, int NC, bool HAT>
-__global__ void __launch_bounds__(TPB)
+// sum_l sum_r v_l[r] out_l[r].  One warp per 32-row slice, walking its rows; the lanes cover
+// the probes two at a time (vector loads, 64 probes per pass), so every gathered neighbour row
+// of the block is one coalesced load.  Grid-stride over slices with a fixed grid so that the
+// partials of one step fill exactly part[0..gridDim.x).  Each lane sums its share of one
+// slice (32 rows, 64 probes per pass) in the block's precision and adds it to an FP64 partial,
+// so the sums across slices are FP64 in both precisions (FP64 issue is 1/64 of FP32 here).
+template <typename T, bool HAT>
+__global__ void __launch_bounds__(TPB, 4)
 k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
-           const int32_t *__restrict__ col, const T *__restrict__ val, int nvec,
-           const uint32_t *__restrict__ bits, const T *__restrict__ x, const T *xprev, T *out,
-           T cc, T sc, double *__restrict__ part)
+           const int32_t *__restrict__ col, const T *__restrict__ val, const int32_t *__restrict__ rlen,
+           int nvec, int ld, const uint32_t *__restrict__ bits, const T *__restrict__ x, const T *xprev,
+           T *out, T cc, T sc, double *__restrict__ part)
 {
+    using V2 = typename Vec2<T>::type;
     __shared__ double red[TPB / 32];
-    int lane = threadIdx.x & 31;
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nw = (nvec + 31) >> 5;
     double mom = 0.0;
     for (int64_t s = warp; s < nslices; s += nwarps) {
-        int64_t base = sptr[s] + lane;
-        int w = (int)((sptr[s + 1] - sptr[s]) >> 5);
-        int64_t r = s * 32 + lane;
-        T v[WREG];
-        int c[WREG];
-        const bool inreg = (w <= WREG);
+        const int64_t sbase = sptr[s];
+        T smom = T(0);  // this lane's share of the slice, in the block's precision
+        for (int rr = 0; rr < 32; rr++) {
+            const int64_t r = s * 32 + rr;
+            if (r >= n) break;
+            const int len = rlen[r];
+            for (int l0 = 0; l0 < nvec; l0 += 64) {
+                const int l = l0 + 2 * lane;
+                const bool act = l < nvec;
+                T a0 = T(0), a1 = T(0);
+                if (len <= WREG) {
 #pragma unroll
-        for (int j = 0; j < WREG; j++) {
-            v[j] = (inreg && j < w) ? val[base + 32 * j] : T(0);
-            c[j] = (inreg && j < w) ? col[base + 32 * j] : 0;
-        }
-        T rowmom = T(0);
-        for (int l0 = 0; l0 < nvec; l0 += NC) {
-            T acc[NC];
-#pragma unroll
-            for (int q = 0; q < NC; q++) acc[q] = T(0);
-            if (inreg) {
-#pragma unroll
-                for (int j = 0; j < WREG; j++)
-                    if (j < w)
-#pragma unroll
-                        for (int q = 0; q < NC; q++)
-                            if (l0 + q < nvec) acc[q] += v[j] * __ldg(x + (int64_t)(l0 + q) * n + c[j]);
-            } else {
-                for (int j = 0; j < w; j++) {
-                    T vj = val[base + 32 * j];
-                    int cj_ = col[base + 32 * j];
-#pragma unroll
-                    for (int q = 0; q < NC; q++)
-                        if (l0 + q < nvec) acc[q] += vj * __ldg(x + (int64_t)(l0 + q) * n + cj_);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < NC; q++) {
-                int l = l0 + q;
-                if (l >= nvec) break;
-                uint32_t word = bits[(int64_t)l * nslices + s];
-                if (r < n) {
-                    int64_t o = (int64_t)l * n + r;
-                    T wv;
-                    if (HAT)
-                        wv = (mode == 1) ? acc[q] - xprev[o] : T(0.5) * acc[q];
-                    else {
-                        wv = (acc[q] - cc * x[o]) * sc;
-                        if (mode == 1) wv -= xprev[o];
+                    for (int j = 0; j < WREG; j++)
+                        if (j < len) {
+                            const int64_t e = sbase + 32 * (int64_t)j + rr;
+                            const T v = val[e];
+                            const int cj = col[e];
+                            if (act) {
+                                const V2 xv = __ldg(reinterpret_cast<const V2 *>(x + (int64_t)cj * ld + l));
+                                a0 += v * xv.x;
+                                a1 += v * xv.y;
+                            }
+                        }
+                } else {
+                    for (int j = 0; j < len; j++) {
+                        const int64_t e = sbase + 32 * (int64_t)j + rr;
+                        const T v = val[e];
+                        const int cj = col[e];
+                        if (act) {
+                            const V2 xv = __ldg(reinterpret_cast<const V2 *>(x + (int64_t)cj * ld + l));
+                            a0 += v * xv.x;
+                            a1 += v * xv.y;
+                        }
                     }
-                    out[o] = wv;
-                    rowmom += ((word >> lane) & 1u) ? -wv : wv;
+                }
+                if (act) {
+                    const int64_t o = r * ld + l;
+                    V2 w;
+                    if (HAT) {
+                        if (mode == 1) {
+                            const V2 pv = *reinterpret_cast<const V2 *>(xprev + o);
+                            w.x = a0 - pv.x;
+                            w.y = a1 - pv.y;
+                        } else {
+                            w.x = T(0.5) * a0;
+                            w.y = T(0.5) * a1;
+                        }
+                    } else {
+                        const V2 xo = *reinterpret_cast<const V2 *>(x + o);
+                        w.x = (a0 - cc * xo.x) * sc;
+                        w.y = (a1 - cc * xo.y) * sc;
+                        if (mode == 1) {
+                            const V2 pv = *reinterpret_cast<const V2 *>(xprev + o);
+                            w.x -= pv.x;
+                            w.y -= pv.y;
+                        }
+                    }
+                    *reinterpret_cast<V2 *>(out + o) = w;
+                    const uint32_t word = bits[r * nw + (l >> 5)];
+                    const int b = l & 31;
+                    smom += ((word >> b) & 1u) ? -w.x : w.x;
+                    if (l + 1 < nvec) smom += ((word >> (b + 1)) & 1u) ? -w.y : w.y;
                 }
             }
         }
-        mom += (double)rowmom;
+        mom += (double)smom;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mom += __shfl_xor_sync(0xffffffffu, mom, off);
@@ -299,24 +325,25 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
     }
 }
 
-// Probes: W0[l*n + r] = sign of draw(seed, KPM, l*n + r); bits as above.
+// Probes in the row-major layout: W0[r * ld + l] = sign of draw(seed, KPM, l * n + r) for
+// l < nvec, 0 for the padding probe; one warp builds one sign word of one row.
 template <typename T>
-__global__ void k_kpm_init(int64_t n, int64_t nslices, int nvec, uint64_t key, T *W0,
-                           uint32_t *bits)
+__global__ void k_kpm_init(int64_t n, int nvec, int ld, uint64_t key, T *W0, uint32_t *bits)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t total = nslices * 32 * (int64_t)nvec;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int nw = (nvec + 31) >> 5;
+    const int64_t total = n * nw * 32;
     if (t >= total) return;  // whole warps exit together: total is a multiple of 32
-    int64_t l = t / (nslices * 32);
-    int64_t r = t - l * nslices * 32;
+    const int64_t r = t / (nw * 32);
+    const int l = (int)(t - r * nw * 32);
     bool neg = false;
-    if (r < n) {
-        uint64_t x = sm_draw(key, (uint64_t)l * (uint64_t)n + (uint64_t)r);
-        neg = (x >> 63) != 0;
-        W0[l * n + r] = neg ? T(-1) : T(1);
+    if (l < nvec) {
+        uint64_t v = sm_draw(key, (uint64_t)l * (uint64_t)n + (uint64_t)r);
+        neg = (v >> 63) != 0;
     }
+    if (l < ld) W0[r * ld + l] = (l < nvec) ? (neg ? T(-1) : T(1)) : T(0);
     uint32_t word = __ballot_sync(0xffffffffu, neg);
-    if ((threadIdx.x & 31) == 0) bits[l * nslices + (r >> 5)] = word;
+    if ((threadIdx.x & 31) == 0) bits[r * nw + (l >> 5)] = word;
 }
 
 __global__ void k_f64_to_f32(int64_t count, const double *__restrict__ x, float *__restrict__ y)
@@ -587,14 +614,18 @@ int spmv_f64(evsl_ctx *c, int nvec, const double *X, double *Y)
 
 int kpm_nblocks(evsl_ctx *c)
 {
+    // one wave: the KPM step keeps 4 blocks of TPB threads resident per SM (64 registers)
     int64_t need = (c->A.nslices * 32 + TPB - 1) / TPB;
-    int64_t cap = (int64_t)c->dev_sm_count * 8;
+    int64_t cap = (int64_t)c->dev_sm_count * 4;
     return (int)std::max<int64_t>(1, std::min(need, cap));
 }
 
+int kpm_ld(int nvec) { return (nvec + 1) & ~1; }
+
 static uint32_t *kpm_bits(evsl_ctx *c, int nvec, int *st)
 {
-    return (uint32_t *)ctx_ws(c, WS_TMP_STAGE, sizeof(uint32_t) * c->A.nslices * nvec, st);
+    const int nw = (nvec + 31) >> 5;
+    return (uint32_t *)ctx_ws(c, WS_TMP_STAGE, sizeof(uint32_t) * c->A.n * nw, st);
 }
 
 template <typename T>
@@ -603,8 +634,8 @@ static int kpm_init_t(evsl_ctx *c, int nvec, uint64_t seed, T *W0)
     int st = EVSL_OK;
     uint32_t *bits = kpm_bits(c, nvec, &st);
     if (st) return st;
-    int64_t total = c->A.nslices * 32 * (int64_t)nvec;
-    k_kpm_init<T><<<blocks_for(total, 256), 256, 0, c->stream>>>(c->A.n, c->A.nslices, nvec,
+    const int64_t total = c->A.n * (int64_t)(((nvec + 31) >> 5) * 32);
+    k_kpm_init<T><<<blocks_for(total, 256), 256, 0, c->stream>>>(c->A.n, nvec, kpm_ld(nvec),
                                                                  sm_key(seed, SM_STREAM_KPM), W0, bits);
     c->launches++;
     return check_launch(c, "kpm_init");
@@ -621,16 +652,16 @@ static int kpm_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xpre
     uint32_t *bits = kpm_bits(c, nvec, &st);
     if (st) return st;
     const DevMatrix &A = c->A;
-    constexpr int NC = sizeof(T) == 8 ? 2 : 4;
+    const int ld = kpm_ld(nvec);
     if (hat && A.vhat) {
         const T *hv = sizeof(T) == 8 ? (const T *)A.vhat : (const T *)A.vhat32;
-        k_kpm_step<T, NC, true><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, hv, nvec,
-                                                             bits, x, xprev, out, (T)cc, (T)sc,
-                                                             part + (int64_t)k * nblk);
+        k_kpm_step<T, true><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, hv, A.rlen, nvec,
+                                                         ld, bits, x, xprev, out, (T)cc, (T)sc,
+                                                         part + (int64_t)k * nblk);
     } else {
-        k_kpm_step<T, NC, false><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, nvec,
-                                                              bits, x, xprev, out, (T)cc, (T)sc,
-                                                              part + (int64_t)k * nblk);
+        k_kpm_step<T, false><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, A.rlen, nvec,
+                                                          ld, bits, x, xprev, out, (T)cc, (T)sc,
+                                                          part + (int64_t)k * nblk);
     }
     c->launches++;
     return check_launch(c, "kpm_step");

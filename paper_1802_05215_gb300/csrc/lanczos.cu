@@ -215,7 +215,7 @@ template <typename T>
 static int kpm_run(evsl_ctx *c, int M, int nvec, uint64_t seed, double lmin, double lmax,
                    double *mu)
 {
-    const int64_t n = c->A.n, N = n * (int64_t)nvec;
+    const int64_t n = c->A.n, N = n * (int64_t)kpm_ld(nvec);   // row-major probe blocks
     const double cc = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
     int st = EVSL_OK;
     T *W0 = (T *)ctx_ws(c, WS_W0, sizeof(T) * N, &st);
