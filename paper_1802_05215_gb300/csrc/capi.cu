@@ -167,6 +167,7 @@ void evsl_destroy(evsl_ctx *c)
     cudaStreamSynchronize(c->stream);
     prof_resolve(c);
     sell_free(c);
+    filter_graphs_clear(c);
     for (size_t i = 0; i < c->ws_ptr.size(); i++) ctx_free(c, c->ws_ptr[i], c->ws_bytes[i]);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);

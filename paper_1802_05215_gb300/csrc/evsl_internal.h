@@ -58,7 +58,17 @@ struct evsl_ctx {
     double prof_ms[EVSL_K_COUNT] = {0};
     int dev_sm_count = 0;
     std::vector<evsl_batch *> batches;  // live batches, destroyed with the context
+    // CUDA graphs of single-vector filter applications, keyed by filter, buffers and matrix
+    struct FilterGraph {
+        uint64_t key = 0;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<FilterGraph> fgraphs;
+    bool graphs_off = false;  // set when capture is not possible on the context's stream
 };
+
+// drop the cached filter graphs (they hold device addresses of the matrix and workspaces)
+void filter_graphs_clear(evsl_ctx *c);
 
 enum WsSlot {
     WS_PARTIAL = 0, WS_SCAL, WS_W0, WS_W1, WS_W2, WS_KPM_PART, WS_F32_X, WS_F32_Y,

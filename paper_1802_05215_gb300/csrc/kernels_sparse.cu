@@ -460,6 +460,7 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, co
 
 void sell_free(evsl_ctx *c)
 {
+    filter_graphs_clear(c);
     DevMatrix &A = c->A;
     ctx_free(c, A.sptr, sizeof(int64_t) * (A.nslices + 1));
     ctx_free(c, A.col, sizeof(int32_t) * A.nstored);

@@ -37,6 +37,128 @@ int h2d(evsl_ctx *c, void *dst, const void *src, size_t bytes)
 
 // Y = rho(Ahat) X on nvec columns with the three-term recurrence; one fused launch per degree.
 // B0, B1: n*nvec FP64 temporaries; fbuf: 4*n*nvec floats (FP32 mode only).  Asynchronous.
+namespace {
+
+constexpr int GRAPH_MIN_DEG = 8;   // filters of lower degree launch directly
+constexpr size_t GRAPH_CACHE = 16;  // graphs kept per context (oldest dropped first)
+
+uint64_t fnv1a(uint64_t h, const void *p, size_t len)
+{
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < len; i++) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+// Issues the recurrence of one filter application on one vector whose input already sits in
+// the second recurrence buffer (FP64: B1; FP32: f1): the same kernels, arguments and buffer
+// rotation as the direct path (from degree 2 on, the direct path also writes w_{j+1} over
+// w_{j-1}), so both give identical results.
+int issue_filter_staged(evsl_ctx *c, const evsl_polfilt *pol, double *Y, evsl_precision prec, double *B0,
+                        double *B1, float *fbuf, bool hat)
+{
+    const int64_t n = c->A.n;
+    const double cc = 0.5 * (pol->lmax + pol->lmin), d = 0.5 * (pol->lmax - pol->lmin);
+    const double *coef = pol->coef;
+    if (prec == EVSL_FP64) {
+        EVSL_TRY(cheb_step_f64(c, 0, 1, B1, nullptr, B0, Y, cc, 1.0 / d, coef[0], coef[1], hat));
+        double *prev = B1, *cur = B0;
+        for (int j = 2; j <= pol->deg; j++) {
+            EVSL_TRY(cheb_step_f64(c, 1, 1, cur, prev, prev, Y, cc, 2.0 / d, 0.0, coef[j], hat));
+            std::swap(prev, cur);
+        }
+        return EVSL_OK;
+    }
+    float *f0 = fbuf + n, *f1 = fbuf + 2 * n, *fy = fbuf + 3 * n;
+    EVSL_TRY(cheb_step_f32(c, 0, 1, f1, nullptr, f0, fy, cc, 1.0 / d, coef[0], coef[1], hat));
+    float *prev = f1, *cur = f0;
+    for (int j = 2; j <= pol->deg; j++) {
+        EVSL_TRY(cheb_step_f32(c, 1, 1, cur, prev, prev, fy, cc, 2.0 / d, 0.0, coef[j], hat));
+        std::swap(prev, cur);
+    }
+    return convert_f32_to_f64(c, n, fy, Y);
+}
+
+// Single-vector filter application through a cached CUDA graph of its deg (+1) launches; the
+// input is copied (FP64) or converted (FP32) into the second recurrence buffer first.
+// Returns 1 if graphs cannot be used here (the caller then launches directly).
+int filter_apply_graph(evsl_ctx *c, const evsl_polfilt *pol, const double *X, double *Y, evsl_precision prec,
+                       double *B0, double *B1, float *fbuf, bool hat)
+{
+    const int64_t n = c->A.n;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return 1;
+    }
+    uint64_t h = 1469598103934665603ull;
+    const void *ptrs[] = {Y, B0, B1, fbuf, c->A.sptr, c->A.col, c->A.val, c->A.val32, c->A.vhat, c->A.vhat32};
+    h = fnv1a(h, ptrs, sizeof(ptrs));
+    const int64_t meta[] = {n, pol->deg, (int64_t)prec, (int64_t)hat};
+    h = fnv1a(h, meta, sizeof(meta));
+    const double dm[] = {pol->lmin, pol->lmax};
+    h = fnv1a(h, dm, sizeof(dm));
+    h = fnv1a(h, pol->coef, sizeof(double) * (size_t)(pol->deg + 1));
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : c->fgraphs)
+        if (g.key == h) exec = g.exec;
+    // stage the input
+    cudaError_t e = cudaSuccess;
+    if (prec == EVSL_FP64)
+        e = cudaMemcpyAsync(B1, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+    else
+        EVSL_TRY(convert_f64_to_f32(c, n, X, fbuf + 2 * n));
+    if (e != cudaSuccess) return ctx_cuda(c, e, "filter input staging");
+    const int nl = pol->deg + (prec == EVSL_FP64 ? 0 : 1);
+    if (!exec) {
+        const int64_t launches0 = c->launches;
+        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->graphs_off = true;
+            return 1;
+        }
+        int st = issue_filter_staged(c, pol, Y, prec, B0, B1, fbuf, hat);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(c->stream, &graph);
+        c->launches = launches0;
+        if (st != EVSL_OK || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            if (st != EVSL_OK) return st;
+            c->graphs_off = true;
+            return 1;
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->graphs_off = true;
+            return 1;
+        }
+        if (c->fgraphs.size() >= GRAPH_CACHE) {
+            cudaGraphExecDestroy(c->fgraphs.front().exec);
+            c->fgraphs.erase(c->fgraphs.begin());
+        }
+        c->fgraphs.push_back({h, exec});
+    }
+    ProfGroup g;
+    prof_begin(c, EVSL_K_CHEB_STEP, &g);
+    e = cudaGraphLaunch(exec, c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "filter graph launch");
+    c->launches += nl;
+    prof_end(c, &g, pol->deg);
+    return EVSL_OK;
+}
+
+}  // namespace
+
+void filter_graphs_clear(evsl_ctx *c)
+{
+    for (auto &g : c->fgraphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    c->fgraphs.clear();
+}
+
 int filter_apply_dev(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const double *X, double *Y,
                evsl_precision prec, double *B0, double *B1, float *fbuf)
 {
@@ -48,6 +170,10 @@ int filter_apply_dev(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doubl
     int st = EVSL_OK;
     const bool hat = ensure_mapped(c, cc, d, &st);
     if (st) return st;
+    if (nvec == 1 && deg >= GRAPH_MIN_DEG && !c->graphs_off && X != B1 && X != B0 && X != Y) {
+        const int r = filter_apply_graph(c, pol, X, Y, prec, B0, B1, fbuf, hat);
+        if (r != 1) return r;
+    }
     ProfGroup g;
     if (prec == EVSL_FP64) {
         prof_begin(c, EVSL_K_CHEB_STEP, &g);

@@ -4,6 +4,7 @@
     python -m paper_1802_05215_gb300.profile_cases gemv      # Gram-Schmidt GEMV-T / GEMV-N
     python -m paper_1802_05215_gb300.profile_cases kpm       # KPM moment step, FP64 then FP32
     python -m paper_1802_05215_gb300.profile_cases multi     # 16-slice batched filter step, FP32
+    python -m paper_1802_05215_gb300.profile_cases fp64rate  # dense FP64 vs FP32 GEMM rate (cuBLAS)
 
 Each case runs on the 100^3 7-point Laplacian (n = 1e6, nnz = 6.94e6) and prints the number of
 kernels the library launched.
@@ -66,9 +67,32 @@ def multi():
     return ctx
 
 
-CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi}
+def fp64rate():
+    """Dense GEMM rate of the part in FP64 and FP32 (library GEMMs, CUDA-event timed): the
+    ceiling that bounds every FP64 kernel of the solver.  Prints one line per precision."""
+    import torch
+    n = 8192
+    for dt in (torch.float64, torch.float32):
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        for _ in range(3):
+            torch.matmul(a, b)
+        reps = 10 if dt == torch.float64 else 50
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) * 1e-3 / reps
+        print(f"{str(dt).split('.')[-1]} GEMM {n}^3: {s * 1e3:.2f} ms = {2 * n ** 3 / s / 1e12:.2f} TFLOP/s")
+    return None
+
+
+CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "fp64rate": fp64rate}
 
 if __name__ == "__main__":
     name = sys.argv[1] if len(sys.argv) > 1 else "cheb"
     ctx = CASES[name]()
-    print(f"{name}: ok, launches={ctx.launch_count()}")
+    if ctx is not None:
+        print(f"{name}: ok, launches={ctx.launch_count()}")
