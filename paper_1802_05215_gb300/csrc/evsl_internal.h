@@ -62,6 +62,7 @@ struct evsl_ctx {
     struct FilterGraph {
         uint64_t key = 0;
         cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;  // kernels in the graph
     };
     std::vector<FilterGraph> fgraphs;
     bool graphs_off = false;  // set when capture is not possible on the context's stream
@@ -113,7 +114,7 @@ bool ensure_mapped(evsl_ctx *c, double cc, double d, int *status);
 // Y = A X (FP64), nvec columns
 int spmv_f64(evsl_ctx *c, int nvec, const double *X, double *Y);
 // KPM: fill W0 with the probes, then steps
-// KPM probe blocks are row-major with leading dimension kpm_ld(nvec) (nvec rounded up to even)
+// KPM probe blocks are row-major with leading dimension kpm_ld(nvec) (nvec rounded up to 4)
 int kpm_ld(int nvec);
 int kpm_init_f64(evsl_ctx *c, int nvec, uint64_t seed, double *W0);
 int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0);

@@ -219,29 +219,36 @@ k_cheb_stepN(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
 }
 
 // KPM block layout: row-major, row r holding its probe values contiguously with leading
-// dimension ld = nvec rounded up to even (the padding probe stays zero); the bit-packed signs
-// are row-major too, bit (l % 32) of word bits[r * nw + l / 32] set <=> v_l[r] = -1.
-template <typename T> struct Vec2;
-template <> struct Vec2<double> { using type = double2; };
-template <> struct Vec2<float> { using type = float2; };
+// dimension ld = nvec rounded up to a multiple of 4 (the padding probes stay zero); the
+// bit-packed signs are row-major too, bit (l % 32) of word bits[r * nw + l / 32] set <=>
+// v_l[r] = -1.
+template <typename T, int PPL> struct VecN;
+template <> struct VecN<double, 2> { using type = double2; };
+template <> struct VecN<float, 2> { using type = float2; };
+template <> struct VecN<float, 4> { using type = float4; };
 
 // KPM step: the same recurrence without y, plus the moment partial sums
-// sum_l sum_r v_l[r] out_l[r].  One warp per 32-row slice, walking its rows; the lanes cover
-// the probes two at a time (vector loads, 64 probes per pass), so every gathered neighbour row
-// of the block is one coalesced load.  Grid-stride over slices with a fixed grid so that the
-// partials of one step fill exactly part[0..gridDim.x).  Each lane sums its share of one
-// slice (32 rows, 64 probes per pass) in the block's precision and adds it to an FP64 partial,
-// so the sums across slices are FP64 in both precisions (FP64 issue is 1/64 of FP32 here).
-template <typename T, bool HAT>
+// sum_l sum_r v_l[r] out_l[r].  One warp per 32-row slice, walking its rows; each lane covers
+// PPL consecutive probes with one vector load (64 probes per pass), so a row takes 64 / PPL
+// lanes and a warp works on 32 PPL / 64 rows at a time (FP64: PPL = 2, one row; FP32:
+// PPL = 4, two rows), and every gathered neighbour row of the block is one coalesced load.
+// Grid-stride over slices with a fixed grid so that the partials of one step fill exactly
+// part[0..gridDim.x).  Each lane sums its share of one slice in the block's precision and adds
+// it to an FP64 partial, so the sums across slices are FP64 in both precisions (FP64 issue is
+// 1/64 of FP32 here).
+template <typename T, bool HAT, int PPL>
 __global__ void __launch_bounds__(TPB, 4)
 k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
            const int32_t *__restrict__ col, const T *__restrict__ val, const int32_t *__restrict__ rlen,
            int nvec, int ld, const uint32_t *__restrict__ bits, const T *__restrict__ x, const T *xprev,
            T *out, T cc, T sc, double *__restrict__ part)
 {
-    using V2 = typename Vec2<T>::type;
+    using VL = typename VecN<T, PPL>::type;
+    constexpr int LPR = 64 / PPL;   // lanes per row
+    constexpr int RPI = 32 / LPR;   // rows per warp at a time
     __shared__ double red[TPB / 32];
     const int lane = threadIdx.x & 31;
+    const int sub = lane % LPR, rsub = lane / LPR;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nw = (nvec + 31) >> 5;
@@ -249,14 +256,16 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
     for (int64_t s = warp; s < nslices; s += nwarps) {
         const int64_t sbase = sptr[s];
         T smom = T(0);  // this lane's share of the slice, in the block's precision
-        for (int rr = 0; rr < 32; rr++) {
+        for (int rr0 = 0; rr0 < 32; rr0 += RPI) {
+            const int rr = rr0 + rsub;
             const int64_t r = s * 32 + rr;
-            if (r >= n) break;
-            const int len = rlen[r];
+            const int len = (r < n) ? rlen[r] : 0;
             for (int l0 = 0; l0 < nvec; l0 += 64) {
-                const int l = l0 + 2 * lane;
-                const bool act = l < nvec;
-                T a0 = T(0), a1 = T(0);
+                const int l = l0 + PPL * sub;
+                const bool act = (r < n) && (l < nvec);
+                T a[PPL];
+#pragma unroll
+                for (int q = 0; q < PPL; q++) a[q] = T(0);
                 if (len <= WREG) {
 #pragma unroll
                     for (int j = 0; j < WREG; j++)
@@ -265,9 +274,10 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                             const T v = val[e];
                             const int cj = col[e];
                             if (act) {
-                                const V2 xv = __ldg(reinterpret_cast<const V2 *>(x + (int64_t)cj * ld + l));
-                                a0 += v * xv.x;
-                                a1 += v * xv.y;
+                                T xv[PPL];
+                                *reinterpret_cast<VL *>(xv) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cj * ld + l));
+#pragma unroll
+                                for (int q = 0; q < PPL; q++) a[q] += v * xv[q];
                             }
                         }
                 } else {
@@ -276,39 +286,35 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                         const T v = val[e];
                         const int cj = col[e];
                         if (act) {
-                            const V2 xv = __ldg(reinterpret_cast<const V2 *>(x + (int64_t)cj * ld + l));
-                            a0 += v * xv.x;
-                            a1 += v * xv.y;
+                            T xv[PPL];
+                            *reinterpret_cast<VL *>(xv) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cj * ld + l));
+#pragma unroll
+                            for (int q = 0; q < PPL; q++) a[q] += v * xv[q];
                         }
                     }
                 }
                 if (act) {
                     const int64_t o = r * ld + l;
-                    V2 w;
+                    T w[PPL], pv[PPL];
+                    if (mode == 1) *reinterpret_cast<VL *>(pv) = *reinterpret_cast<const VL *>(xprev + o);
                     if (HAT) {
-                        if (mode == 1) {
-                            const V2 pv = *reinterpret_cast<const V2 *>(xprev + o);
-                            w.x = a0 - pv.x;
-                            w.y = a1 - pv.y;
-                        } else {
-                            w.x = T(0.5) * a0;
-                            w.y = T(0.5) * a1;
-                        }
+#pragma unroll
+                        for (int q = 0; q < PPL; q++) w[q] = (mode == 1) ? a[q] - pv[q] : T(0.5) * a[q];
                     } else {
-                        const V2 xo = *reinterpret_cast<const V2 *>(x + o);
-                        w.x = (a0 - cc * xo.x) * sc;
-                        w.y = (a1 - cc * xo.y) * sc;
-                        if (mode == 1) {
-                            const V2 pv = *reinterpret_cast<const V2 *>(xprev + o);
-                            w.x -= pv.x;
-                            w.y -= pv.y;
+                        T xo[PPL];
+                        *reinterpret_cast<VL *>(xo) = *reinterpret_cast<const VL *>(x + o);
+#pragma unroll
+                        for (int q = 0; q < PPL; q++) {
+                            w[q] = (a[q] - cc * xo[q]) * sc;
+                            if (mode == 1) w[q] -= pv[q];
                         }
                     }
-                    *reinterpret_cast<V2 *>(out + o) = w;
+                    *reinterpret_cast<VL *>(out + o) = *reinterpret_cast<const VL *>(w);
                     const uint32_t word = bits[r * nw + (l >> 5)];
                     const int b = l & 31;
-                    smom += ((word >> b) & 1u) ? -w.x : w.x;
-                    if (l + 1 < nvec) smom += ((word >> (b + 1)) & 1u) ? -w.y : w.y;
+#pragma unroll
+                    for (int q = 0; q < PPL; q++)
+                        if (l + q < nvec) smom += ((word >> (b + q)) & 1u) ? -w[q] : w[q];
                 }
             }
         }
@@ -326,7 +332,7 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
 }
 
 // Probes in the row-major layout: W0[r * ld + l] = sign of draw(seed, KPM, l * n + r) for
-// l < nvec, 0 for the padding probe; one warp builds one sign word of one row.
+// l < nvec, 0 for the padding probes; one warp builds one sign word of one row.
 template <typename T>
 __global__ void k_kpm_init(int64_t n, int nvec, int ld, uint64_t key, T *W0, uint32_t *bits)
 {
@@ -621,7 +627,7 @@ int kpm_nblocks(evsl_ctx *c)
     return (int)std::max<int64_t>(1, std::min(need, cap));
 }
 
-int kpm_ld(int nvec) { return (nvec + 1) & ~1; }
+int kpm_ld(int nvec) { return (nvec + 3) & ~3; }
 
 static uint32_t *kpm_bits(evsl_ctx *c, int nvec, int *st)
 {
@@ -654,15 +660,16 @@ static int kpm_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xpre
     if (st) return st;
     const DevMatrix &A = c->A;
     const int ld = kpm_ld(nvec);
+    constexpr int PPL = sizeof(T) == 8 ? 2 : 4;
     if (hat && A.vhat) {
         const T *hv = sizeof(T) == 8 ? (const T *)A.vhat : (const T *)A.vhat32;
-        k_kpm_step<T, true><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, hv, A.rlen, nvec,
-                                                         ld, bits, x, xprev, out, (T)cc, (T)sc,
-                                                         part + (int64_t)k * nblk);
+        k_kpm_step<T, true, PPL><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, hv, A.rlen,
+                                                              nvec, ld, bits, x, xprev, out, (T)cc, (T)sc,
+                                                              part + (int64_t)k * nblk);
     } else {
-        k_kpm_step<T, false><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, A.rlen, nvec,
-                                                          ld, bits, x, xprev, out, (T)cc, (T)sc,
-                                                          part + (int64_t)k * nblk);
+        k_kpm_step<T, false, PPL><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, A.rlen,
+                                                               nvec, ld, bits, x, xprev, out, (T)cc, (T)sc,
+                                                               part + (int64_t)k * nblk);
     }
     c->launches++;
     return check_launch(c, "kpm_step");

@@ -78,6 +78,66 @@ int issue_filter_staged(evsl_ctx *c, const evsl_polfilt *pol, double *Y, evsl_pr
     return convert_f32_to_f64(c, n, fy, Y);
 }
 
+// Replays the cached CUDA graph with key h, capturing it from issue() (kernel launches only,
+// on the context's stream) the first time.  The launches are timed as one filter group of
+// `degree` steps.  Returns 1 if graphs cannot be used here (the caller then launches directly).
+template <typename F>
+int launch_graph(evsl_ctx *c, uint64_t h, int degree, F issue)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return 1;
+    }
+    cudaGraphExec_t exec = nullptr;
+    int64_t nl = 0;
+    for (auto &g : c->fgraphs)
+        if (g.key == h) {
+            exec = g.exec;
+            nl = g.launches;
+        }
+    if (!exec) {
+        const int64_t launches0 = c->launches;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->graphs_off = true;
+            return 1;
+        }
+        int st = issue();
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(c->stream, &graph);
+        nl = c->launches - launches0;
+        c->launches = launches0;
+        if (st != EVSL_OK || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            if (st != EVSL_OK) return st;
+            c->graphs_off = true;
+            return 1;
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->graphs_off = true;
+            return 1;
+        }
+        if (c->fgraphs.size() >= GRAPH_CACHE) {
+            cudaGraphExecDestroy(c->fgraphs.front().exec);
+            c->fgraphs.erase(c->fgraphs.begin());
+        }
+        c->fgraphs.push_back({h, exec, nl});
+    }
+    ProfGroup g;
+    prof_begin(c, EVSL_K_CHEB_STEP, &g);
+    cudaError_t e = cudaGraphLaunch(exec, c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "filter graph launch");
+    c->launches += nl;
+    prof_end(c, &g, degree);
+    return EVSL_OK;
+}
+
 // Single-vector filter application through a cached CUDA graph of its deg (+1) launches; the
 // input is copied (FP64) or converted (FP32) into the second recurrence buffer first.
 // Returns 1 if graphs cannot be used here (the caller then launches directly).
@@ -98,56 +158,51 @@ int filter_apply_graph(evsl_ctx *c, const evsl_polfilt *pol, const double *X, do
     const double dm[] = {pol->lmin, pol->lmax};
     h = fnv1a(h, dm, sizeof(dm));
     h = fnv1a(h, pol->coef, sizeof(double) * (size_t)(pol->deg + 1));
-    cudaGraphExec_t exec = nullptr;
-    for (auto &g : c->fgraphs)
-        if (g.key == h) exec = g.exec;
     // stage the input
-    cudaError_t e = cudaSuccess;
-    if (prec == EVSL_FP64)
-        e = cudaMemcpyAsync(B1, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
-    else
+    if (prec == EVSL_FP64) {
+        cudaError_t e = cudaMemcpyAsync(B1, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "filter input staging");
+    } else {
         EVSL_TRY(convert_f64_to_f32(c, n, X, fbuf + 2 * n));
-    if (e != cudaSuccess) return ctx_cuda(c, e, "filter input staging");
-    const int nl = pol->deg + (prec == EVSL_FP64 ? 0 : 1);
-    if (!exec) {
-        const int64_t launches0 = c->launches;
-        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            c->graphs_off = true;
-            return 1;
-        }
-        int st = issue_filter_staged(c, pol, Y, prec, B0, B1, fbuf, hat);
-        cudaGraph_t graph = nullptr;
-        e = cudaStreamEndCapture(c->stream, &graph);
-        c->launches = launches0;
-        if (st != EVSL_OK || e != cudaSuccess || !graph) {
-            if (graph) cudaGraphDestroy(graph);
-            cudaGetLastError();
-            if (st != EVSL_OK) return st;
-            c->graphs_off = true;
-            return 1;
-        }
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            c->graphs_off = true;
-            return 1;
-        }
-        if (c->fgraphs.size() >= GRAPH_CACHE) {
-            cudaGraphExecDestroy(c->fgraphs.front().exec);
-            c->fgraphs.erase(c->fgraphs.begin());
-        }
-        c->fgraphs.push_back({h, exec});
     }
-    ProfGroup g;
-    prof_begin(c, EVSL_K_CHEB_STEP, &g);
-    e = cudaGraphLaunch(exec, c->stream);
-    if (e != cudaSuccess) return ctx_cuda(c, e, "filter graph launch");
-    c->launches += nl;
-    prof_end(c, &g, pol->deg);
-    return EVSL_OK;
+    return launch_graph(c, h, pol->deg, [&]() { return issue_filter_staged(c, pol, Y, prec, B0, B1, fbuf, hat); });
+}
+
+// The recurrence of a multi-slice filter application on the degree-sorted block Xs (the
+// coefficient tables at dtab, active[j] columns still running at degree j), into Ys.
+int issue_filter_multi(evsl_ctx *c, int npol, const std::vector<int> &active, int maxdeg, const double *Xs,
+                       double *Ys, const void *dtab, evsl_precision prec, bool hat, double cc, double d,
+                       double *B0, double *B1, float *fb)
+{
+    const int64_t N = c->A.n * (int64_t)npol;
+    if (prec == EVSL_FP64) {
+        const double *t64 = (const double *)dtab;
+        EVSL_TRY(cheb_step_multi_f64(c, 0, npol, Xs, nullptr, B0, Ys, cc, 1.0 / d, t64 + npol, t64, hat));
+        const double *prev = Xs;
+        double *cur = B0;
+        for (int j = 2; j <= maxdeg; j++) {
+            double *out = (j == 2) ? B1 : const_cast<double *>(prev);
+            EVSL_TRY(cheb_step_multi_f64(c, 1, active[j], cur, prev, out, Ys, cc, 2.0 / d,
+                                         t64 + (size_t)j * npol, nullptr, hat));
+            prev = cur;
+            cur = out;
+        }
+        return EVSL_OK;
+    }
+    float *fx = fb, *f0 = fb + N, *f1 = fb + 2 * N, *fy = fb + 3 * N;
+    const float *t32 = (const float *)dtab;
+    EVSL_TRY(convert_f64_to_f32(c, N, Xs, fx));
+    EVSL_TRY(cheb_step_multi_f32(c, 0, npol, fx, nullptr, f0, fy, cc, 1.0 / d, t32 + npol, t32, hat));
+    const float *prev = fx;
+    float *cur = f0;
+    for (int j = 2; j <= maxdeg; j++) {
+        float *out = (j == 2) ? f1 : const_cast<float *>(prev);
+        EVSL_TRY(cheb_step_multi_f32(c, 1, active[j], cur, prev, out, fy, cc, 2.0 / d,
+                                     t32 + (size_t)j * npol, nullptr, hat));
+        prev = cur;
+        cur = out;
+    }
+    return convert_f32_to_f64(c, N, fy, Ys);
 }
 
 }  // namespace
@@ -280,47 +335,45 @@ int filter_apply_multi_dev(evsl_ctx *c, int npol, const evsl_polfilt *pols, cons
     const double cc = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
     const bool hat = ensure_mapped(c, cc, d, &st);
     if (st) return st;
-    ProfGroup g;
     if (maxdeg == 0) {
         for (int t = 0; t < npol; t++)
             EVSL_TRY(scale_vec(c, n, Xs + (int64_t)t * n, tab[t], Ys + (int64_t)t * n));
-    } else if (prec == EVSL_FP64) {
-        double *B0 = (double *)ctx_ws(c, WS_W0, sizeof(double) * N, &st);
-        if (st) return st;
-        double *B1 = (double *)ctx_ws(c, WS_W1, sizeof(double) * N, &st);
-        if (st) return st;
-        const double *t64 = (const double *)dtab;
-        prof_begin(c, EVSL_K_CHEB_STEP, &g);
-        EVSL_TRY(cheb_step_multi_f64(c, 0, npol, Xs, nullptr, B0, Ys, cc, 1.0 / d, t64 + npol, t64, hat));
-        const double *prev = Xs;
-        double *cur = B0;
-        for (int j = 2; j <= maxdeg; j++) {
-            double *out = (j == 2) ? B1 : const_cast<double *>(prev);
-            EVSL_TRY(cheb_step_multi_f64(c, 1, active[j], cur, prev, out, Ys, cc, 2.0 / d,
-                                         t64 + (size_t)j * npol, nullptr, hat));
-            prev = cur;
-            cur = out;
-        }
-        prof_end(c, &g, maxdeg);
     } else {
-        float *fb = (float *)ctx_ws(c, WS_F32_X, sizeof(float) * 4 * N, &st);
-        if (st) return st;
-        float *fx = fb, *f0 = fb + N, *f1 = fb + 2 * N, *fy = fb + 3 * N;
-        const float *t32 = (const float *)dtab;
-        EVSL_TRY(convert_f64_to_f32(c, N, Xs, fx));
-        prof_begin(c, EVSL_K_CHEB_STEP, &g);
-        EVSL_TRY(cheb_step_multi_f32(c, 0, npol, fx, nullptr, f0, fy, cc, 1.0 / d, t32 + npol, t32, hat));
-        const float *prev = fx;
-        float *cur = f0;
-        for (int j = 2; j <= maxdeg; j++) {
-            float *out = (j == 2) ? f1 : const_cast<float *>(prev);
-            EVSL_TRY(cheb_step_multi_f32(c, 1, active[j], cur, prev, out, fy, cc, 2.0 / d,
-                                         t32 + (size_t)j * npol, nullptr, hat));
-            prev = cur;
-            cur = out;
+        double *B0 = nullptr, *B1 = nullptr;
+        float *fb = nullptr;
+        if (prec == EVSL_FP64) {
+            B0 = (double *)ctx_ws(c, WS_W0, sizeof(double) * N, &st);
+            if (st) return st;
+            B1 = (double *)ctx_ws(c, WS_W1, sizeof(double) * N, &st);
+            if (st) return st;
+        } else {
+            fb = (float *)ctx_ws(c, WS_F32_X, sizeof(float) * 4 * N, &st);
+            if (st) return st;
         }
-        prof_end(c, &g, maxdeg);
-        EVSL_TRY(convert_f32_to_f64(c, N, fy, Ys));
+        auto issue = [&]() -> int {
+            return issue_filter_multi(c, npol, active, maxdeg, Xs, Ys, dtab, prec, hat, cc, d, B0, B1, fb);
+        };
+        int r = 1;
+        if (maxdeg >= GRAPH_MIN_DEG && !c->graphs_off) {
+            uint64_t h = 1469598103934665603ull;
+            const void *ptrs[] = {Xs, Ys, dtab, B0, B1, fb, c->A.sptr, c->A.col, c->A.val, c->A.val32,
+                                  c->A.vhat, c->A.vhat32};
+            h = fnv1a(h, ptrs, sizeof(ptrs));
+            const int64_t meta[] = {-1, n, npol, maxdeg, (int64_t)prec, (int64_t)hat};
+            h = fnv1a(h, meta, sizeof(meta));
+            const double dm[] = {cc, d};
+            h = fnv1a(h, dm, sizeof(dm));
+            h = fnv1a(h, active.data(), sizeof(int) * active.size());
+            r = launch_graph(c, h, maxdeg, issue);
+        }
+        if (r == 1) {
+            ProfGroup g;
+            prof_begin(c, EVSL_K_CHEB_STEP, &g);
+            EVSL_TRY(issue());
+            prof_end(c, &g, maxdeg);
+        } else if (r != EVSL_OK) {
+            return r;
+        }
     }
     // scatter back: Y[:, perm[t]] = Ys[:, t]
     std::vector<int> inv(npol);

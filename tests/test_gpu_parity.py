@@ -389,6 +389,27 @@ def test_batch_continuous_admission_same_results_alone_and_in_mix(ctx, nat):
         assert np.array_equal(r["Y"][:r["nev"]], s["Y"][:s["nev"]])
 
 
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_filter_graph_replay_matches_block_kernel_bitwise(ctx, nat, prec):
+    # a single-vector filter application replays a cached CUDA graph of its degree launches;
+    # its result must equal, bit for bit, the same column filtered by the direct block kernel,
+    # on the first call (capture), on the second (replay), and after the matrix is replaced
+    # (the cache holds device addresses of the matrix and must be dropped)
+    import torch
+    for nx in (20, 21):
+        A = I.laplacian_3d(nx)
+        ctx.set_csr(A)
+        f = nat.cheb_filter_build(1.0, 1.3, 0.0, 12.0)
+        assert f.deg >= 8
+        X = torch.tensor(np.random.default_rng(nx).standard_normal((2, A.n)), device="cuda")
+        Y2 = torch.empty_like(X)
+        ctx.filter_apply(f, X, Y2, prec=prec)             # two columns: block kernel, direct
+        for _ in range(2):
+            Y1 = torch.full((1, A.n), np.nan, dtype=torch.float64, device="cuda")
+            ctx.filter_apply(f, X[0:1].clone(), Y1, prec=prec)
+            assert torch.equal(Y1[0], Y2[0])
+
 def test_batch_admission_respects_hbm_budget(nat):
     # a 64 MiB budget holds the matrix, the workspaces and a few jobs' bases (~6.6 MB each);
     # admission must then refuse with EVSL_ERR_NOMEM and leave the admitted jobs intact
