@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/evsl_gb300.h"
@@ -66,7 +67,15 @@ struct evsl_ctx {
     };
     std::vector<FilterGraph> fgraphs;
     bool graphs_off = false;  // set when capture is not possible on the context's stream
+    // autotuned tile shape of the multi-column filter step, per (n, columns, precision)
+    std::map<uint64_t, int> tune;
 };
+
+// autotuner of the multi-column filter step (kernels_sparse.cu): times the tile shapes on the
+// block X once per (matrix, nvec, precision); tune_lookup gives the chosen shape (0 = default)
+int tune_block_f64(evsl_ctx *c, int nvec, const double *X);
+int tune_block_f32(evsl_ctx *c, int nvec, const float *X);
+int tune_lookup(evsl_ctx *c, int nvec, int bytes);
 
 // drop the cached filter graphs (they hold device addresses of the matrix and workspaces)
 void filter_graphs_clear(evsl_ctx *c);
@@ -74,7 +83,7 @@ void filter_graphs_clear(evsl_ctx *c);
 enum WsSlot {
     WS_PARTIAL = 0, WS_SCAL, WS_W0, WS_W1, WS_W2, WS_KPM_PART, WS_F32_X, WS_F32_Y,
     WS_LAN_U, WS_LAN_Q, WS_LAN_Y, WS_LAN_Z, WS_LAN_VEC, WS_LAN_T, WS_LAN_S, WS_LAN_IDX,
-    WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_POL_V, WS_POL_W, WS_POL_B, WS_POL_S, WS_POL_Y, WS_POL_R,
+    WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_POL_V, WS_POL_W, WS_POL_B, WS_POL_S, WS_POL_Y, WS_POL_R, WS_TUNE,
     WS_COUNT
 };
 

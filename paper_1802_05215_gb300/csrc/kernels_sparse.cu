@@ -467,6 +467,7 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, co
 void sell_free(evsl_ctx *c)
 {
     filter_graphs_clear(c);
+    c->tune.clear();
     DevMatrix &A = c->A;
     ctx_free(c, A.sptr, sizeof(int64_t) * (A.nslices + 1));
     ctx_free(c, A.col, sizeof(int32_t) * A.nstored);
@@ -478,24 +479,63 @@ void sell_free(evsl_ctx *c)
     A = DevMatrix();
 }
 
+// Tile shapes of the multi-column step: NC columns per warp pass (the gathers in flight per
+// warp) and a multiplier on the number of column groups (the warps per slice).  The autotuner
+// (tune_cheb_block) picks one per (matrix, column count, precision); every shape computes each
+// column with the same operations in the same order.
+struct ChebTile {
+    int nc, gmul;
+};
+constexpr ChebTile TILES_F64[] = {{2, 1}, {1, 1}, {4, 1}, {2, 2}, {4, 2}};
+constexpr ChebTile TILES_F32[] = {{4, 1}, {2, 1}, {8, 1}, {4, 2}, {8, 2}};
+constexpr int NTILES = 5;
+
+template <typename T, int MODE, int NC, bool HAT>
+static void launch_stepN(evsl_ctx *c, int gmul, int nvec, const T *val, const T *x, const T *xprev, T *out,
+                         T *y, T cc, T sc, T c0, T cj, const T *ctab, const T *c0tab)
+{
+    const DevMatrix &A = c->A;
+    // (slice, column group) warps: about 64 warps per SM, times the tile's multiplier
+    const int npack = (nvec + NC - 1) / NC;
+    const int64_t want = (int64_t)c->dev_sm_count * 64 * gmul;
+    const int ngroups = (int)std::max<int64_t>(1, std::min<int64_t>(npack, (want + A.nslices - 1) / A.nslices));
+    const unsigned g2 = blocks_for(A.nslices * 32 * (int64_t)ngroups, TPB);
+    k_cheb_stepN<T, MODE, NC, HAT><<<g2, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec, ngroups,
+                                                             x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+}
+
+template <typename T>
+static ChebTile current_tile(evsl_ctx *c, int nvec)
+{
+    const int t = tune_lookup(c, nvec, sizeof(T));
+    return sizeof(T) == 8 ? TILES_F64[t] : TILES_F32[t];
+}
+
 template <typename T, int MODE, bool HAT>
 static void launch_cheb(evsl_ctx *c, unsigned grid, int nvec, const T *val, const T *x, const T *xprev,
                         T *out, T *y, T cc, T sc, T c0, T cj, const T *ctab, const T *c0tab)
 {
     const DevMatrix &A = c->A;
-    constexpr int NC = sizeof(T) == 8 ? 2 : 4;
-    if (nvec == 1 && !ctab)
+    if (nvec == 1 && !ctab) {
         k_cheb_step1<T, MODE, HAT><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, x, xprev,
                                                                out, y, cc, sc, c0, cj);
-    else {
-        // enough (slice, column group) warps to fill the GPU: 64 warps per SM
-        const int npack = (nvec + NC - 1) / NC;
-        const int64_t want = (int64_t)c->dev_sm_count * 64;
-        const int ngroups = (int)std::max<int64_t>(1, std::min<int64_t>(npack, (want + A.nslices - 1) / A.nslices));
-        const unsigned g2 = blocks_for(A.nslices * 32 * (int64_t)ngroups, TPB);
-        k_cheb_stepN<T, MODE, NC, HAT><<<g2, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, nvec,
-                                                                 ngroups, x, xprev, out, y, cc, sc, c0, cj,
-                                                                 ctab, c0tab);
+        return;
+    }
+    const ChebTile tl = current_tile<T>(c, nvec);
+    if constexpr (sizeof(T) == 8) {
+        if (tl.nc == 1)
+            launch_stepN<T, MODE, 1, HAT>(c, tl.gmul, nvec, val, x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+        else if (tl.nc == 4)
+            launch_stepN<T, MODE, 4, HAT>(c, tl.gmul, nvec, val, x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+        else
+            launch_stepN<T, MODE, 2, HAT>(c, tl.gmul, nvec, val, x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+    } else {
+        if (tl.nc == 2)
+            launch_stepN<T, MODE, 2, HAT>(c, tl.gmul, nvec, val, x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+        else if (tl.nc == 8)
+            launch_stepN<T, MODE, 8, HAT>(c, tl.gmul, nvec, val, x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
+        else
+            launch_stepN<T, MODE, 4, HAT>(c, tl.gmul, nvec, val, x, xprev, out, y, cc, sc, c0, cj, ctab, c0tab);
     }
 }
 
@@ -617,6 +657,99 @@ int cheb_step_f32(evsl_ctx *c, int mode, int nvec, const float *x, const float *
 int spmv_f64(evsl_ctx *c, int nvec, const double *X, double *Y)
 {
     return cheb_step_t<double>(c, 2, nvec, X, nullptr, Y, nullptr, 0.0, 1.0, 0.0, 0.0, c->A.val, false);
+}
+
+// ------------------------------------------------------------------------------------------
+// Autotuner of the multi-column filter step.  For a (matrix, column count, precision) seen for
+// the first time, every tile shape runs the plain block SpMV (mode 2) on the caller's block
+// into a scratch block: one untimed launch, then three timed with CUDA events; the fastest is
+// kept in the context (cleared when the matrix changes).  Must not run while the stream is
+// being captured.
+// column counts are bucketed by powers of two; a count whose bucket has not been timed uses
+// the nearest timed bucket above it (the batch's full width), else the default shape
+static int tune_bucket(int nvec)
+{
+    int b = 1;
+    while (b < nvec && b < (1 << 20)) b <<= 1;
+    return b;
+}
+
+static uint64_t tune_key(int64_t n, int bucket, int bytes)
+{
+    return ((uint64_t)n << 24) ^ ((uint64_t)bucket << 4) ^ (uint64_t)bytes;
+}
+
+int tune_lookup(evsl_ctx *c, int nvec, int bytes)
+{
+    if (c->tune.empty()) return 0;
+    for (int b = tune_bucket(nvec); b <= (1 << 20); b <<= 1) {
+        auto it = c->tune.find(tune_key(c->A.n, b, bytes));
+        if (it != c->tune.end()) return it->second;
+    }
+    return 0;
+}
+
+template <typename T>
+static int tune_block_t(evsl_ctx *c, int nvec, const T *X, const T *val)
+{
+    const uint64_t key = tune_key(c->A.n, tune_bucket(nvec), sizeof(T));
+    if (c->tune.count(key)) return EVSL_OK;
+    int st = EVSL_OK;
+    T *scratch = (T *)ctx_ws(c, WS_TUNE, sizeof(T) * c->A.n * (size_t)nvec, &st);
+    if (st) return st;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return ctx_cuda(c, cudaGetLastError(), "tune event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return ctx_cuda(c, cudaGetLastError(), "tune event");
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    float times[NTILES] = {0};
+    for (int t = 0; t < NTILES && st == EVSL_OK; t++) {
+        c->tune[key] = t;
+        for (int rep = 0; rep < 4 && st == EVSL_OK; rep++) {
+            if (rep == 1) cudaEventRecord(e0, c->stream);
+            launch_cheb<T, 2, false>(c, 0, nvec, val, X, nullptr, scratch, nullptr, T(0), T(1), T(0), T(0), nullptr,
+                                     nullptr);
+            c->launches++;
+            st = check_launch(c, "tune");
+        }
+        cudaEventRecord(e1, c->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) st = ctx_cuda(c, e, "tune");
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        times[t] = ms / 3.0f;
+        if (st == EVSL_OK && ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune[key] = best;
+    const char *venv = getenv("EVSL_VERBOSE");
+    if (venv && venv[0] == '1') {
+        const ChebTile *tl = sizeof(T) == 8 ? TILES_F64 : TILES_F32;
+        fprintf(stderr, "[evsl] tune %s n=%lld columns<=%d:", sizeof(T) == 8 ? "fp64" : "fp32",
+                (long long)c->A.n, tune_bucket(nvec));
+        for (int t = 0; t < NTILES; t++) fprintf(stderr, " (nc %d, x%d) %.1f us", tl[t].nc, tl[t].gmul, times[t] * 1e3f);
+        fprintf(stderr, " -> (nc %d, x%d)\n", tl[best].nc, tl[best].gmul);
+    }
+    return st;
+}
+
+int tune_block_f64(evsl_ctx *c, int nvec, const double *X)
+{
+    if (nvec < 2) return EVSL_OK;
+    return tune_block_t<double>(c, nvec, X, c->A.val);
+}
+
+int tune_block_f32(evsl_ctx *c, int nvec, const float *X)
+{
+    if (nvec < 2) return EVSL_OK;
+    return tune_block_t<float>(c, nvec, X, c->A.val32);
 }
 
 int kpm_nblocks(evsl_ctx *c)

@@ -225,6 +225,11 @@ int filter_apply_dev(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doubl
     int st = EVSL_OK;
     const bool hat = ensure_mapped(c, cc, d, &st);
     if (st) return st;
+    if (nvec > 1) {
+        // tile shape of the block step (timed once per matrix, width and precision)
+        if (prec == EVSL_FP64) EVSL_TRY(tune_block_f64(c, nvec, X));
+        else EVSL_TRY(tune_block_f32(c, nvec, fbuf));
+    }
     if (nvec == 1 && deg >= GRAPH_MIN_DEG && !c->graphs_off && X != B1 && X != B0 && X != Y) {
         const int r = filter_apply_graph(c, pol, X, Y, prec, B0, B1, fbuf, hat);
         if (r != 1) return r;
@@ -350,6 +355,9 @@ int filter_apply_multi_dev(evsl_ctx *c, int npol, const evsl_polfilt *pols, cons
             fb = (float *)ctx_ws(c, WS_F32_X, sizeof(float) * 4 * N, &st);
             if (st) return st;
         }
+        // tile shape of the block step (timed once per matrix, width and precision)
+        if (prec == EVSL_FP64) EVSL_TRY(tune_block_f64(c, npol, Xs));
+        else EVSL_TRY(tune_block_f32(c, npol, fb));
         auto issue = [&]() -> int {
             return issue_filter_multi(c, npol, active, maxdeg, Xs, Ys, dtab, prec, hat, cc, d, B0, B1, fb);
         };

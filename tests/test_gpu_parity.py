@@ -182,6 +182,20 @@ def test_cheblantr_laplacian(ctx, nat, oracle_mod, case):
     assert np.linalg.norm(P - Po, 2) <= 1e-7
 
 
+def test_cheblantr_stats_count_filter_matvecs(ctx, nat):
+    # matvec accounting: every Lanczos step applies the degree-d filter once, i.e. d products
+    # with A, so nmv = deg * niter; the timings are non-negative and fit in the total
+    A = I.laplacian_2d(40)
+    ctx.set_csr(A)
+    f = nat.cheb_filter_build(0.5, 0.8, 0.0, 8.0)
+    r = ctx.chebLanTr(0.5, 0.8, f, m=120)
+    st = r["stats"]
+    assert r["status"] == 0 and st["niter"] > 0
+    assert st["nmv"] == f.deg * st["niter"]
+    assert min(st["t_filter"], st["t_orth"], st["t_restart"]) >= 0.0
+    assert st["t_filter"] + st["t_orth"] + st["t_restart"] <= st["t_total"] * 1.05 + 1e-3
+
+
 @pytest.mark.parametrize("a,b", [(-1.0, 1.0), (3.0, 5.0)])
 def test_cheblantr_anderson_bruteforce(ctx, nat, oracle_mod, a, b):
     A = I.anderson_3d(7, 4.0, 0)
