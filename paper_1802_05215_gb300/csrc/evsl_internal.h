@@ -174,9 +174,6 @@ int gemm_nn(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t lda,
 // C -= A B (same shapes as gemm_nn)
 int gemm_nn_sub(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t lda,
                 const double *B, int64_t ldb, double *C, int64_t ldc);
-// Out[:, j] = Z[:, j] + coef[j] X[:, j], coef device (Out may alias X)
-int axpy_cols(evsl_ctx *c, int64_t n, int k, const double *coef, const double *X, const double *Z,
-              double *Out);
 // Y[:, j] *= scale[j] (rows x k, ld rows), scale device
 int colscale(evsl_ctx *c, int64_t rows, int k, double *Y, const double *scale);
 // C (p x q, ldc) = A^T B, A: n x p (lda), B: n x q (ldb); split over rows, fixed-order sums

@@ -237,15 +237,6 @@ __global__ void k_colscale(int64_t n, int k, double *__restrict__ Y, const doubl
     if (i < n && j < k) Y[(int64_t)j * n + i] *= 1.0 / sqrt(nrm2[j]);
 }
 
-// Out[:, j] = Z[:, j] + coef[j] X[:, j] (Out may alias X)
-__global__ void k_axpy_cols(int64_t n, const double *__restrict__ coef, const double *X,
-                            const double *__restrict__ Z, double *Out)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int j = blockIdx.y;
-    if (i < n) Out[(int64_t)j * n + i] = Z[(int64_t)j * n + i] + coef[j] * X[(int64_t)j * n + i];
-}
-
 // Y[:, j] *= scale[j] (columns of length rows)
 __global__ void k_colscale_by(int64_t rows, double *__restrict__ Y, const double *__restrict__ scale)
 {
@@ -744,15 +735,6 @@ int gemm_nn_sub(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t l
     k_gemm_nn<true><<<grid, 256, 0, c->stream>>>(n, l, k, A, lda, B, ldb, C, ldc);
     c->launches++;
     return check_launch(c, "gemm_nn_sub");
-}
-
-int axpy_cols(evsl_ctx *c, int64_t n, int k, const double *coef, const double *X, const double *Z,
-              double *Out)
-{
-    if (k <= 0) return EVSL_OK;
-    k_axpy_cols<<<dim3(nblk(n, 256), k), 256, 0, c->stream>>>(n, coef, X, Z, Out);
-    c->launches++;
-    return check_launch(c, "axpy_cols");
 }
 
 int colscale(evsl_ctx *c, int64_t rows, int k, double *Y, const double *scale)
