@@ -129,7 +129,13 @@ int evsl_cheb_filter_build(double a, double b, double lmin, double lmax,
 
 /* Filter application (Eq. (2.4) with the three-term Chebyshev recurrence): Y = rho(Ahat) X for
  * nvec columns.  X and Y are DEVICE pointers to n x nvec column-major FP64 blocks (Y must not
- * overlap X).  prec = EVSL_FP32 runs the recurrence in FP32 (X/Y stay FP64). */
+ * overlap X).  prec = EVSL_FP32 runs the recurrence in FP32 (X/Y stay FP64).
+ * Execution: a single column of degree >= 8 replays a CUDA graph of the degree launches that the
+ * context captures on first use and caches (keyed by filter, buffers and matrix; dropped by
+ * evsl_set_csr and evsl_destroy).  The first block of a given width on a matrix times five tile
+ * shapes of the block kernel once (synchronously) and keeps the fastest; results do not depend
+ * on the shape.  Neither happens while the context's stream is being captured by the caller
+ * (then the launches are issued directly). */
 int evsl_filter_apply(evsl_ctx *ctx, const evsl_polfilt *pol, int nvec, const double *X,
                       double *Y, evsl_precision prec);
 
@@ -174,7 +180,14 @@ int evsl_filter_apply_noalloc(evsl_ctx *ctx, const evsl_polfilt *pol, int nvec, 
  * Outputs: *nev pairs, eigenvalues ascending in lam[cap] and res[cap] (relative residuals) on
  * the HOST, eigenvectors in Y (n x cap column-major), which may be host or device memory
  * (detected).  If more than cap pairs converge: EVSL_ERR_CAPACITY, *nev = cap, outputs hold
- * the first cap found. */
+ * the first cap found.
+ * prec = EVSL_FP32 (not in the paper): the filter runs in FP32 and everything else in FP64.  The
+ * Lanczos phase then locks at max(tol, 1e-6) (relaxed up to 1e-4 if candidates stall) in the slice
+ * widened by that level times ||A||, and an FP64 polish (restarted block Krylov iteration with
+ * the FP64 filter, Rayleigh-Ritz with A on the converged Ritz vectors of rho) brings the pairs to
+ * tol and decides membership; pairs still above tol after the polish are dropped and the call
+ * returns EVSL_ERR_NOCONV.  The polish holds about 6 n (p + max(16, p/4)) doubles of workspace
+ * for p locked pairs. */
 typedef struct {
     int m;                  /* Krylov dimension before a restart                        */
     int maxit;              /* limit on Lanczos steps (0 = 20*m)                        */
