@@ -694,6 +694,11 @@ static int tune_block_t(evsl_ctx *c, int nvec, const T *X, const T *val)
 {
     const uint64_t key = tune_key(c->A.n, tune_bucket(nvec), sizeof(T));
     if (c->tune.count(key)) return EVSL_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return EVSL_OK;  // the caller is capturing: keep the default shape, time nothing
+    }
     int st = EVSL_OK;
     T *scratch = (T *)ctx_ws(c, WS_TUNE, sizeof(T) * c->A.n * (size_t)nvec, &st);
     if (st) return st;
