@@ -62,6 +62,9 @@ def _load():
         _lib.orc_cheblantr.restype = i32
         _lib.orc_cheblantr.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d,
                                        i32, i32, i32, d, d, u64, i32, P, P, P, P, P]
+        _lib.orc_cheblannr.restype = i32
+        _lib.orc_cheblannr.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d,
+                                       i32, i32, d, d, u64, i32, P, P, P, P, P]
     return _lib
 
 
@@ -173,6 +176,26 @@ def reorth(z: np.ndarray, B: np.ndarray) -> int:
     order): CGS with the DGKS test, at most two passes (Sec. 2.3).  Returns the passes."""
     assert z.flags.c_contiguous and B.flags.f_contiguous and z.dtype == B.dtype == np.float64
     return int(_load().orc_reorth_cgs(len(z), _p(z), _p(B), B.shape[1]))
+
+
+def cheblannr(A, a, b, pol, m=200, ncycle=10, tol=1e-8, tau1=1e-10, seed=0, cap=None,
+              right_closed=True):
+    """Filtered non-restart Lanczos (ChebLanNr) with a basis of at most m vectors.  Returns a
+    dict (niter, nmv, extractions, npass in place of the restart statistics)."""
+    cap = cap or m
+    lam = np.empty(cap)
+    res = np.empty(cap)
+    Y = np.empty((A.n, cap), order="F")
+    nev = C.c_int()
+    stats = np.zeros(4, dtype=np.int64)
+    coef = np.ascontiguousarray(pol["coef"], dtype=np.float64)
+    st = _load().orc_cheblannr(*_csr_args(A), a, b, int(right_closed), pol["lmin"], pol["lmax"],
+                               len(coef) - 1, _p(coef), pol["bar"], m, ncycle, tol, tau1, seed, cap,
+                               C.byref(nev), _p(lam), _p(Y), _p(res), _p(stats))
+    k = nev.value
+    return dict(status=st, nev=k, lam=lam[:k].copy(), Y=Y[:, :k].copy(), res=res[:k].copy(),
+                niter=int(stats[0]), nmv=int(stats[1]), extractions=int(stats[2]),
+                npass=int(stats[3]))
 
 
 def cheblantr(A, a, b, pol, m=100, maxit=None, ncycle=10, tol=1e-8, tau1=1e-10, seed=0,

@@ -890,3 +890,155 @@ done:
     free(u); free(Au); free(theta); free(S); free(Tk); free(trv); free(trtheta); free(trs);
     return status;
 }
+
+/* Filtered non-restart Lanczos (ChebLanNr; the paper names a "simple non-restart Lanczos
+ * algorithm", Sec. 2.3, and times it in Tables 2 and 4, but prints no listing).  READING:
+ * Algorithm 2 without restarts and without locking.  One Krylov basis of rho(Ahat) is built
+ * with full reorthogonalisation (CGS, DGKS second pass), up to m vectors, from the seeded start
+ * vector.  Every Ncycle steps the sum t of the Ritz values >= bar is formed (the same test as
+ * Algorithm 2's early restart).  When it is stable (|t - t_old| < tau1 max(1, |t|) with at least
+ * one value >= bar) the candidate Ritz pairs (theta >= bar) are extracted: u = Q y normalised,
+ * lambda = u^T A u, pairs outside the slice dropped.  If every remaining pair has
+ * ||A u - lambda u|| <= tol ||A|| the run stops with them.  Otherwise the same basis is extended
+ * and tested again (t_old is reset).  A test with no Ritz value >= bar after one without any,
+ * once max(2 Ncycle, m/4) steps are done, ends the run with an empty result.  After m steps the
+ * converged in-slice pairs are returned, with status -4 if some in-slice candidate did not
+ * converge.  A breakdown (beta <= 1e-13 ||y||) continues with a fresh seeded vector orthogonal
+ * to the basis and a zero coupling, as in orc_cheblantr.  stats: its, nmv, extractions, passes. */
+int orc_cheblannr(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                  double a, double b, int right_closed, double lmin, double lmax,
+                  int deg, const double *coef, double bar,
+                  int m, int ncycle, double tol, double tau1, uint64_t seed,
+                  int cap, int *nev, double *lam, double *Y, double *res, long *stats)
+{
+    orc_csr A = {n, rp, ci, v};
+    orc_filt F = {&A, 0.5 * (lmax + lmin), 0.5 * (lmax - lmin), deg, coef, NULL, NULL, NULL, 0};
+    F.w0 = malloc(sizeof(double) * n);
+    F.w1 = malloc(sizeof(double) * n);
+    F.w2 = malloc(sizeof(double) * n);
+    double normA = fmax(fabs(lmin), fabs(lmax));
+    if (m > n) m = (int)n;
+    double *Q = calloc((size_t)n * (m + 1), sizeof(double));
+    double *T = calloc((size_t)(m + 1) * (m + 1), sizeof(double));
+    double *Tk = malloc(sizeof(double) * (size_t)(m + 1) * (m + 1));
+    double *S = malloc(sizeof(double) * (size_t)(m + 1) * (m + 1));
+    double *theta = malloc(sizeof(double) * (m + 1));
+    double *y = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+    double *u = malloc(sizeof(double) * n), *Au = malloc(sizeof(double) * n);
+    int its = 0, status = 0, found = 0, extractions = 0, done = 0;
+    long npass = 0;
+    uint64_t fresh_index = 0;
+    double t_old = 0.0;
+    int have_old = 0, prev_nabove = 0;
+
+    orc_fresh_vector(n, seed, fresh_index++, Q, NULL, 0, NULL, 0);
+    for (int i = 0; i < m && !done; i++) {
+        its++;
+        double *qi = Q + (size_t)i * n;
+        orc_apply_filter(&F, qi, y);
+        for (int64_t r = 0; r < n; r++) z[r] = y[r];
+        if (i > 0) {
+            double bi = AT(T, i - 1, i, m + 1);
+            const double *qp = Q + (size_t)(i - 1) * n;
+            for (int64_t r = 0; r < n; r++) z[r] -= bi * qp[r];
+        }
+        double alpha = orc_dot(n, qi, z);
+        for (int64_t r = 0; r < n; r++) z[r] -= alpha * qi[r];
+        npass += orc_reorth(n, z, NULL, 0, Q, i + 1);
+        AT(T, i, i, m + 1) = alpha;
+        double beta = orc_nrm2(n, z);
+        double *qn = Q + (size_t)(i + 1) * n;
+        if (beta <= 1e-13 * orc_nrm2(n, y)) {
+            orc_fresh_vector(n, seed, fresh_index++, qn, NULL, 0, Q, i + 1);
+            beta = 0.0;
+        } else {
+            for (int64_t r = 0; r < n; r++) qn[r] = z[r] / beta;
+        }
+        AT(T, i, i + 1, m + 1) = beta;
+        AT(T, i + 1, i, m + 1) = beta;
+        int k = i + 1;
+        int extract = (k == m);
+        if (k % ncycle == 0 && k < m) {
+            for (int jj = 0; jj < k; jj++)
+                for (int ii = 0; ii < k; ii++) AT(Tk, ii, jj, k) = AT(T, ii, jj, m + 1);
+            orc_syev(k, Tk, theta, NULL);
+            double t_new = 0.0;
+            int nabove = 0;
+            for (int jj = 0; jj < k; jj++)
+                if (theta[jj] >= bar) { t_new += theta[jj]; nabove++; }
+            int min_empty = (2 * ncycle > m / 4) ? 2 * ncycle : m / 4;
+            if (have_old && nabove == 0 && prev_nabove == 0 && k >= min_empty) {
+                done = 1;                                    /* empty slice */
+                break;
+            }
+            if (have_old && nabove > 0 && fabs(t_new - t_old) < tau1 * fmax(1.0, fabs(t_new))) extract = 1;
+            t_old = t_new;
+            prev_nabove = nabove;
+            have_old = 1;
+        }
+        if (!extract) continue;
+        /* candidate Ritz pairs of T_k, largest theta first */
+        extractions++;
+        for (int jj = 0; jj < k; jj++)
+            for (int ii = 0; ii < k; ii++) AT(Tk, ii, jj, k) = AT(T, ii, jj, m + 1);
+        orc_syev(k, Tk, theta, S);
+        int nconv = 0, nunconv = 0;
+        for (int jj = k - 1; jj >= 0; jj--) {
+            if (theta[jj] < bar) break;
+            const double *s = S + (size_t)jj * k;
+            for (int64_t r = 0; r < n; r++) {
+                double acc = 0.0;
+                for (int p = 0; p < k; p++) acc += Q[(size_t)p * n + r] * s[p];
+                u[r] = acc;
+            }
+            double nu = orc_nrm2(n, u);
+            for (int64_t r = 0; r < n; r++) u[r] /= nu;
+            orc_matvec(&A, u, Au);
+            double lamj = orc_dot(n, u, Au);
+            int inside = (lamj >= a) && (right_closed ? (lamj <= b) : (lamj < b));
+            if (!inside) continue;
+            for (int64_t r = 0; r < n; r++) Au[r] -= lamj * u[r];
+            double rj = orc_nrm2(n, Au) / normA;
+            if (rj > tol) { nunconv++; continue; }
+            if (nconv >= cap) { status = -5; break; }
+            if (Y) memcpy(Y + (size_t)nconv * n, u, sizeof(double) * n);
+            lam[nconv] = lamj;
+            res[nconv] = rj;
+            nconv++;
+        }
+        found = nconv;
+        if (status == -5) break;
+        if (nunconv == 0 || k == m) {
+            if (nunconv > 0) status = -4;
+            done = 1;
+            break;
+        }
+        have_old = 0;                                        /* extend the same basis */
+    }
+    /* sort ascending (selection sort), eigenvectors along */
+    for (int i = 0; i < found; i++) {
+        int best = i;
+        for (int j = i + 1; j < found; j++)
+            if (lam[j] < lam[best]) best = j;
+        if (best != i) {
+            double t = lam[i]; lam[i] = lam[best]; lam[best] = t;
+            t = res[i]; res[i] = res[best]; res[best] = t;
+            if (Y)
+                for (int64_t r = 0; r < n; r++) {
+                    t = Y[(size_t)i * n + r];
+                    Y[(size_t)i * n + r] = Y[(size_t)best * n + r];
+                    Y[(size_t)best * n + r] = t;
+                }
+        }
+    }
+    *nev = found;
+    if (stats) {
+        stats[0] = its;
+        stats[1] = F.nmv;
+        stats[2] = extractions;
+        stats[3] = npass;
+    }
+    free(F.w0); free(F.w1); free(F.w2); free(Q); free(T); free(Tk); free(S); free(theta);
+    free(y); free(z); free(u); free(Au);
+    return status;
+}

@@ -328,6 +328,49 @@ def test_cheblantr_anderson_bruteforce(oracle_mod, a, b):
     _check_eigs(A, r, ex)
 
 
+
+# ---------------------------------------------------------------- filtered non-restart Lanczos
+@pytest.mark.parametrize("case", [("2d", 20, 1.0, 1.6), ("2d", 40, 0.5, 0.8), ("3d", 12, 0.8, 1.6)])
+def test_cheblannr_against_closed_form(oracle_mod, case):
+    # one Krylov space finds every copy of the Laplacians' multiple eigenvalues (multiplicity 2
+    # in 2-D, up to 6 in 3-D): the copies beyond the first grow from rounding in the basis
+    kind, nx, a, b = case
+    A = I.laplacian_2d(nx) if kind == "2d" else I.laplacian_3d(nx)
+    e = lap_eigs(2 if kind == "2d" else 3, nx)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    ex = e[(e >= a) & (e <= b)]
+    r = oracle_mod.cheblannr(A, a, b, pol, m=max(6 * len(ex), 200))
+    assert r["status"] == 0
+    _check_eigs(A, r, ex)
+    assert r["nmv"] == r["niter"] * (len(pol["coef"]) - 1)
+
+
+@pytest.mark.parametrize("a,b", [(-1.0, 1.0), (3.0, 5.0), (6.0, 6.5)])
+def test_cheblannr_anderson_bruteforce(oracle_mod, a, b):
+    A = I.anderson_3d(7, 4.0, 0)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    ex = ev[(ev >= a) & (ev <= b)]
+    r = oracle_mod.cheblannr(A, a, b, pol, m=max(6 * len(ex), 200))
+    assert r["status"] == 0
+    _check_eigs(A, r, ex)
+
+
+def test_cheblannr_short_basis_reports_noconv(oracle_mod):
+    # a basis too short to converge every pair returns the converged ones and status -4
+    A = I.laplacian_2d(40)
+    e = lap_eigs(2, 40)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(0.5, 0.8, lo, hi)
+    r = oracle_mod.cheblannr(A, 0.5, 0.8, pol, m=30)
+    assert r["status"] == -4 and r["niter"] == 30 and r["nev"] < 40
+    ex = e[(e >= 0.5) & (e <= 0.8)]
+    for lam in r["lam"]:
+        assert np.min(np.abs(ex - lam)) <= 1e-9 * max(1.0, abs(lam))
+    assert np.all(r["res"] <= 1e-8)
+
 def test_cheblantr_half_open_slices_partition(oracle_mod):
     # adjacent half-open slices [a, cut) and [cut, b] neither lose nor duplicate eigenvalues
     # (cut midway between two distinct eigenvalues, so rounding cannot decide membership)
