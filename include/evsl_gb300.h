@@ -214,6 +214,23 @@ int evsl_chebLanTr(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol,
                    const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
                    double *res, evsl_stats *stats);
 
+/* Filtered non-restart Lanczos (ChebLanNr, the variant the paper times in Tables 2 and 4; the
+ * paper gives it no listing, and this is Algorithm 2 without restarts or locking).  One Krylov
+ * basis of rho(A) with full reorthogonalisation grows up to opts->m vectors (opts->maxit is not
+ * used).  Every ncycle steps the sum of the Ritz values >= pol->bar is formed; when it is stable
+ * (relative change < tau1) the candidates are extracted as in evsl_chebLanTr (Rayleigh quotients
+ * with A, pairs outside the slice dropped).  If every in-slice candidate has
+ * ||A u - lambda u|| <= tol ||A|| the run returns them; otherwise the same basis keeps growing.
+ * With a full basis the converged in-slice pairs are returned and the status is EVSL_ERR_NOCONV
+ * if some in-slice candidate did not converge.  A slice with no Ritz value >= bar at two
+ * consecutive tests after max(2 ncycle, m/4) steps returns 0 pairs.  Arguments, outputs,
+ * EVSL_ERR_CAPACITY and the FP32 filter mode are as in evsl_chebLanTr; stats->nrestart counts
+ * the extractions.  Device memory: about 2 n (m + 1) doubles for the basis and the Ritz block,
+ * plus n cap for the result. */
+int evsl_chebLanNr(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol,
+                   const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
+                   double *res, evsl_stats *stats);
+
 /* Several slices of one matrix solved together (Sec. 2.6: slices are independent; here they
  * share the GPU instead of separate processes).  Each job is one slice with its own filter,
  * Krylov dimension and outputs; the slices advance in lockstep and every Lanczos step applies

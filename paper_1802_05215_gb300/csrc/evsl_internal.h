@@ -213,7 +213,7 @@ evsl_ctx *batch_ctx(evsl_batch *bt);
 int drv_bounds(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax);
 int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
                   const evsl_lan_opts *o, int cap, int *nev, double *lam, double *Y,
-                  double *res, evsl_stats *st);
+                  double *res, evsl_stats *st, bool nonrestart = false);
 int drv_filter_apply(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const double *X,
                      double *Y, evsl_precision prec);
 int drv_filter_apply_multi(evsl_ctx *c, int npol, const evsl_polfilt *pols, const double *X,

@@ -62,12 +62,15 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b)
 
 class SliceSolver {
 public:
+    // nonrestart: the non-restart variant (ChebLanNr): one basis of at most m vectors, no locking
+    // or thick restart; see end_cycle_nr
     SliceSolver(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts &o,
-                int m, int cap, bool right_closed)
-        : c_(c), n_(c->A.n), a_(a), b_(b), pol_(pol), o_(o), cap_(cap), right_closed_(right_closed)
+                int m, int cap, bool right_closed, bool nonrestart = false)
+        : c_(c), n_(c->A.n), a_(a), b_(b), pol_(pol), o_(o), cap_(cap), right_closed_(right_closed),
+          nonrestart_(nonrestart)
     {
         m_ = std::min<int64_t>(m, n_);
-        maxit_ = o.maxit > 0 ? o.maxit : 20 * m_;
+        maxit_ = nonrestart ? m_ : (o.maxit > 0 ? o.maxit : 20 * m_);
         ncycle_ = o.ncycle > 0 ? o.ncycle : 10;
         tol_ = o.tol > 0 ? o.tol : 1e-8;
         tau1_ = o.tau1 > 0 ? o.tau1 : 1e-10;
@@ -134,6 +137,11 @@ public:
         }
         bool stop_cycle = false;
         EVSL_TRY(lanczos_step(y, &stop_cycle));
+        if (nonrestart_) {
+            if (stop_cycle || i_ + 1 >= m_) EVSL_TRY(end_cycle_nr(i_ + 1 >= m_));
+            if (!done_) i_++;
+            return EVSL_OK;
+        }
         if (stop_cycle || its_ > maxit_ || i_ + 1 >= m_) return end_cycle();
         i_++;
         return EVSL_OK;
@@ -364,6 +372,131 @@ private:
         return EVSL_OK;
     }
 
+    // Ritz pairs of T_k with theta >= bar (largest first): their vectors Q S, normalised, go to
+    // Yt (n x ncand0); lam = u^T A u, res = ||A u - lam u||^2, slast = last row of S.
+    struct Cands {
+        int ncand0 = 0, sweeps = 0;
+        double betak = 0.0;
+        std::vector<double> w, lam, res, slast;
+        std::vector<int> order;
+    };
+
+    int ritz_candidates(int k, double *Yt, Cands *cd)
+    {
+        int st = EVSL_OK;
+        const int zcols = std::min(m_, 128);
+        double *Z = (double *)ctx_ws(c_, WS_LAN_Z, sizeof(double) * n_ * zcols, &st);
+        if (st) return st;
+        const int Mk = k + (k & 1) < 2 ? 2 : k + (k & 1);
+        double *Vj = (double *)ctx_ws(c_, WS_LAN_T, sizeof(double) * (size_t)Mk * Mk, &st);
+        if (st) return st;
+        int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * (size_t)(2 * (m_ + 1) + 8), &st);
+        if (st) return st;
+        double *vd = (double *)ctx_ws(c_, WS_LAN_G, sizeof(double) * 3 * (size_t)(m_ + 1), &st);
+        if (st) return st;
+        double *lamd = vd, *resd = vd + (m_ + 1), *nrmd = vd + 2 * (m_ + 1);
+        std::vector<double> Tk((size_t)k * k);
+        cd->w.assign(k, 0.0);
+        for (int j = 0; j < k; j++)
+            for (int i = 0; i < k; i++) Tk[(size_t)j * k + i] = t(i, j);
+        int ldv = 0;
+        // jacobi_eig keeps its working copy in WS_LAN_S; the candidate block reuses it afterwards
+        EVSL_TRY(jacobi_eig(c_, k, Tk.data(), cd->w.data(), Vj, &ldv, &cd->sweeps));
+        double *Sd = (double *)ctx_ws(c_, WS_LAN_S, sizeof(double) * (size_t)Mk * Mk, &st);
+        if (st) return st;
+        cd->betak = t(k - 1, k);
+        cd->order.resize(k);
+        std::iota(cd->order.begin(), cd->order.end(), 0);
+        const std::vector<double> &w = cd->w;
+        std::sort(cd->order.begin(), cd->order.end(), [&](int x, int y) { return w[x] > w[y]; });
+        int ncand0 = 0;
+        while (ncand0 < k && w[cd->order[ncand0]] >= bar_) ncand0++;
+        cd->ncand0 = ncand0;
+        cd->lam.assign(ncand0, 0.0);
+        cd->res.assign(ncand0, 0.0);
+        cd->slast.assign(ncand0, 0.0);
+        if (ncand0 == 0) return EVSL_OK;
+        EVSL_TRY(h2d(c_, idx, cd->order.data(), sizeof(int) * ncand0));
+        EVSL_TRY(gather_cols(c_, k, ncand0, Vj, ldv, idx, Sd, k));
+        ProfGroup g;
+        prof_begin(c_, EVSL_K_RITZ_GEMM, &g);
+        EVSL_TRY(gemm_nn(c_, n_, ncand0, k, Q_, n_, Sd, k, Yt, n_));
+        prof_end(c_, &g, 1);
+        EVSL_TRY(coldot(c_, n_, ncand0, Yt, n_, Yt, n_, nrmd));
+        EVSL_TRY(colscale_inv_sqrt(c_, n_, ncand0, Yt, nrmd));
+        for (int j0 = 0; j0 < ncand0; j0 += zcols) {
+            int nc = std::min(zcols, ncand0 - j0);
+            EVSL_TRY(spmv_f64(c_, nc, Yt + (int64_t)j0 * n_, Z));
+            EVSL_TRY(coldot(c_, n_, nc, Yt + (int64_t)j0 * n_, n_, Z, n_, lamd + j0));
+            EVSL_TRY(colres2(c_, n_, nc, Z, Yt + (int64_t)j0 * n_, n_, lamd + j0, resd + j0));
+        }
+        EVSL_TRY(d2h(c_, cd->lam.data(), lamd, sizeof(double) * ncand0));
+        EVSL_TRY(d2h(c_, cd->res.data(), resd, sizeof(double) * ncand0));
+        cudaError_t e = cudaMemcpy2DAsync(cd->slast.data(), sizeof(double), Sd + (k - 1), sizeof(double) * k,
+                                          sizeof(double), ncand0, cudaMemcpyDeviceToHost, c_->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c_->stream);
+        if (e != cudaSuccess) return ctx_cuda(c_, e, "last-row readback");
+        return EVSL_OK;
+    }
+
+    // Non-restart variant (ChebLanNr), called when the sum test of the Ritz values >= bar is
+    // stable, when the slice looks empty, or when the basis is full (`full`): the candidates are
+    // extracted as at a restart; if every one in the slice meets the locking tolerance (or the
+    // basis is full) the converged ones become the result and the run ends, otherwise the same
+    // basis keeps growing and the sum test starts over.
+    int end_cycle_nr(bool full)
+    {
+        cudaEventRecord(e0_, c_->stream);
+        const int k = k_;
+        last_k_ = k;
+        nrestart_++;
+        int st = EVSL_OK;
+        double *Yt = (double *)ctx_ws(c_, WS_LAN_Y, sizeof(double) * n_ * m_, &st);
+        if (st) return st;
+        Cands cd;
+        EVSL_TRY(ritz_candidates(k, Yt, &cd));
+        std::vector<int> conv;
+        int unconv = 0;
+        for (int cnd = 0; cnd < cd.ncand0; cnd++) {
+            const double lj = cd.lam[cnd];
+            const bool inside = (lj >= a_ - widen_) && ((right_closed_ || widen_ > 0) ? (lj <= b_ + widen_) : (lj < b_));
+            if (!inside) continue;
+            const double rj = std::sqrt(std::max(0.0, cd.res[cnd])) / normA_;
+            if (rj <= tol_lock_) conv.push_back(cnd);
+            else unconv++;
+        }
+        if (verbose_)
+            fprintf(stderr, "[evsl] extraction %d: k=%d cand>=bar=%d converged=%zu unconverged=%d%s\n", nrestart_, k,
+                    cd.ncand0, conv.size(), unconv, full ? " (basis full)" : "");
+        if (unconv == 0 || full) {
+            if ((int)conv.size() > cap_) {
+                status_ = EVSL_ERR_CAPACITY;
+                conv.resize(cap_);
+            } else if (unconv > 0) {
+                status_ = EVSL_ERR_NOCONV;
+            }
+            if (!conv.empty()) {
+                int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * (size_t)(2 * (m_ + 1) + 8), &st);
+                if (st) return st;
+                EVSL_TRY(h2d(c_, idx, conv.data(), sizeof(int) * conv.size()));
+                EVSL_TRY(gather_cols(c_, n_, (int)conv.size(), Yt, n_, idx, U_, n_));
+                for (int cnd : conv) {
+                    lam_l_.push_back(cd.lam[cnd]);
+                    res_l_.push_back(std::sqrt(std::max(0.0, cd.res[cnd])) / normA_);
+                }
+                nlock_ = (int)conv.size();
+            }
+            done_ = true;
+        } else {
+            have_old_ = false;  // extend the same basis; the sum test starts over
+            prev_nabove_ = 0;
+        }
+        cudaEventRecord(e1_, c_->stream);
+        cudaEventSynchronize(e1_);
+        t_restart_ += ev_ms(e0_, e1_) * 1e-3;
+        return EVSL_OK;
+    }
+
     // Restart: Ritz pairs of T_k, candidates theta >= bar, Rayleigh quotients with A, locking.
     int end_cycle()
     {
@@ -372,64 +505,21 @@ private:
         last_k_ = k;
         nrestart_++;
         int st = EVSL_OK;
-        const int zcols = std::min(m_, 128);
         double *Yt = (double *)ctx_ws(c_, WS_LAN_Y, sizeof(double) * n_ * m_, &st);
         if (st) return st;
-        double *Z = (double *)ctx_ws(c_, WS_LAN_Z, sizeof(double) * n_ * zcols, &st);
-        if (st) return st;
-        const int Mk = k + (k & 1) < 2 ? 2 : k + (k & 1);
-        double *Vj = (double *)ctx_ws(c_, WS_LAN_T, sizeof(double) * (size_t)Mk * Mk, &st);
-        if (st) return st;
-        double *Sd = (double *)ctx_ws(c_, WS_LAN_S, sizeof(double) * (size_t)Mk * Mk, &st);
-        if (st) return st;
+        Cands cd;
+        EVSL_TRY(ritz_candidates(k, Yt, &cd));
         int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * (size_t)(2 * (m_ + 1) + 8), &st);
         if (st) return st;
-        double *vd = (double *)ctx_ws(c_, WS_LAN_G, sizeof(double) * 3 * (size_t)(m_ + 1), &st);
-        if (st) return st;
-        double *lamd = vd, *resd = vd + (m_ + 1), *nrmd = vd + 2 * (m_ + 1);
-
-        std::vector<double> Tk((size_t)k * k), w(k);
-        for (int j = 0; j < k; j++)
-            for (int i = 0; i < k; i++) Tk[(size_t)j * k + i] = t(i, j);
-        int ldv = 0, sweeps = 0;
-        // jacobi_eig keeps its working copy in WS_LAN_S; the candidate block reuses it afterwards
-        EVSL_TRY(jacobi_eig(c_, k, Tk.data(), w.data(), Vj, &ldv, &sweeps));
-        Sd = (double *)ctx_ws(c_, WS_LAN_S, sizeof(double) * (size_t)Mk * Mk, &st);
-        if (st) return st;
-        const double betak = t(k - 1, k);
-        std::vector<int> order(k);
-        std::iota(order.begin(), order.end(), 0);
-        std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
-        int ncand0 = 0;
-        while (ncand0 < k && w[order[ncand0]] >= bar_) ncand0++;
+        const int ncand0 = cd.ncand0, sweeps = cd.sweeps;
+        const double betak = cd.betak;
+        const std::vector<double> &w = cd.w, &lamh = cd.lam, &resh = cd.res, &slast = cd.slast;
+        const std::vector<int> &order = cd.order;
         int ncand = 0;
         const int nlock_before = nlock_;
         std::vector<int> lock_idx, tr_idx;
         std::vector<double> new_trtheta, new_trs, tr_res;
         if (ncand0 > 0) {
-            EVSL_TRY(h2d(c_, idx, order.data(), sizeof(int) * ncand0));
-            EVSL_TRY(gather_cols(c_, k, ncand0, Vj, ldv, idx, Sd, k));
-            ProfGroup g;
-            prof_begin(c_, EVSL_K_RITZ_GEMM, &g);
-            EVSL_TRY(gemm_nn(c_, n_, ncand0, k, Q_, n_, Sd, k, Yt, n_));
-            prof_end(c_, &g, 1);
-            EVSL_TRY(coldot(c_, n_, ncand0, Yt, n_, Yt, n_, nrmd));
-            EVSL_TRY(colscale_inv_sqrt(c_, n_, ncand0, Yt, nrmd));
-            std::vector<double> lamh(ncand0), resh(ncand0), slast(ncand0);
-            for (int j0 = 0; j0 < ncand0; j0 += zcols) {
-                int nc = std::min(zcols, ncand0 - j0);
-                EVSL_TRY(spmv_f64(c_, nc, Yt + (int64_t)j0 * n_, Z));
-                EVSL_TRY(coldot(c_, n_, nc, Yt + (int64_t)j0 * n_, n_, Z, n_, lamd + j0));
-                EVSL_TRY(colres2(c_, n_, nc, Z, Yt + (int64_t)j0 * n_, n_, lamd + j0, resd + j0));
-            }
-            EVSL_TRY(d2h(c_, lamh.data(), lamd, sizeof(double) * ncand0));
-            EVSL_TRY(d2h(c_, resh.data(), resd, sizeof(double) * ncand0));
-            {
-                cudaError_t e = cudaMemcpy2DAsync(slast.data(), sizeof(double), Sd + (k - 1), sizeof(double) * k,
-                                                  sizeof(double), ncand0, cudaMemcpyDeviceToHost, c_->stream);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(c_->stream);
-                if (e != cudaSuccess) return ctx_cuda(c_, e, "last-row readback");
-            }
             for (int cnd = 0; cnd < ncand0; cnd++) {
                 double lj = lamh[cnd];
                 bool inside = (lj >= a_ - widen_) && ((right_closed_ || widen_ > 0) ? (lj <= b_ + widen_) : (lj < b_));
@@ -868,7 +958,7 @@ private:
     const evsl_polfilt *pol_;
     evsl_lan_opts o_;
     int m_ = 0, cap_ = 0, maxit_ = 0, ncycle_ = 10;
-    bool right_closed_ = true, verbose_ = false, mixed_ = false;
+    bool right_closed_ = true, nonrestart_ = false, verbose_ = false, mixed_ = false;
     double tol_ = 1e-8, tau1_ = 1e-10, bar_ = 0.0, normA_ = 1.0, tol_lock_ = 1e-8, widen_ = 0.0;
     double *U_ = nullptr, *Q_ = nullptr, *sc_ = nullptr, *h_ = nullptr;
     size_t nsc_ = 0;
@@ -898,7 +988,7 @@ int status_message(evsl_ctx *c, int st, int cap, int maxit)
 // ------------------------------------------------------------------------------------------
 int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
                   const evsl_lan_opts *o, int cap, int *nev, double *lam, double *Y, double *res,
-                  evsl_stats *st)
+                  evsl_stats *st, bool nonrestart)
 {
     cudaEvent_t ta, tb, fa, fb;
     cudaEventCreate(&ta);
@@ -908,7 +998,7 @@ int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
     cudaEventRecord(ta, c->stream);
     int rc = EVSL_OK;
     {
-        SliceSolver S(c, a, b, pol, *o, o->m, cap, o->right_closed != 0);
+        SliceSolver S(c, a, b, pol, *o, o->m, cap, o->right_closed != 0, nonrestart);
         rc = S.init();
         const int64_t n = c->A.n;
         double *y = nullptr, *B0 = nullptr, *B1 = nullptr;
@@ -938,7 +1028,8 @@ int drv_chebLanTr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ta, tb);
             rc = S.finish(nev, lam, res, Y, st, ms * 1e-3);
-            if (rc == EVSL_OK) rc = status_message(c, S.status(), cap, o->maxit > 0 ? o->maxit : 20 * o->m);
+            if (rc == EVSL_OK)
+                rc = status_message(c, S.status(), cap, nonrestart ? o->m : (o->maxit > 0 ? o->maxit : 20 * o->m));
         }
     }
     cudaEventDestroy(ta);

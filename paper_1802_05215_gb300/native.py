@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True):
         "evsl_filter_apply_noalloc": (i32, [P, P, i32, P, P]),
         "evsl_filter_apply_multi": (i32, [P, i32, P, P, P, i32]),
         "evsl_chebLanTr": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
+        "evsl_chebLanNr": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_chebLanTr_batch": (i32, [P, i32, P, P]),
         "evsl_batch_create": (i32, [P, P, C.POINTER(P)]),
         "evsl_batch_add": (i32, [P, P]),
@@ -261,6 +262,27 @@ class Context:
                                      C.byref(stats))
         if st != EVSL_OK and not (allow_partial and st in (-4, -5)):
             self._check(st, "chebLanTr")
+        k = nev.value
+        return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
+                    stats=stats.as_dict())
+
+    def chebLanNr(self, a, b, filt: Filter, m=400, ncycle=10, tol=1e-8, tau1=1e-10, seed=0,
+                  prec=FP64, right_closed=True, cap=None, Y=None, allow_partial=False):
+        """Filtered non-restart Lanczos on [a, b] with a basis of at most m vectors; same
+        outputs as chebLanTr (stats["nrestart"] counts the extractions)."""
+        cap = cap or m
+        opts = LanOpts(m, 0, ncycle, tol, tau1, seed, prec, int(right_closed))
+        lam = np.zeros(cap)
+        res = np.zeros(cap)
+        if Y is None:
+            Y = np.zeros((cap, self.n))
+        nev = C.c_int()
+        stats = Stats()
+        st = self.lib.evsl_chebLanNr(self.h, a, b, C.byref(filt.pol), C.byref(opts), cap,
+                                     C.byref(nev), _addr(lam), _addr(Y), _addr(res),
+                                     C.byref(stats))
+        if st != EVSL_OK and not (allow_partial and st in (-4, -5)):
+            self._check(st, "chebLanNr")
         k = nev.value
         return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
                     stats=stats.as_dict())

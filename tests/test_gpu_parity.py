@@ -424,6 +424,65 @@ def test_filter_graph_replay_matches_block_kernel_bitwise(ctx, nat, prec):
             ctx.filter_apply(f, X[0:1].clone(), Y1, prec=prec)
             assert torch.equal(Y1[0], Y2[0])
 
+
+# ------------------------------------------------------------------------------ non-restart Lanczos
+@pytest.mark.parametrize("case", [("lap2d", 40, 0.5, 0.8), ("lap3d", 12, 0.8, 1.6)])
+def test_cheblannr_laplacian_matches_closed_form_and_oracle(ctx, nat, oracle_mod, case):
+    # ChebLanNr (one basis, no restarts) finds every copy of the multiple eigenvalues: exact
+    # count and values against the closed form, residuals recomputed densely; the oracle's
+    # non-restart run finds the same eigenvalues
+    kind, nx, a, b = case
+    A = I.laplacian_2d(nx) if kind == "lap2d" else I.laplacian_3d(nx)
+    e = lap_eigs(2 if kind == "lap2d" else 3, nx)
+    ex = e[(e >= a) & (e <= b)]
+    ctx.set_csr(A)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    f = nat.cheb_filter_build(a, b, lo, hi)
+    m = max(6 * len(ex), 200)
+    r = ctx.chebLanNr(a, b, f, m=m)
+    assert r["status"] == 0 and r["nev"] == len(ex)
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.maximum(1, np.abs(ex)))
+    Y = r["Y"][:r["nev"]].T
+    assert np.max(_dense_residuals(A, r["lam"], Y)) <= 1e-8
+    assert np.max(np.abs(Y.T @ Y - np.eye(r["nev"]))) <= 1e-10
+    assert r["stats"]["nmv"] == f.deg * r["stats"]["niter"]
+    ro = oracle_mod.cheblannr(A, a, b, oracle_mod.filter_build(a, b, lo, hi), m=m)
+    assert ro["nev"] == r["nev"]
+    assert np.all(np.abs(ro["lam"] - r["lam"]) <= 1e-9 * np.maximum(1, np.abs(ex)))
+
+
+@pytest.mark.parametrize("a,b", [(-1.0, 1.0), (3.0, 5.0)])
+def test_cheblannr_anderson_bruteforce(ctx, nat, a, b):
+    A = I.anderson_3d(7, 4.0, 0)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    ex = ev[(ev >= a) & (ev <= b)]
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(80, 0)
+    f = nat.cheb_filter_build(a, b, lo, hi)
+    r = ctx.chebLanNr(a, b, f, m=max(6 * len(ex), 200))
+    assert r["status"] == 0 and r["nev"] == len(ex)
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.maximum(1, np.abs(ex)))
+    assert np.max(_dense_residuals(A, r["lam"], r["Y"][:r["nev"]].T)) <= 1e-8
+
+
+def test_cheblannr_short_basis_reports_noconv_and_fp32_mode(ctx, nat):
+    # a basis too short to converge every pair: the converged ones and EVSL_ERR_NOCONV;
+    # the FP32 filter with the FP64 polish meets the FP64 tolerances
+    A = I.laplacian_2d(40)
+    e = lap_eigs(2, 40)
+    ex = e[(e >= 0.5) & (e <= 0.8)]
+    ctx.set_csr(A)
+    f = nat.cheb_filter_build(0.5, 0.8, 0.0, 8.0)
+    r = ctx.chebLanNr(0.5, 0.8, f, m=30, allow_partial=True)
+    assert r["status"] == -4 and r["stats"]["niter"] == 30 and r["nev"] < len(ex)
+    for lam in r["lam"]:
+        assert np.min(np.abs(ex - lam)) <= 1e-9 * max(1.0, abs(lam))
+    assert np.all(r["res"] <= 1e-8)
+    r32 = ctx.chebLanNr(0.5, 0.8, f, m=300, prec=nat.FP32)
+    assert r32["status"] == 0 and r32["nev"] == len(ex)
+    assert np.all(np.abs(r32["lam"] - ex) <= 1e-9 * np.maximum(1, np.abs(ex)))
+    assert np.max(_dense_residuals(A, r32["lam"], r32["Y"][:r32["nev"]].T)) <= 1e-8
+
 def test_batch_admission_respects_hbm_budget(nat):
     # a 64 MiB budget holds the matrix, the workspaces and a few jobs' bases (~6.6 MB each);
     # admission must then refuse with EVSL_ERR_NOMEM and leave the admitted jobs intact
