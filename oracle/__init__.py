@@ -62,6 +62,9 @@ def _load():
         _lib.orc_cheblantr.restype = i32
         _lib.orc_cheblantr.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d,
                                        i32, i32, i32, d, d, u64, i32, P, P, P, P, P]
+        _lib.orc_chebsi.restype = i32
+        _lib.orc_chebsi.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d, i32, i32, d, u64,
+                                    i32, P, P, P, P, P]
         _lib.orc_cheblannr.restype = i32
         _lib.orc_cheblannr.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d,
                                        i32, i32, d, d, u64, i32, P, P, P, P, P]
@@ -176,6 +179,25 @@ def reorth(z: np.ndarray, B: np.ndarray) -> int:
     order): CGS with the DGKS test, at most two passes (Sec. 2.3).  Returns the passes."""
     assert z.flags.c_contiguous and B.flags.f_contiguous and z.dtype == B.dtype == np.float64
     return int(_load().orc_reorth_cgs(len(z), _p(z), _p(B), B.shape[1]))
+
+
+def chebsi(A, a, b, pol, nv, maxit=100, tol=1e-8, seed=0, cap=None, right_closed=True):
+    """Polynomial filtered subspace iteration (ChebSI) with a block of nv vectors.  Returns a
+    dict (niter = filter passes that fed a Rayleigh-Ritz step, nmv = all filter matvecs)."""
+    cap = cap or nv
+    lam = np.empty(cap)
+    res = np.empty(cap)
+    Y = np.empty((A.n, cap), order="F")
+    nev = C.c_int()
+    stats = np.zeros(4, dtype=np.int64)
+    coef = np.ascontiguousarray(pol["coef"], dtype=np.float64)
+    st = _load().orc_chebsi(*_csr_args(A), a, b, int(right_closed), pol["lmin"], pol["lmax"],
+                            len(coef) - 1, _p(coef), pol["bar"], nv, maxit, tol, seed, cap, C.byref(nev),
+                            _p(lam), _p(Y), _p(res), _p(stats))
+    k = nev.value
+    order = np.argsort(lam[:k])
+    return dict(status=st, nev=k, lam=lam[:k][order].copy(), Y=Y[:, :k][:, order].copy(),
+                res=res[:k][order].copy(), niter=int(stats[0]), nmv=int(stats[1]), npass=int(stats[3]))
 
 
 def cheblannr(A, a, b, pol, m=200, ncycle=10, tol=1e-8, tau1=1e-10, seed=0, cap=None,

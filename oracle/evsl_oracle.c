@@ -1042,3 +1042,109 @@ int orc_cheblannr(int64_t n, const int64_t *rp, const int32_t *ci, const double 
     free(y); free(z); free(u); free(Au);
     return status;
 }
+
+/* Polynomial filtered subspace iteration (ChebSI; the paper lists it among EVSL's projection
+ * methods, Sec. 2.6 and Sec. 3, and notes that the subspace dimension comes from the DOS count,
+ * but prints no listing).  READING: V (n x nv) starts as nv seeded random vectors (stream 3,
+ * indices 0..nv-1), orthonormalised.  Each pass forms W = rho(Ahat) V; when V holds the Ritz
+ * vectors of the previous pass, mu_j = v_j^T w_j is the filter's Rayleigh quotient of v_j.  A
+ * vector made only of eigenvectors outside the slice has mu < bar (rho < bar outside the slice),
+ * an eigenvector inside has mu >= bar, so the in-slice Ritz pairs with mu >= bar are the wanted
+ * ones: when all of them have ||A v - theta v|| <= tol ||A||, the run stops and returns the
+ * converged in-slice pairs.  Otherwise W is orthonormalised (CGS with the DGKS second pass,
+ * column by column; a column that vanishes is replaced by the next seeded vector) and
+ * Rayleigh-Ritz with A gives the next V = W S (W^T A W = S diag(theta) S^T, theta ascending).
+ * After maxit passes the converged in-slice pairs are returned with status -4.
+ * stats: passes, nmv, 0, CGS passes. */
+int orc_chebsi(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+               double a, double b, int right_closed, double lmin, double lmax,
+               int deg, const double *coef, double bar, int nv, int maxit, double tol, uint64_t seed,
+               int cap, int *nev, double *lam, double *Y, double *res, long *stats)
+{
+    orc_csr A = {n, rp, ci, v};
+    orc_filt F = {&A, 0.5 * (lmax + lmin), 0.5 * (lmax - lmin), deg, coef, NULL, NULL, NULL, 0};
+    F.w0 = malloc(sizeof(double) * n);
+    F.w1 = malloc(sizeof(double) * n);
+    F.w2 = malloc(sizeof(double) * n);
+    double normA = fmax(fabs(lmin), fabs(lmax));
+    if (nv > n) nv = (int)n;
+    double *V = malloc(sizeof(double) * (size_t)n * nv), *W = malloc(sizeof(double) * (size_t)n * nv);
+    double *AW = malloc(sizeof(double) * (size_t)n * nv);
+    double *G = malloc(sizeof(double) * (size_t)nv * nv), *S = malloc(sizeof(double) * (size_t)nv * nv);
+    double *th = malloc(sizeof(double) * nv), *rr = malloc(sizeof(double) * nv), *r = malloc(sizeof(double) * n);
+    uint64_t fresh_index = 0;
+    long npass = 0;
+    int it = 0, status = -4, found = 0, ritz = 0;
+    for (int j = 0; j < nv; j++)
+        orc_fresh_vector(n, seed, fresh_index++, V + (size_t)j * n, NULL, 0, V, j);
+    for (it = 1; it <= maxit + 1; it++) {
+        for (int j = 0; j < nv; j++) orc_apply_filter(&F, V + (size_t)j * n, W + (size_t)j * n);
+        if (ritz) {
+            /* the previous pass's Ritz pairs: stop if every wanted one has converged */
+            int all = 1;
+            for (int j = 0; j < nv; j++) {
+                int inside = (th[j] >= a) && (right_closed ? (th[j] <= b) : (th[j] < b));
+                double mu = orc_dot(n, V + (size_t)j * n, W + (size_t)j * n);
+                if (inside && mu >= bar && rr[j] > tol) all = 0;
+            }
+            if (all || it == maxit + 1) {
+                found = 0;
+                status = all ? 0 : -4;
+                for (int j = 0; j < nv; j++) {
+                    int inside = (th[j] >= a) && (right_closed ? (th[j] <= b) : (th[j] < b));
+                    if (!inside || rr[j] > tol) continue;
+                    if (found >= cap) { status = -5; break; }
+                    lam[found] = th[j];
+                    res[found] = rr[j];
+                    if (Y) memcpy(Y + (size_t)found * n, V + (size_t)j * n, sizeof(double) * n);
+                    found++;
+                }
+                it--;                   /* this filter pass only served the test */
+                break;
+            }
+        }
+        for (int j = 0; j < nv; j++) {
+            double *w = W + (size_t)j * n;
+            double before = orc_nrm2(n, w);
+            npass += orc_reorth(n, w, W, j, NULL, 0);
+            double nw = orc_nrm2(n, w);
+            if (!(nw > 1e-12 * before)) {                    /* dependent: a fresh direction */
+                orc_fresh_vector(n, seed, fresh_index++, w, W, j, NULL, 0);
+                continue;
+            }
+            for (int64_t i = 0; i < n; i++) w[i] /= nw;
+        }
+        for (int j = 0; j < nv; j++) orc_matvec(&A, W + (size_t)j * n, AW + (size_t)j * n);
+        for (int j = 0; j < nv; j++)
+            for (int i = 0; i <= j; i++) {
+                double g = 0.5 * (orc_dot(n, W + (size_t)i * n, AW + (size_t)j * n) +
+                                  orc_dot(n, W + (size_t)j * n, AW + (size_t)i * n));
+                AT(G, i, j, nv) = g;
+                AT(G, j, i, nv) = g;
+            }
+        orc_syev(nv, G, th, S);
+        for (int64_t i = 0; i < n; i++)
+            for (int j = 0; j < nv; j++) {
+                double acc = 0.0;
+                for (int p = 0; p < nv; p++) acc += W[(size_t)p * n + i] * AT(S, p, j, nv);
+                V[(size_t)j * n + i] = acc;
+            }
+        for (int j = 0; j < nv; j++) {
+            const double *vj = V + (size_t)j * n;
+            orc_matvec(&A, vj, r);
+            for (int64_t i = 0; i < n; i++) r[i] -= th[j] * vj[i];
+            rr[j] = orc_nrm2(n, r) / normA;
+        }
+        ritz = 1;
+    }
+    *nev = found;
+    if (stats) {
+        stats[0] = it;
+        stats[1] = F.nmv;
+        stats[2] = 0;
+        stats[3] = npass;
+    }
+    free(F.w0); free(F.w1); free(F.w2); free(V); free(W); free(AW); free(G); free(S); free(th);
+    free(rr); free(r);
+    return status;
+}

@@ -371,6 +371,46 @@ def test_cheblannr_short_basis_reports_noconv(oracle_mod):
         assert np.min(np.abs(ex - lam)) <= 1e-9 * max(1.0, abs(lam))
     assert np.all(r["res"] <= 1e-8)
 
+
+# ---------------------------------------------------------------- filtered subspace iteration
+@pytest.mark.parametrize("a,b", [(-1.0, 1.0), (3.0, 5.0), (6.0, 6.5)])
+def test_chebsi_anderson_bruteforce(oracle_mod, a, b):
+    A = I.anderson_3d(7, 4.0, 0)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    ex = ev[(ev >= a) & (ev <= b)]
+    r = oracle_mod.chebsi(A, a, b, pol, nv=int(1.5 * len(ex)) + 20)
+    assert r["status"] == 0
+    _check_eigs(A, r, ex)
+
+
+@pytest.mark.parametrize("case", [("2d", 40, 0.5, 0.8), ("3d", 12, 0.8, 1.6)])
+def test_chebsi_against_closed_form(oracle_mod, case):
+    # a block iteration holds every copy of a multiple eigenvalue from the start
+    kind, nx, a, b = case
+    A = I.laplacian_2d(nx) if kind == "2d" else I.laplacian_3d(nx)
+    e = lap_eigs(2 if kind == "2d" else 3, nx)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    ex = e[(e >= a) & (e <= b)]
+    r = oracle_mod.chebsi(A, a, b, pol, nv=int(1.5 * len(ex)) + 20)
+    assert r["status"] == 0
+    _check_eigs(A, r, ex)
+
+
+def test_chebsi_too_few_passes_reports_noconv(oracle_mod):
+    A = I.anderson_3d(7, 4.0, 0)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(3.0, 5.0, lo, hi)
+    r = oracle_mod.chebsi(A, 3.0, 5.0, pol, nv=137, maxit=3)
+    assert r["status"] == -4 and r["niter"] <= 3
+    ex = ev[(ev >= 3.0) & (ev <= 5.0)]
+    for lam in r["lam"]:
+        assert np.min(np.abs(ex - lam)) <= 1e-9 * max(1.0, abs(lam))
+    assert np.all(r["res"] <= 1e-8)
+
 def test_cheblantr_half_open_slices_partition(oracle_mod):
     # adjacent half-open slices [a, cut) and [cut, b] neither lose nor duplicate eigenvalues
     # (cut midway between two distinct eigenvalues, so rounding cannot decide membership)
