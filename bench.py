@@ -624,6 +624,48 @@ def run_table4_nr(args):
     return line
 
 
+def run_si_49(args):
+    """ChebSI against ChebLanNr on one slice of Table 4's case: the 49^3 Laplacian on
+    [0.33926, 0.51429] (the paper's second of 6 slices, 328 eigenvalues by the closed form),
+    sigma damping; ChebSI with a block of 1.5 nu + 20 vectors from the closed-form count."""
+    import torch
+
+    from paper_1802_05215_gb300 import native
+    A = inputs.laplacian_3d(49)
+    a, b = 0.33926, 0.51429
+    f1 = 2.0 - 2.0 * np.cos(np.arange(1, 50) * np.pi / 50)
+    ev = np.sort((f1[:, None, None] + f1[None, :, None] + f1[None, None, :]).ravel())
+    exact = int(np.count_nonzero((ev >= a) & (ev <= b)))
+    out = {}
+    with native.Context(0) as ctx:
+        ctx.set_csr(A)
+        lo, hi = ctx.bounds(BOUNDS_STEPS, SEED)
+        f = native.cheb_filter_build(a, b, lo, hi, damping=native.DAMP_SIGMA)
+        nv = int(1.5 * exact) + 20
+        Y = torch.empty(nv * A.n, dtype=torch.float64, device="cuda")
+        ctx.chebSI(a, b, f, nv=nv, maxit=2, cap=nv, Y=Y, allow_partial=True)      # warm-up
+        for name, run in [("chebsi", lambda: ctx.chebSI(a, b, f, nv=nv, cap=nv, Y=Y, tol=TOL, seed=SEED)),
+                          ("cheblannr", lambda: ctx.chebLanNr(a, b, f, m=int(5 * exact + 100), cap=nv, Y=Y,
+                                                              tol=TOL, seed=SEED))]:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = run()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st = r["stats"]
+            out[name] = {"eigenpairs": r["nev"], "seconds": dt, "eigenpairs_per_s": r["nev"] / dt,
+                         "iterations": st["niter"], "nmv": st["nmv"], "t_filter": st["t_filter"],
+                         "t_orth": st["t_orth"], "t_projection": st["t_restart"],
+                         "max_res": float(r["res"].max()) if r["nev"] else 0.0}
+    line = {"metric": "eigenpairs/s at resid<=1e-8, ChebSI vs ChebLanNr (49^3 Laplacian, one Table 4 slice)",
+            "value": out["chebsi"]["eigenpairs_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic (closed-form 3-D Laplacian)",
+            "config": {"workload": "3-D 7-point Laplacian 49^3, [0.33926, 0.51429], sigma damping"},
+            "exact_count": exact, "deg": f.deg, **out}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def run_kpm_200(args):
     """KPM density of the Anderson 200^3 model (W = 2, n = 8e6, nnz = 5.576e7): degree 300 with
     64 Rademacher probes in one block, FP64 and FP32; the FP64 moments of the first probe are
@@ -686,7 +728,7 @@ def run_kpm_200(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["lap3d_100", "serving", "anderson3d_80", "kpm_200", "table2_nr", "table4_nr"],
+    ap.add_argument("--workload", choices=["lap3d_100", "serving", "anderson3d_80", "kpm_200", "table2_nr", "table4_nr", "si_49"],
                     default="lap3d_100")
     ap.add_argument("--slices", type=int, default=4,
                     help="anderson3d_80: how many of the 16 slices to solve (<= 0: all)")
@@ -708,6 +750,8 @@ def main():
         run_table2_nr(args)
     elif args.workload == "table4_nr":
         run_table4_nr(args)
+    elif args.workload == "si_49":
+        run_si_49(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -231,6 +231,20 @@ int evsl_chebLanNr(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol,
                    const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
                    double *res, evsl_stats *stats);
 
+/* Polynomial filtered subspace iteration (ChebSI; the paper lists it among EVSL's projection
+ * methods and notes that its subspace dimension comes from the DOS count, but gives no listing).
+ * A block of opts->m vectors (about 1.5 times the slice's estimated count plus a margin) starts
+ * from seeded random vectors; each pass applies rho(A) to the block, orthonormalises it and
+ * performs Rayleigh-Ritz with A.  The filter's Rayleigh quotient mu = v^T rho(A) v of each Ritz
+ * vector (free from the next pass) separates wanted pairs (mu >= pol->bar) from mixtures of
+ * eigenvectors outside the slice (mu < bar); the run stops when every in-slice Ritz pair with
+ * mu >= bar meets tol, after at most opts->maxit passes (0 = 100; then EVSL_ERR_NOCONV with the
+ * converged pairs).  FP64 filter only (EVSL_ERR_ARG otherwise); outputs and EVSL_ERR_CAPACITY
+ * as in evsl_chebLanTr; stats->niter counts passes, stats->nmv all filter matvecs.  Device
+ * memory: about 4 n m doubles. */
+int evsl_chebSI(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *opts,
+                int cap, int *nev, double *lam, double *Y, double *res, evsl_stats *stats);
+
 /* Several slices of one matrix solved together (Sec. 2.6: slices are independent; here they
  * share the GPU instead of separate processes).  Each job is one slice with its own filter,
  * Krylov dimension and outputs; the slices advance in lockstep and every Lanczos step applies

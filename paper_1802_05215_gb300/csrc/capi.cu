@@ -280,6 +280,19 @@ int evsl_chebLanNr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, con
     return drv_chebLanTr(c, a, b, pol, opts, cap, nev, lam, Y, res, stats, true);
 }
 
+int evsl_chebSI(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *opts,
+                int cap, int *nev, double *lam, double *Y, double *res, evsl_stats *stats)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!pol || !pol->coef || !opts || !nev || !lam || !res || cap < 1 || !(b > a) || opts->m < 1)
+        return ctx_fail(c, EVSL_ERR_ARG, "chebSI: bad arguments");
+    if (opts->prec != EVSL_FP64) return ctx_fail(c, EVSL_ERR_ARG, "chebSI: only the FP64 filter is supported");
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "chebSI: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_chebSI(c, a, b, pol, opts, cap, nev, lam, Y, res, stats);
+}
+
 int evsl_chebLanTr_batch(evsl_ctx *c, int njobs, evsl_slice_job *jobs, const evsl_lan_opts *opts)
 {
     if (!c) return EVSL_ERR_ARG;

@@ -83,7 +83,7 @@ void filter_graphs_clear(evsl_ctx *c);
 enum WsSlot {
     WS_PARTIAL = 0, WS_SCAL, WS_W0, WS_W1, WS_W2, WS_KPM_PART, WS_F32_X, WS_F32_Y,
     WS_LAN_U, WS_LAN_Q, WS_LAN_Y, WS_LAN_Z, WS_LAN_VEC, WS_LAN_T, WS_LAN_S, WS_LAN_IDX,
-    WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_POL_V, WS_POL_W, WS_POL_B, WS_POL_S, WS_POL_Y, WS_POL_R, WS_TUNE,
+    WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_POL_V, WS_POL_W, WS_POL_B, WS_POL_S, WS_POL_Y, WS_POL_R, WS_TUNE, WS_POL_H,
     WS_COUNT
 };
 
@@ -205,6 +205,8 @@ int filter_apply_dev(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doubl
 int filter_apply_multi_dev(evsl_ctx *c, int npol, const evsl_polfilt *pols, const double *X,
                            double *Y, evsl_precision prec);
 int drv_chebLanTr_batch(evsl_ctx *c, int njobs, evsl_slice_job *jobs, const evsl_lan_opts *o);
+int drv_chebSI(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *o, int cap,
+               int *nev, double *lam, double *Y, double *res, evsl_stats *st);
 int batch_create(evsl_ctx *c, const evsl_lan_opts *o, evsl_batch **out);
 void batch_destroy(evsl_batch *bt);
 int batch_add(evsl_batch *bt, evsl_slice_job *job);

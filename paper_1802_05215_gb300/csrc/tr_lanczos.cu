@@ -112,6 +112,106 @@ public:
     }
 
     bool done() const { return done_; }
+
+    // Polynomial filtered subspace iteration (ChebSI) with a block of nv = m vectors held in the
+    // basis array, at most `maxpass` Rayleigh-Ritz passes.  V starts as nv seeded random vectors,
+    // orthonormalised; each pass forms W = rho(Ahat) V, and when V holds the previous pass's Ritz
+    // vectors, mu_j = v_j^T w_j is the filter's Rayleigh quotient of v_j: a vector made only of
+    // eigenvectors outside the slice has mu < bar, an in-slice eigenvector mu >= bar.  The run
+    // stops when every in-slice Ritz pair with mu >= bar meets tol; otherwise W is orthonormalised
+    // (dropped dependent directions are replaced by fresh seeded vectors) and Rayleigh-Ritz with A
+    // gives the next V.  The converged in-slice pairs become the result (EVSL_ERR_NOCONV after
+    // maxpass passes with wanted pairs unconverged, EVSL_ERR_CAPACITY beyond cap).
+    int run_si(int maxpass)
+    {
+        const int nv = m_;
+        const int nc = std::min(nv, 64);
+        int st = EVSL_OK;
+        double *V = Q_;
+        double *W = (double *)ctx_ws(c_, WS_POL_W, sizeof(double) * n_ * nv, &st);
+        if (st) return st;
+        double *B = (double *)ctx_ws(c_, WS_POL_B, sizeof(double) * n_ * 2 * nc, &st);
+        if (st) return st;
+        double *mud = (double *)ctx_ws(c_, WS_POL_H, sizeof(double) * ((size_t)nv + 8), &st);
+        if (st) return st;
+        for (int j = 0; j < nv; j++)
+            EVSL_TRY(fill_uniform_f64(c_, n_, o_.seed, SM_STREAM_LANCZOS, fresh_index_++, V + (int64_t)j * n_));
+        int kv = 0;
+        EVSL_TRY(orthonormalize(V, nv, W, &kv));
+        EVSL_TRY(refill_block(V, kv, nv, W, &kv));
+        std::vector<double> th, r2, mu;
+        bool ritz = false;
+        for (int pass = 1; pass <= maxpass + 1; pass++) {
+            cudaEventRecord(e0_, c_->stream);
+            for (int j0 = 0; j0 < kv; j0 += nc) {
+                const int mcols = std::min(nc, kv - j0);
+                const int64_t o = (int64_t)j0 * n_;
+                EVSL_TRY(filter_apply_dev(c_, pol_, mcols, V + o, W + o, EVSL_FP64, B, B + (int64_t)mcols * n_, nullptr));
+            }
+            cudaEventRecord(e1_, c_->stream);
+            cudaEventSynchronize(e1_);
+            t_filter_ += ev_ms(e0_, e1_) * 1e-3;
+            nmv_ += (int64_t)pol_->deg * kv;
+            if (ritz) {
+                EVSL_TRY(coldot(c_, n_, kv, V, n_, W, n_, mud));
+                mu.assign(kv, 0.0);
+                EVSL_TRY(d2h(c_, mu.data(), mud, sizeof(double) * kv));
+                bool all = true;
+                for (int j = 0; j < kv; j++)
+                    if (in_slice(th[j]) && mu[j] >= bar_ && std::sqrt(std::max(0.0, r2[j])) / normA_ > tol_)
+                        all = false;
+                if (verbose_) {
+                    int nin = 0, nconv = 0;
+                    for (int j = 0; j < kv; j++)
+                        if (in_slice(th[j])) {
+                            nin++;
+                            nconv += std::sqrt(std::max(0.0, r2[j])) / normA_ <= tol_;
+                        }
+                    fprintf(stderr, "[evsl] si pass %d: block=%d in_slice=%d converged=%d%s\n", pass - 1, kv, nin,
+                            nconv, all ? " (done)" : "");
+                }
+                if (all || pass == maxpass + 1) {
+                    std::vector<int> keep;
+                    for (int j = 0; j < kv; j++) {
+                        const double rj = std::sqrt(std::max(0.0, r2[j])) / normA_;
+                        if (!in_slice(th[j]) || rj > tol_) continue;
+                        if ((int)keep.size() >= cap_) {
+                            status_ = EVSL_ERR_CAPACITY;
+                            break;
+                        }
+                        keep.push_back(j);
+                        lam_l_.push_back(th[j]);
+                        res_l_.push_back(rj);
+                    }
+                    if (!all && status_ == EVSL_OK) status_ = EVSL_ERR_NOCONV;
+                    if (!keep.empty()) {
+                        int *idx = (int *)ctx_ws(c_, WS_LAN_IDX, sizeof(int) * (keep.size() + 8), &st);
+                        if (st) return st;
+                        EVSL_TRY(h2d(c_, idx, keep.data(), sizeof(int) * keep.size()));
+                        EVSL_TRY(gather_cols(c_, n_, (int)keep.size(), V, n_, idx, U_, n_));
+                    }
+                    nlock_ = (int)keep.size();
+                    its_ = pass - 1;
+                    break;
+                }
+            }
+            cudaEventRecord(e0_, c_->stream);
+            int kw = 0;
+            EVSL_TRY(orthonormalize(W, kv, V, &kw));
+            EVSL_TRY(refill_block(W, kw, kv, V, &kw));
+            int sweeps = 0;
+            EVSL_TRY(rayleigh_ritz(W, kw, V, th, r2, &sweeps));
+            kv = kw;
+            ritz = true;
+            nrestart_++;
+            cudaEventRecord(e1_, c_->stream);
+            cudaEventSynchronize(e1_);
+            t_restart_ += ev_ms(e0_, e1_) * 1e-3;
+            its_ = pass;
+        }
+        done_ = true;
+        return EVSL_OK;
+    }
     int status() const { return status_; }
     const evsl_polfilt *pol() const { return pol_; }
 
@@ -621,6 +721,20 @@ private:
     }
 
     bool in_slice(double t) const { return t >= a_ && (right_closed_ ? t <= b_ : t < b_); }
+
+    // After orthonormalize kept k < want columns of X: fresh seeded vectors fill columns
+    // k..want-1 and the block is orthonormalised again (Tmp: n x want scratch).
+    int refill_block(double *X, int k, int want, double *Tmp, int *kout)
+    {
+        int kk = k;
+        for (int tries = 0; tries < 3 && kk < want; tries++) {
+            for (int j = kk; j < want; j++)
+                EVSL_TRY(fill_uniform_f64(c_, n_, o_.seed, SM_STREAM_LANCZOS, fresh_index_++, X + (int64_t)j * n_));
+            EVSL_TRY(orthonormalize(X, want, Tmp, &kk));
+        }
+        *kout = kk;
+        return EVSL_OK;
+    }
 
     // FP64 recovery after an FP32-filter run: restarted block Krylov iteration with the FP64
     // filter.  The start block V0 = orth[U, G] holds the pairs the FP32 phase locked and g guard
@@ -1183,6 +1297,37 @@ int batch_step(evsl_batch *bt, int *nactive, int *nfinished)
 }
 
 evsl_ctx *batch_ctx(evsl_batch *bt) { return bt->c; }
+
+int drv_chebSI(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *o, int cap,
+               int *nev, double *lam, double *Y, double *res, evsl_stats *st)
+{
+    cudaEvent_t ta, tb;
+    cudaEventCreate(&ta);
+    cudaEventCreate(&tb);
+    cudaEventRecord(ta, c->stream);
+    int rc = EVSL_OK;
+    {
+        SliceSolver S(c, a, b, pol, *o, o->m, cap, o->right_closed != 0);
+        rc = S.init();
+        if (rc == EVSL_OK) rc = S.run_si(o->maxit > 0 ? o->maxit : 100);
+        if (rc == EVSL_OK) {
+            cudaEventRecord(tb, c->stream);
+            cudaEventSynchronize(tb);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ta, tb);
+            rc = S.finish(nev, lam, res, Y, st, ms * 1e-3);
+            if (rc == EVSL_OK) {
+                const int s2 = S.status();
+                if (s2 == EVSL_ERR_NOCONV) rc = ctx_fail(c, s2, "chebSI: some wanted pairs did not reach tol in %d passes",
+                                                         o->maxit > 0 ? o->maxit : 100);
+                else rc = status_message(c, s2, cap, 0);
+            }
+        }
+    }
+    cudaEventDestroy(ta);
+    cudaEventDestroy(tb);
+    return rc;
+}
 
 int drv_chebLanTr_batch(evsl_ctx *c, int njobs, evsl_slice_job *jobs, const evsl_lan_opts *o)
 {

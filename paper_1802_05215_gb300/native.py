@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
         "evsl_filter_apply_multi": (i32, [P, i32, P, P, P, i32]),
         "evsl_chebLanTr": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_chebLanNr": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
+        "evsl_chebSI": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_chebLanTr_batch": (i32, [P, i32, P, P]),
         "evsl_batch_create": (i32, [P, P, C.POINTER(P)]),
         "evsl_batch_add": (i32, [P, P]),
@@ -262,6 +263,26 @@ class Context:
                                      C.byref(stats))
         if st != EVSL_OK and not (allow_partial and st in (-4, -5)):
             self._check(st, "chebLanTr")
+        k = nev.value
+        return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
+                    stats=stats.as_dict())
+
+    def chebSI(self, a, b, filt: Filter, nv, maxit=100, tol=1e-8, seed=0, right_closed=True,
+               cap=None, Y=None, allow_partial=False):
+        """Polynomial filtered subspace iteration with a block of nv vectors; same outputs as
+        chebLanTr (stats["niter"] counts passes)."""
+        cap = cap or nv
+        opts = LanOpts(nv, maxit, 10, tol, 1e-10, seed, FP64, int(right_closed))
+        lam = np.zeros(cap)
+        res = np.zeros(cap)
+        if Y is None:
+            Y = np.zeros((cap, self.n))
+        nev = C.c_int()
+        stats = Stats()
+        st = self.lib.evsl_chebSI(self.h, a, b, C.byref(filt.pol), C.byref(opts), cap, C.byref(nev),
+                                  _addr(lam), _addr(Y), _addr(res), C.byref(stats))
+        if st != EVSL_OK and not (allow_partial and st in (-4, -5)):
+            self._check(st, "chebSI")
         k = nev.value
         return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
                     stats=stats.as_dict())

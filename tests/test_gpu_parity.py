@@ -483,6 +483,56 @@ def test_cheblannr_short_basis_reports_noconv_and_fp32_mode(ctx, nat):
     assert np.all(np.abs(r32["lam"] - ex) <= 1e-9 * np.maximum(1, np.abs(ex)))
     assert np.max(_dense_residuals(A, r32["lam"], r32["Y"][:r32["nev"]].T)) <= 1e-8
 
+
+# ------------------------------------------------------------------------------ subspace iteration
+@pytest.mark.parametrize("a,b", [(-1.0, 1.0), (3.0, 5.0), (6.0, 6.5)])
+def test_chebsi_anderson_bruteforce(ctx, nat, a, b):
+    A = I.anderson_3d(7, 4.0, 0)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    ex = ev[(ev >= a) & (ev <= b)]
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(80, 0)
+    f = nat.cheb_filter_build(a, b, lo, hi)
+    r = ctx.chebSI(a, b, f, nv=int(1.5 * len(ex)) + 20)
+    assert r["status"] == 0 and r["nev"] == len(ex)
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.maximum(1, np.abs(ex)))
+    Y = r["Y"][:r["nev"]].T
+    assert np.max(_dense_residuals(A, r["lam"], Y)) <= 1e-8
+    assert np.max(np.abs(Y.T @ Y - np.eye(r["nev"]))) <= 1e-10
+
+
+def test_chebsi_laplacian_multiplicities_and_oracle(ctx, nat, oracle_mod):
+    # the block holds every copy of the 2-D Laplacian's double eigenvalues; same eigenvalues as
+    # the oracle's subspace iteration
+    A = I.laplacian_2d(40)
+    e = lap_eigs(2, 40)
+    ex = e[(e >= 0.5) & (e <= 0.8)]
+    ctx.set_csr(A)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    f = nat.cheb_filter_build(0.5, 0.8, lo, hi)
+    nv = int(1.5 * len(ex)) + 20
+    r = ctx.chebSI(0.5, 0.8, f, nv=nv)
+    assert r["status"] == 0 and r["nev"] == len(ex)
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.maximum(1, np.abs(ex)))
+    assert np.max(_dense_residuals(A, r["lam"], r["Y"][:r["nev"]].T)) <= 1e-8
+    ro = oracle_mod.chebsi(A, 0.5, 0.8, oracle_mod.filter_build(0.5, 0.8, lo, hi), nv=nv)
+    assert ro["nev"] == r["nev"]
+    assert np.all(np.abs(ro["lam"] - r["lam"]) <= 1e-9 * np.maximum(1, np.abs(ex)))
+
+
+def test_chebsi_too_few_passes_reports_noconv(ctx, nat):
+    A = I.anderson_3d(7, 4.0, 0)
+    ev = np.linalg.eigvalsh(A.to_dense())
+    ex = ev[(ev >= 3.0) & (ev <= 5.0)]
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(80, 0)
+    f = nat.cheb_filter_build(3.0, 5.0, lo, hi)
+    r = ctx.chebSI(3.0, 5.0, f, nv=137, maxit=3, allow_partial=True)
+    assert r["status"] == -4 and r["stats"]["niter"] <= 3 and r["nev"] < len(ex)
+    for lam in r["lam"]:
+        assert np.min(np.abs(ex - lam)) <= 1e-9 * max(1.0, abs(lam))
+    assert np.all(r["res"] <= 1e-8)
+
 def test_batch_admission_respects_hbm_budget(nat):
     # a 64 MiB budget holds the matrix, the workspaces and a few jobs' bases (~6.6 MB each);
     # admission must then refuse with EVSL_ERR_NOMEM and leave the admitted jobs intact
