@@ -62,6 +62,8 @@ def _load():
         _lib.orc_cheblantr.restype = i32
         _lib.orc_cheblantr.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d,
                                        i32, i32, i32, d, d, u64, i32, P, P, P, P, P]
+        _lib.orc_landos.restype = i32
+        _lib.orc_landos.argtypes = [i64, P, P, P, i32, i32, u64, P, P, P]
         _lib.orc_chebsi.restype = i32
         _lib.orc_chebsi.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d, i32, i32, d, u64,
                                     i32, P, P, P, P, P]
@@ -179,6 +181,25 @@ def reorth(z: np.ndarray, B: np.ndarray) -> int:
     order): CGS with the DGKS test, at most two passes (Sec. 2.3).  Returns the passes."""
     assert z.flags.c_contiguous and B.flags.f_contiguous and z.dtype == B.dtype == np.float64
     return int(_load().orc_reorth_cgs(len(z), _p(z), _p(B), B.shape[1]))
+
+
+def landos(A, m, nvec, seed=0):
+    """Lanczos / Gaussian-quadrature density: nodes, weights (nvec x m) and steps used."""
+    nodes = np.zeros((nvec, m))
+    weights = np.zeros((nvec, m))
+    mused = np.zeros(nvec, dtype=np.int32)
+    _load().orc_landos(*_csr_args(A), m, nvec, seed, _p(nodes), _p(weights), _p(mused))
+    return dict(nodes=nodes, weights=weights, mused=mused)
+
+
+def landos_count(d, n, t):
+    """Cumulative count N(t) = (n / nvec) sum of the weights of the nodes <= t."""
+    nvec = d["nodes"].shape[0]
+    tot = 0.0
+    for l in range(nvec):
+        k = int(d["mused"][l])
+        tot += d["weights"][l, :k][d["nodes"][l, :k] <= t].sum()
+    return n * tot / nvec
 
 
 def chebsi(A, a, b, pol, nv, maxit=100, tol=1e-8, seed=0, cap=None, right_closed=True):

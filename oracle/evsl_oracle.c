@@ -53,7 +53,8 @@ uint64_t orc_draw(uint64_t seed, uint64_t stream, uint64_t k)
 static double orc_unit(uint64_t x) { return (double)(x >> 11) * (1.0 / 9007199254740992.0); }
 static double orc_sign(uint64_t x) { return (x >> 63) ? -1.0 : 1.0; }
 
-enum { ORC_STREAM_ANDERSON = 1, ORC_STREAM_KPM = 2, ORC_STREAM_LANCZOS = 3, ORC_STREAM_BOUNDS = 4 };
+enum { ORC_STREAM_ANDERSON = 1, ORC_STREAM_KPM = 2, ORC_STREAM_LANCZOS = 3, ORC_STREAM_BOUNDS = 4,
+       ORC_STREAM_LANDOS = 5 };
 
 /* ------------------------------------------------------------------------------------ */
 /* Sparse matrix in CSR form (Sec. 3.1): y = A x.                                          */
@@ -1147,4 +1148,62 @@ int orc_chebsi(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
     free(F.w0); free(F.w1); free(F.w2); free(V); free(W); free(AW); free(G); free(S); free(th);
     free(rr); free(r);
     return status;
+}
+
+/* Lanczos spectral density (landos; Sec. 2.1 names the Lanczos / Gaussian-quadrature DOS of
+ * Lin, Saad and Yang as the second DOS method, with no formulas).  READING: for each of nvec unit
+ * vectors v_l (uniform(-1, 1) entries from stream 5, index l n + i, normalised) an m-step Lanczos
+ * run on A with full reorthogonalisation (CGS, DGKS second pass) gives T = S diag(theta) S^T;
+ * the Gaussian quadrature of v_l^T f(A) v_l has nodes theta_j and weights tau_j = S_{1j}^2.  The
+ * density is (n / nvec) sum_l sum_j tau_lj delta(t - theta_lj).  A breakdown (beta <= 1e-13 ||Av||)
+ * ends the run of that vector (mused[l] < m: the quadrature is then exact for v_l).
+ * Outputs (nvec x m, row l = vector l): nodes, weights, mused. */
+int orc_landos(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int m, int nvec,
+               uint64_t seed, double *nodes, double *weights, int *mused)
+{
+    orc_csr A = {n, rp, ci, v};
+    if (m > n) m = (int)n;
+    double *Q = calloc((size_t)n * (m + 1), sizeof(double));
+    double *T = calloc((size_t)m * m, sizeof(double)), *S = malloc(sizeof(double) * (size_t)m * m);
+    double *th = malloc(sizeof(double) * m), *z = malloc(sizeof(double) * n);
+    for (int l = 0; l < nvec; l++) {
+        double *q0 = Q;
+        for (int64_t i = 0; i < n; i++)
+            q0[i] = 2.0 * orc_unit(orc_draw(seed, ORC_STREAM_LANDOS, (uint64_t)l * (uint64_t)n + (uint64_t)i)) - 1.0;
+        double nq = orc_nrm2(n, q0);
+        for (int64_t i = 0; i < n; i++) q0[i] /= nq;
+        memset(T, 0, sizeof(double) * (size_t)m * m);
+        int k = 0;
+        double beta = 0.0;
+        for (int j = 0; j < m; j++) {
+            double *qj = Q + (size_t)j * n;
+            orc_matvec(&A, qj, z);
+            double nz = orc_nrm2(n, z);
+            if (j > 0)
+                for (int64_t i = 0; i < n; i++) z[i] -= beta * Q[(size_t)(j - 1) * n + i];
+            double alpha = orc_dot(n, qj, z);
+            for (int64_t i = 0; i < n; i++) z[i] -= alpha * qj[i];
+            orc_reorth(n, z, NULL, 0, Q, j + 1);
+            AT(T, j, j, m) = alpha;
+            k = j + 1;
+            beta = orc_nrm2(n, z);
+            if (j + 1 == m || beta <= 1e-13 * nz) break;
+            AT(T, j, j + 1, m) = beta;
+            AT(T, j + 1, j, m) = beta;
+            for (int64_t i = 0; i < n; i++) Q[(size_t)(j + 1) * n + i] = z[i] / beta;
+        }
+        double *Tk = malloc(sizeof(double) * (size_t)k * k), *Sk = malloc(sizeof(double) * (size_t)k * k);
+        for (int c = 0; c < k; c++)
+            for (int r = 0; r < k; r++) AT(Tk, r, c, k) = AT(T, r, c, m);
+        orc_syev(k, Tk, th, Sk);
+        for (int j = 0; j < m; j++) {
+            nodes[(size_t)l * m + j] = j < k ? th[j] : 0.0;
+            weights[(size_t)l * m + j] = j < k ? AT(Sk, 0, j, k) * AT(Sk, 0, j, k) : 0.0;
+        }
+        mused[l] = k;
+        free(Tk);
+        free(Sk);
+    }
+    free(Q); free(T); free(S); free(th); free(z);
+    return 0;
 }

@@ -31,6 +31,7 @@ STREAM_ANDERSON = 1     # Anderson disorder, k = row index
 STREAM_KPM = 2          # KPM Rademacher probes, k = probe * n + row
 STREAM_LANCZOS = 3      # Lanczos start vectors, k = restart_index * n + row
 STREAM_BOUNDS = 4       # start vector of the spectral-bounds Lanczos run, k = row
+STREAM_LANDOS = 5       # start vectors of the Lanczos density runs, k = vector * n + row
 
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)

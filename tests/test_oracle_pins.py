@@ -411,6 +411,51 @@ def test_chebsi_too_few_passes_reports_noconv(oracle_mod):
         assert np.min(np.abs(ex - lam)) <= 1e-9 * max(1.0, abs(lam))
     assert np.all(r["res"] <= 1e-8)
 
+
+# ---------------------------------------------------------------- Lanczos density (quadrature)
+def test_landos_full_run_is_the_exact_spectral_measure(oracle_mod):
+    # a full-length run on a matrix with distinct eigenvalues: the nodes are the eigenvalues and
+    # the weights (v . x_j)^2 for the normalised seeded start vector v (stream 5, vector 0)
+    A = I.anderson_3d(7, 4.0, 0)
+    w, Z = np.linalg.eigh(A.to_dense())
+    v = I.start_vector(A.n, 3, I.STREAM_LANDOS, 0)
+    v /= np.linalg.norm(v)
+    d = oracle_mod.landos(A, A.n, 1, 3)
+    k = int(d["mused"][0])
+    assert k == A.n
+    assert np.max(np.abs(np.sort(d["nodes"][0, :k]) - w)) <= 1e-10 * np.abs(w).max()
+    order = np.argsort(d["nodes"][0, :k])
+    assert np.max(np.abs(d["weights"][0, :k][order] - (Z.T @ v) ** 2)) <= 1e-10
+
+
+def test_landos_quadrature_is_exact_to_degree_2m_minus_1(oracle_mod):
+    # m-point Gauss quadrature from m Lanczos steps integrates t^p exactly for p <= 2m - 1:
+    # sum_j tau_j theta_j^p = v^T A^p v (v the normalised start vector), and sum_j tau_j = 1
+    A = I.laplacian_3d(10)
+    D = A.to_dense()
+    m, nvec = 6, 3
+    d = oracle_mod.landos(A, m, nvec, 7)
+    for l in range(nvec):
+        v = I.start_vector(A.n, 7, I.STREAM_LANDOS, l)
+        v /= np.linalg.norm(v)
+        th, tau = d["nodes"][l, :m], d["weights"][l, :m]
+        x = v.copy()
+        for p in range(2 * m):
+            assert abs(np.sum(tau * th ** p) - v @ x) <= 1e-10 * 12.0 ** p
+            x = D @ x
+
+
+def test_landos_count_tracks_closed_form(oracle_mod):
+    # the cumulative quadrature count estimates the exact eigenvalue count of a 12^3 Laplacian
+    # (statistical: 30 vectors; the count at the top is n exactly)
+    A = I.laplacian_3d(12)
+    e = lap_eigs(3, 12)
+    d = oracle_mod.landos(A, 40, 30, 1)
+    assert abs(oracle_mod.landos_count(d, A.n, 13.0) - A.n) <= 1e-9 * A.n
+    for t in (2.0, 4.0, 6.0, 8.0, 10.0):
+        exact = np.count_nonzero(e <= t)
+        assert abs(oracle_mod.landos_count(d, A.n, t) - exact) <= 0.03 * A.n
+
 def test_cheblantr_half_open_slices_partition(oracle_mod):
     # adjacent half-open slices [a, cut) and [cut, b] neither lose nor duplicate eigenvalues
     # (cut midway between two distinct eigenvalues, so rounding cannot decide membership)
