@@ -64,6 +64,8 @@ def _load():
                                        i32, i32, i32, d, d, u64, i32, P, P, P, P, P]
         _lib.orc_landos.restype = i32
         _lib.orc_landos.argtypes = [i64, P, P, P, i32, i32, u64, P, P, P]
+        _lib.orc_slicer_landos.restype = i32
+        _lib.orc_slicer_landos.argtypes = [P, P, P, i32, i32, i64, d, d, i32, P, P]
         _lib.orc_chebsi.restype = i32
         _lib.orc_chebsi.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d, i32, i32, d, u64,
                                     i32, P, P, P, P, P]
@@ -200,6 +202,22 @@ def landos_count(d, n, t):
         k = int(d["mused"][l])
         tot += d["weights"][l, :k][d["nodes"][l, :k] <= t].sum()
     return n * tot / nvec
+
+
+def slicer_landos(d, n, xi, eta, ns):
+    """Slices of [xi, eta] with equal quadrature counts (spslicer2 reading)."""
+    m = d["nodes"].shape[1]
+    nvec = d["nodes"].shape[0]
+    sli = np.zeros(ns + 1)
+    est = np.zeros(ns)
+    nodes = np.ascontiguousarray(d["nodes"])
+    weights = np.ascontiguousarray(d["weights"])
+    mused = np.ascontiguousarray(d["mused"], dtype=np.int32)
+    st = _load().orc_slicer_landos(_p(nodes), _p(weights), mused.ctypes.data_as(C.c_void_p), m, nvec, n,
+                                   xi, eta, ns, _p(sli), _p(est))
+    if st != 0:
+        raise ValueError("no quadrature node in [xi, eta]")
+    return sli, est
 
 
 def chebsi(A, a, b, pol, nv, maxit=100, tol=1e-8, seed=0, cap=None, right_closed=True):

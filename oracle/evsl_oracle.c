@@ -1207,3 +1207,62 @@ int orc_landos(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
     free(Q); free(T); free(S); free(th); free(z);
     return 0;
 }
+
+/* Slicer on the Lanczos density (spslicer2; the paper names it with no definition).  READING: the
+ * cumulative count N(t) = (n / nvec) sum of the weights of the nodes <= t is a step function.
+ * With C0 = N just below xi and C1 = N(eta), boundary t_i (0 < i < ns) is placed midway between
+ * the first node in [xi, eta] at which N reaches C0 + (i / ns)(C1 - C0) and the node before it
+ * (xi if there is none); t_0 = xi, t_ns = eta; est[i] = N(t_{i+1}) - N(t_i) (with N just below
+ * xi for i = 0).  Returns 0, or -1 if no node lies in [xi, eta]. */
+int orc_slicer_landos(const double *nodes, const double *weights, const int *mused, int m, int nvec,
+                      int64_t n, double xi, double eta, int ns, double *sli, double *est)
+{
+    int tot = 0;
+    for (int l = 0; l < nvec; l++) tot += mused[l];
+    double *t = malloc(sizeof(double) * (tot > 0 ? tot : 1)), *w = malloc(sizeof(double) * (tot > 0 ? tot : 1));
+    int q = 0;
+    for (int l = 0; l < nvec; l++)
+        for (int j = 0; j < mused[l]; j++) {
+            t[q] = nodes[(size_t)l * m + j];
+            w[q] = weights[(size_t)l * m + j] * (double)n / (double)nvec;
+            q++;
+        }
+    /* insertion sort by node (stable) */
+    for (int i = 1; i < tot; i++) {
+        double ti = t[i], wi = w[i];
+        int j = i - 1;
+        while (j >= 0 && t[j] > ti) { t[j + 1] = t[j]; w[j + 1] = w[j]; j--; }
+        t[j + 1] = ti;
+        w[j + 1] = wi;
+    }
+    double c0 = 0.0, c1 = 0.0;
+    int first = -1, last = -1;
+    for (int i = 0; i < tot; i++) {
+        if (t[i] < xi) c0 += w[i];
+        if (t[i] <= eta) c1 += w[i];
+        if (t[i] >= xi && t[i] <= eta) { if (first < 0) first = i; last = i; }
+    }
+    if (first < 0) { free(t); free(w); return -1; }
+    sli[0] = xi;
+    sli[ns] = eta;
+    double cum = c0;
+    int p = first;
+    for (int s = 1; s < ns; s++) {
+        double target = c0 + (double)s / ns * (c1 - c0);
+        while (p <= last && cum + w[p] < target) { cum += w[p]; p++; }
+        if (p > last) p = last;
+        double prev = (p > first) ? t[p - 1] : xi;
+        sli[s] = 0.5 * (prev + t[p]);
+    }
+    for (int s = 0; s < ns; s++) {
+        double lo = 0.0, hi = 0.0;
+        for (int i = 0; i < tot; i++) {
+            if (t[i] < sli[s]) lo += w[i];
+            if (s + 1 == ns ? t[i] <= sli[s + 1] : t[i] < sli[s + 1]) hi += w[i];
+        }
+        est[s] = hi - lo;
+    }
+    free(t);
+    free(w);
+    return 0;
+}

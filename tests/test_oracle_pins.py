@@ -456,6 +456,25 @@ def test_landos_count_tracks_closed_form(oracle_mod):
         exact = np.count_nonzero(e <= t)
         assert abs(oracle_mod.landos_count(d, A.n, t) - exact) <= 0.03 * A.n
 
+
+def test_slicer_landos_balances_within_one_node(oracle_mod):
+    # the slices partition [xi, eta]; their counts add up to the total, and each differs from
+    # the equal share by at most the largest single node weight (first-crossing rule); on an
+    # Anderson model (no multiple eigenvalues) the exact counts of the slices are balanced
+    A = I.anderson_3d(12, 4.0, 0)
+    e = np.linalg.eigvalsh(A.to_dense())
+    d = oracle_mod.landos(A, 80, 200, 2)
+    xi, eta, ns = 1.0, 5.0, 4
+    sli, est = oracle_mod.slicer_landos(d, A.n, xi, eta, ns)
+    assert sli[0] == xi and sli[-1] == eta and np.all(np.diff(sli) > 0)
+    total = oracle_mod.landos_count(d, A.n, eta) - oracle_mod.landos_count(d, A.n, np.nextafter(xi, -1))
+    assert abs(est.sum() - total) <= 1e-9 * A.n
+    wmax = A.n * d["weights"].max() / d["nodes"].shape[0]
+    assert np.all(np.abs(est - total / ns) <= wmax + 1e-9 * A.n)
+    exact = np.array([np.count_nonzero((e >= sli[i]) & ((e < sli[i + 1]) if i < ns - 1 else (e <= sli[i + 1])))
+                      for i in range(ns)])
+    assert exact.max() / exact.min() <= 1.3
+
 def test_cheblantr_half_open_slices_partition(oracle_mod):
     # adjacent half-open slices [a, cut) and [cut, b] neither lose nor duplicate eigenvalues
     # (cut midway between two distinct eigenvalues, so rounding cannot decide membership)
