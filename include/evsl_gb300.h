@@ -214,6 +214,24 @@ int evsl_chebLanTr(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol,
                    const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
                    double *res, evsl_stats *stats);
 
+/* Lanczos spectral density (landos; Sec. 2.1 names the Lanczos / Gaussian-quadrature method of
+ * Lin, Saad and Yang as the alternative to KPM).  For each of nvec seeded unit vectors (stream 5),
+ * an m-step Lanczos run on A with full reorthogonalisation gives T = S diag(theta) S^T; the
+ * quadrature of v^T f(A) v has nodes theta_j and weights S_{1j}^2, and the density is
+ * (n / nvec) sum_l sum_j w_lj delta(t - theta_lj).  Outputs on the HOST (row l = vector l,
+ * m entries): nodes, weights, and mused[l] <= m, the steps actually run (a breakdown, beta <=
+ * 1e-13 ||A q||, ends a run early: the quadrature is then exact for that vector). */
+int evsl_landos(evsl_ctx *ctx, int m, int nvec, uint64_t seed, double *nodes, double *weights, int *mused);
+
+/* Slicer on the Lanczos density (spslicer2; host only, no context).  The cumulative count is the
+ * step function N(t) = (n / nvec) sum of the weights of the nodes <= t; with C0 = N just below xi
+ * and C1 = N(eta), boundary t_i (0 < i < nslices) lies midway between the first node in [xi, eta]
+ * where N reaches C0 + (i / nslices)(C1 - C0) and the node before it.  sli[nslices + 1] and
+ * est[nslices] (estimated count per slice) caller-owned.  EVSL_ERR_ARG if no node lies in
+ * [xi, eta] or the arguments are invalid. */
+int evsl_slice_by_landos(const double *nodes, const double *weights, const int *mused, int m, int nvec,
+                         int64_t n, double xi, double eta, int nslices, double *sli, double *est);
+
 /* Filtered non-restart Lanczos (ChebLanNr, the variant the paper times in Tables 2 and 4; the
  * paper gives it no listing, and this is Algorithm 2 without restarts or locking).  One Krylov
  * basis of rho(A) with full reorthogonalisation grows up to opts->m vectors (opts->maxit is not

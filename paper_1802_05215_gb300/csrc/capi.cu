@@ -280,6 +280,26 @@ int evsl_chebLanNr(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, con
     return drv_chebLanTr(c, a, b, pol, opts, cap, nev, lam, Y, res, stats, true);
 }
 
+int evsl_landos(evsl_ctx *c, int m, int nvec, uint64_t seed, double *nodes, double *weights, int *mused)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (m < 1 || nvec < 1 || !nodes || !weights || !mused) return ctx_fail(c, EVSL_ERR_ARG, "landos: bad arguments");
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "landos: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_landos(c, m, nvec, seed, nodes, weights, mused);
+}
+
+int evsl_slice_by_landos(const double *nodes, const double *weights, const int *mused, int m, int nvec,
+                         int64_t n, double xi, double eta, int nslices, double *sli, double *est)
+{
+    if (!nodes || !weights || !mused || m < 1 || nvec < 1 || n < 1 || !(eta > xi) || nslices < 1 || !sli || !est)
+        return EVSL_ERR_ARG;
+    for (int l = 0; l < nvec; l++)
+        if (mused[l] < 0 || mused[l] > m) return EVSL_ERR_ARG;
+    return host_slicer_landos(nodes, weights, mused, m, nvec, n, xi, eta, nslices, sli, est);
+}
+
 int evsl_chebSI(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *opts,
                 int cap, int *nev, double *lam, double *Y, double *res, evsl_stats *stats)
 {

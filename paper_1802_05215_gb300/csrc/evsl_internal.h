@@ -11,7 +11,8 @@
 #include "../../include/evsl_gb300.h"
 
 // SplitMix64 stream tags (must agree with the seeded-input definition used by callers).
-enum { SM_STREAM_ANDERSON = 1, SM_STREAM_KPM = 2, SM_STREAM_LANCZOS = 3, SM_STREAM_BOUNDS = 4 };
+enum { SM_STREAM_ANDERSON = 1, SM_STREAM_KPM = 2, SM_STREAM_LANCZOS = 3, SM_STREAM_BOUNDS = 4,
+       SM_STREAM_LANDOS = 5 };
 
 constexpr int SELL_C = 32;  // rows per ELLPACK slice (one warp)
 
@@ -205,6 +206,9 @@ int filter_apply_dev(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doubl
 int filter_apply_multi_dev(evsl_ctx *c, int npol, const evsl_polfilt *pols, const double *X,
                            double *Y, evsl_precision prec);
 int drv_chebLanTr_batch(evsl_ctx *c, int njobs, evsl_slice_job *jobs, const evsl_lan_opts *o);
+int drv_landos(evsl_ctx *c, int m, int nvec, uint64_t seed, double *nodes, double *weights, int *mused);
+int host_slicer_landos(const double *nodes, const double *weights, const int *mused, int m, int nvec,
+                       int64_t n, double xi, double eta, int ns, double *sli, double *est);
 int drv_chebSI(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *o, int cap,
                int *nev, double *lam, double *Y, double *res, evsl_stats *st);
 int batch_create(evsl_ctx *c, const evsl_lan_opts *o, evsl_batch **out);

@@ -249,3 +249,51 @@ int host_count_below(int k, int l, const double *d, const double *e, double sigm
     }
     return neg;
 }
+
+// ------------------------------------------------------------------------------------------
+// Slices with equal counts under the Lanczos quadrature density.  The cumulative count
+// N(t) = (n / nvec) sum of the weights of the nodes <= t is a step function; with C0 = N just
+// below xi and C1 = N(eta), boundary t_i (0 < i < ns) lies midway between the first node in
+// [xi, eta] at which N reaches C0 + (i / ns)(C1 - C0) and the node before it (xi if none).
+int host_slicer_landos(const double *nodes, const double *weights, const int *mused, int m, int nvec,
+                       int64_t n, double xi, double eta, int ns, double *sli, double *est)
+{
+    std::vector<std::pair<double, double>> nw;
+    for (int l = 0; l < nvec; l++)
+        for (int j = 0; j < mused[l]; j++)
+            nw.emplace_back(nodes[(size_t)l * m + j], weights[(size_t)l * m + j] * (double)n / (double)nvec);
+    std::stable_sort(nw.begin(), nw.end(), [](const std::pair<double, double> &x, const std::pair<double, double> &y) {
+        return x.first < y.first;
+    });
+    double c0 = 0.0, c1 = 0.0;
+    int first = -1, last = -1;
+    for (int i = 0; i < (int)nw.size(); i++) {
+        if (nw[i].first < xi) c0 += nw[i].second;
+        if (nw[i].first <= eta) c1 += nw[i].second;
+        if (nw[i].first >= xi && nw[i].first <= eta) {
+            if (first < 0) first = i;
+            last = i;
+        }
+    }
+    if (first < 0) return EVSL_ERR_ARG;
+    sli[0] = xi;
+    sli[ns] = eta;
+    double cum = c0;
+    int p = first;
+    for (int s = 1; s < ns; s++) {
+        const double target = c0 + (double)s / ns * (c1 - c0);
+        while (p <= last && cum + nw[p].second < target) cum += nw[p++].second;
+        if (p > last) p = last;
+        const double prev = (p > first) ? nw[p - 1].first : xi;
+        sli[s] = 0.5 * (prev + nw[p].first);
+    }
+    for (int s = 0; s < ns; s++) {
+        double lo = 0.0, hi = 0.0;
+        for (const auto &q : nw) {
+            if (q.first < sli[s]) lo += q.second;
+            if (s + 1 == ns ? q.first <= sli[s + 1] : q.first < sli[s + 1]) hi += q.second;
+        }
+        est[s] = hi - lo;
+    }
+    return EVSL_OK;
+}

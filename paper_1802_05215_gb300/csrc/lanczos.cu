@@ -458,6 +458,78 @@ int drv_kpm(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, doubl
 }
 
 // ------------------------------------------------------------------------------------------
+// Lanczos / Gaussian-quadrature density: for each of nvec seeded unit vectors, an m-step Lanczos
+// run on A with full reorthogonalisation; T = S diag(theta) S^T gives the quadrature nodes theta_j
+// and weights S_{1j}^2.  A breakdown (beta <= 1e-13 ||A q_j||) ends that vector's run early.
+int drv_landos(evsl_ctx *c, int m, int nvec, uint64_t seed, double *nodes, double *weights, int *mused)
+{
+    const int64_t n = c->A.n;
+    const int mm = (int)std::min<int64_t>(m, n);
+    int st = EVSL_OK;
+    double *Q = (double *)ctx_ws(c, WS_LAN_Q, sizeof(double) * n * (mm + 1), &st);
+    if (st) return st;
+    double *z = (double *)ctx_ws(c, WS_LAN_VEC, sizeof(double) * n * 3, &st);
+    if (st) return st;
+    double *sc = (double *)ctx_ws(c, WS_SCAL, sizeof(double) * (Scal::H + mm + 8), &st);
+    if (st) return st;
+    double *h = sc + Scal::H;
+    const int M = std::max(2, mm + (mm & 1));
+    double *V = (double *)ctx_ws(c, WS_LAN_T, sizeof(double) * (size_t)M * M, &st);
+    if (st) return st;
+    for (int l = 0; l < nvec; l++) {
+        EVSL_TRY(fill_uniform_f64(c, n, seed, SM_STREAM_LANDOS, (uint64_t)l, Q));
+        EVSL_TRY(coldot(c, n, 1, Q, n, Q, n, sc + Scal::TMP));
+        double nq2 = 0;
+        EVSL_TRY(d2h(c, &nq2, sc + Scal::TMP, sizeof(double)));
+        EVSL_TRY(scale_vec(c, n, Q, 1.0 / std::sqrt(nq2), nullptr));
+        std::vector<double> T((size_t)mm * mm, 0.0);
+        double beta = 0.0;
+        int k = 0;
+        for (int j = 0; j < mm; j++) {
+            double *qj = Q + (int64_t)j * n;
+            EVSL_TRY(spmv_f64(c, 1, qj, z));
+            EVSL_TRY(coldot(c, n, 1, z, n, z, n, sc + Scal::NRM_Y));
+            EVSL_TRY(lan_three_term(c, n, z, j > 0 ? Q + (int64_t)(j - 1) * n : nullptr, beta, qj, z, sc + Scal::ALPHA));
+            EVSL_TRY(lan_sub_alpha(c, n, z, qj, sc + Scal::ALPHA, sc + Scal::NRM_BEFORE));
+            EVSL_TRY(cgs_pass(c, z, Q, j + 1, nullptr, 0, h, sc + Scal::NRM_AFTER));
+            double hs[4];
+            EVSL_TRY(d2h(c, hs, sc, sizeof(double) * 4));
+            double nrm2 = hs[2];
+            if (hs[2] < DGKS_ETA2 * hs[1]) {
+                EVSL_TRY(cgs_pass(c, z, Q, j + 1, nullptr, 0, h, sc + Scal::NRM_AFTER));
+                EVSL_TRY(d2h(c, &nrm2, sc + Scal::NRM_AFTER, sizeof(double)));
+            }
+            T[(size_t)j * mm + j] = hs[0];
+            k = j + 1;
+            beta = std::sqrt(nrm2);
+            if (j + 1 == mm || beta <= 1e-13 * std::sqrt(hs[3])) break;
+            T[(size_t)(j + 1) * mm + j] = beta;
+            T[(size_t)j * mm + j + 1] = beta;
+            EVSL_TRY(scale_vec(c, n, z, 1.0 / beta, Q + (int64_t)(j + 1) * n));
+        }
+        std::vector<double> Tk((size_t)k * k), w(k), s0(k);
+        for (int jj = 0; jj < k; jj++)
+            for (int ii = 0; ii < k; ii++) Tk[(size_t)jj * k + ii] = T[(size_t)jj * mm + ii];
+        int ldv = 0, sweeps = 0;
+        EVSL_TRY(jacobi_eig(c, k, Tk.data(), w.data(), V, &ldv, &sweeps));
+        // first row of the eigenvector matrix
+        cudaError_t e = cudaMemcpy2DAsync(s0.data(), sizeof(double), V, sizeof(double) * ldv, sizeof(double), k,
+                                          cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "landos first row");
+        for (int j = 0; j < mm; j++) {
+            nodes[(size_t)l * m + j] = j < k ? w[j] : 0.0;
+            weights[(size_t)l * m + j] = j < k ? s0[j] * s0[j] : 0.0;
+        }
+        for (int j = mm; j < m; j++) {
+            nodes[(size_t)l * m + j] = 0.0;
+            weights[(size_t)l * m + j] = 0.0;
+        }
+        mused[l] = k;
+    }
+    return EVSL_OK;
+}
+
 int drv_bounds(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax)
 {
     const int64_t n = c->A.n;

@@ -95,6 +95,8 @@ def load(build_if_missing: bool = True):
         "evsl_chebLanTr": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_chebLanNr": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_chebSI": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
+        "evsl_landos": (i32, [P, i32, i32, u64, P, P, P]),
+        "evsl_slice_by_landos": (i32, [P, P, P, i32, i32, i64, d, d, i32, P, P]),
         "evsl_chebLanTr_batch": (i32, [P, i32, P, P]),
         "evsl_batch_create": (i32, [P, P, C.POINTER(P)]),
         "evsl_batch_add": (i32, [P, P]),
@@ -154,6 +156,22 @@ def cheb_filter_build(a, b, lmin, lmax, tau=0.8, tau_ext=0.4, damping=DAMP_JACKS
         raise EvslError(st, "cheb_filter_build")
     coef = coef[:pol.deg + 1].copy()
     return Filter(pol, coef, st)
+
+
+def slice_by_landos(d, n, xi, eta, nslices):
+    """Slices of [xi, eta] with equal counts under a Lanczos quadrature density d (from
+    Context.landos); returns (sli, est)."""
+    lib = load()
+    nodes = np.ascontiguousarray(d["nodes"], dtype=np.float64)
+    weights = np.ascontiguousarray(d["weights"], dtype=np.float64)
+    mused = np.ascontiguousarray(d["mused"], dtype=np.int32)
+    sli = np.zeros(nslices + 1)
+    est = np.zeros(nslices)
+    st = lib.evsl_slice_by_landos(_addr(nodes), _addr(weights), mused.ctypes.data, nodes.shape[1],
+                                  nodes.shape[0], n, xi, eta, nslices, _addr(sli), _addr(est))
+    if st != EVSL_OK:
+        raise EvslError(st, "slice_by_landos")
+    return sli, est
 
 
 def slice_by_dos(mu, n, lmin, lmax, xi, eta, nslices, npts=0):
@@ -266,6 +284,15 @@ class Context:
         k = nev.value
         return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
                     stats=stats.as_dict())
+
+    def landos(self, m, nvec, seed=0):
+        """Lanczos quadrature density: dict of nodes, weights (nvec x m) and mused."""
+        nodes = np.zeros((nvec, m))
+        weights = np.zeros((nvec, m))
+        mused = np.zeros(nvec, dtype=np.int32)
+        self._check(self.lib.evsl_landos(self.h, m, nvec, seed, _addr(nodes), _addr(weights),
+                                         mused.ctypes.data), "landos")
+        return dict(nodes=nodes, weights=weights, mused=mused)
 
     def chebSI(self, a, b, filt: Filter, nv, maxit=100, tol=1e-8, seed=0, right_closed=True,
                cap=None, Y=None, allow_partial=False):

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from conftest import ROOT, golden
+from paper_1802_05215_gb300 import inputs as I
 
 HEADER = os.path.join(ROOT, "include", "evsl_gb300.h")
 
@@ -80,6 +81,19 @@ def test_slicer_matches_oracle(native, oracle_mod):
         so, eo = oracle_mod.slicer(mu, lo, hi, 0.3, 2.5, ns, npts or None)
         assert np.max(np.abs(s - so)) < 1e-12 and np.max(np.abs(e - eo)) < 1e-9
 
+
+
+def test_slicer_landos_matches_oracle(native, oracle_mod):
+    # the host slicer on a Lanczos quadrature density (nodes and weights from the oracle)
+    A = I.anderson_3d(12, 4.0, 0)
+    d = oracle_mod.landos(A, 60, 50, 4)
+    for xi, eta, ns in [(1.0, 5.0, 4), (-0.5, 12.0, 7), (6.0, 6.5, 2)]:
+        sli, est = native.slice_by_landos(d, A.n, xi, eta, ns)
+        sli_o, est_o = oracle_mod.slicer_landos(d, A.n, xi, eta, ns)
+        assert np.allclose(sli, sli_o, rtol=0, atol=1e-12)
+        assert np.allclose(est, est_o, rtol=0, atol=1e-9 * A.n)
+    with pytest.raises(native.EvslError):
+        native.slice_by_landos(d, A.n, 50.0, 60.0, 3)
 
 def test_context_needs_a_gpu(native):
     # without a usable device the library refuses instead of computing on the CPU

@@ -533,6 +533,24 @@ def test_chebsi_too_few_passes_reports_noconv(ctx, nat):
         assert np.min(np.abs(ex - lam)) <= 1e-9 * max(1.0, abs(lam))
     assert np.all(r["res"] <= 1e-8)
 
+
+# ------------------------------------------------------------------------------ Lanczos density
+def test_landos_matches_oracle(ctx, nat, oracle_mod):
+    # same seeded start vectors: the quadrature nodes and weights agree with the oracle's, and the
+    # slices cut from them agree too
+    A = I.anderson_3d(12, 4.0, 0)
+    ctx.set_csr(A)
+    m, nvec = 40, 6
+    dg = ctx.landos(m, nvec, 4)
+    do = oracle_mod.landos(A, m, nvec, 4)
+    assert np.array_equal(dg["mused"], do["mused"])
+    assert np.max(np.abs(dg["nodes"] - do["nodes"])) <= 1e-9 * 12.0
+    assert np.max(np.abs(dg["weights"] - do["weights"])) <= 1e-9
+    assert np.allclose(dg["weights"].sum(axis=1), 1.0, atol=1e-12)
+    sli, est = nat.slice_by_landos(dg, A.n, 1.0, 5.0, 4)
+    sli_o, est_o = oracle_mod.slicer_landos(do, A.n, 1.0, 5.0, 4)
+    assert np.allclose(est, est_o, atol=1e-6 * A.n)
+
 def test_batch_admission_respects_hbm_budget(nat):
     # a 64 MiB budget holds the matrix, the workspaces and a few jobs' bases (~6.6 MB each);
     # admission must then refuse with EVSL_ERR_NOMEM and leave the admitted jobs intact
