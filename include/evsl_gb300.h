@@ -219,7 +219,7 @@ int evsl_chebLanTr(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol,
  * an m-step Lanczos run on A with full reorthogonalisation gives T = S diag(theta) S^T; the
  * quadrature of v^T f(A) v has nodes theta_j and weights S_{1j}^2, and the density is
  * (n / nvec) sum_l sum_j w_lj delta(t - theta_lj).  Outputs on the HOST (row l = vector l,
- * m entries): nodes, weights, and mused[l] <= m, the steps actually run (a breakdown, beta <=
+ * m entries): nodes (ascending within a row), their weights, and mused[l] <= m, the steps actually run (a breakdown, beta <=
  * 1e-13 ||A q||, ends a run early: the quadrature is then exact for that vector). */
 int evsl_landos(evsl_ctx *ctx, int m, int nvec, uint64_t seed, double *nodes, double *weights, int *mused);
 

@@ -517,9 +517,12 @@ int drv_landos(evsl_ctx *c, int m, int nvec, uint64_t seed, double *nodes, doubl
                                           cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return ctx_cuda(c, e, "landos first row");
+        std::vector<int> order(k);
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] < w[y]; });
         for (int j = 0; j < mm; j++) {
-            nodes[(size_t)l * m + j] = j < k ? w[j] : 0.0;
-            weights[(size_t)l * m + j] = j < k ? s0[j] * s0[j] : 0.0;
+            nodes[(size_t)l * m + j] = j < k ? w[order[j]] : 0.0;
+            weights[(size_t)l * m + j] = j < k ? s0[order[j]] * s0[order[j]] : 0.0;
         }
         for (int j = mm; j < m; j++) {
             nodes[(size_t)l * m + j] = 0.0;
