@@ -49,6 +49,8 @@ def _load():
         _lib.orc_bounds.argtypes = [i64, P, P, P, i32, u64, P, P]
         _lib.orc_kpm_moments.restype = i32
         _lib.orc_kpm_moments.argtypes = [i64, P, P, P, i32, i32, u64, d, d, P]
+        _lib.orc_kpm_moments_doubling.restype = i32
+        _lib.orc_kpm_moments_doubling.argtypes = [i64, P, P, P, i32, i32, u64, d, d, P]
         _lib.orc_jackson.argtypes = [i32, P]
         _lib.orc_dos_count.restype = d
         _lib.orc_dos_count.argtypes = [P, i32, d, d, d]
@@ -121,6 +123,13 @@ def bounds(A, steps: int = 80, seed: int = 0):
     if st != 0:
         raise RuntimeError("oracle bounds failed")
     return lo.value, hi.value
+
+
+def kpm_moments_doubling(A, degree: int, nvec: int, seed: int, lmin: float, lmax: float) -> np.ndarray:
+    """KPM moments from ceil(degree/2) recurrence steps (doubling identities)."""
+    mu = np.empty(degree + 1)
+    _load().orc_kpm_moments_doubling(*_csr_args(A), degree, nvec, seed, lmin, lmax, _p(mu))
+    return mu
 
 
 def kpm_moments(A, degree: int, nvec: int, seed: int, lmin: float, lmax: float) -> np.ndarray:

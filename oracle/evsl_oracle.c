@@ -1266,3 +1266,41 @@ int orc_slicer_landos(const double *nodes, const double *weights, const int *mus
     free(w);
     return 0;
 }
+
+/* KPM moments with the doubling identities (the moment-doubling variant of the KPM density,
+ * listed beside kpmdos; Chebyshev identities T_{2k} = 2 T_k^2 - T_0 and
+ * T_{2k+1} = 2 T_{k+1} T_k - T_1): with w_k = T_k(Ahat) v_l,
+ *   mu_{2k} = (1/nvec) sum_l (2 w_k^T w_k - v_l^T v_l),
+ *   mu_{2k+1} = (1/nvec) sum_l (2 w_{k+1}^T w_k - v_l^T w_1),
+ * so moments up to M need only ceil(M/2) recurrence steps.  Same probes as orc_kpm_moments. */
+int orc_kpm_moments_doubling(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                             int M, int nvec, uint64_t seed, double lmin, double lmax, double *mu)
+{
+    orc_csr A = {n, rp, ci, v};
+    double c = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+    double *w0 = malloc(sizeof(double) * n), *w1 = malloc(sizeof(double) * n), *w2 = malloc(sizeof(double) * n);
+    for (int k = 0; k <= M; k++) mu[k] = 0.0;
+    const int K = (M + 1) / 2;   /* w_0 .. w_K are formed; 2K >= M */
+    for (int l = 0; l < nvec; l++) {
+        for (int64_t i = 0; i < n; i++)
+            w0[i] = orc_sign(orc_draw(seed, ORC_STREAM_KPM, (uint64_t)l * (uint64_t)n + (uint64_t)i));
+        const double m0 = orc_dot(n, w0, w0);
+        mu[0] += m0;
+        if (M == 0) continue;
+        orc_mapped_matvec(&A, c, d, w0, w1);
+        const double m1 = orc_dot(n, w0, w1);
+        mu[1] += m1;
+        /* k = 1: mu_2 = 2 w1.w1 - m0, mu_3 = 2 w2.w1 - m1, ... */
+        for (int k = 1; k <= K; k++) {
+            if (2 * k <= M) mu[2 * k] += 2.0 * orc_dot(n, w1, w1) - m0;
+            if (2 * k + 1 > M) break;
+            orc_mapped_matvec(&A, c, d, w1, w2);
+            for (int64_t i = 0; i < n; i++) w2[i] = 2.0 * w2[i] - w0[i];
+            mu[2 * k + 1] += 2.0 * orc_dot(n, w2, w1) - m1;
+            double *t = w0; w0 = w1; w1 = w2; w2 = t;
+        }
+    }
+    for (int k = 0; k <= M; k++) mu[k] /= nvec;
+    free(w0); free(w1); free(w2);
+    return 0;
+}

@@ -164,6 +164,18 @@ def test_kpm_statistics_against_closed_form_trace(oracle_mod):
         assert abs(mu[k] - tk.sum()) <= 6 * sig + 1e-9
 
 
+
+@pytest.mark.parametrize("M", [0, 1, 7, 40])
+def test_kpm_doubling_matches_direct_moments(oracle_mod, M):
+    # T_{2k} = 2 T_k^2 - T_0 and T_{2k+1} = 2 T_{k+1} T_k - T_1: the doubled moments equal the
+    # directly computed ones (same probes) up to rounding; mu_0 = n exactly
+    A = I.anderson_3d(8, 4.0, 0)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    mu_d = oracle_mod.kpm_moments(A, M, 5, 3, lo, hi)
+    mu_x = oracle_mod.kpm_moments_doubling(A, M, 5, 3, lo, hi)
+    assert mu_x[0] == A.n
+    assert np.max(np.abs(mu_x - mu_d)) <= 1e-11 * A.n
+
 def test_jackson_coefficients_identities(oracle_mod):
     for M in [1, 5, 80, 300]:
         g = oracle_mod.jackson(M)
