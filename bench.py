@@ -690,6 +690,14 @@ def run_kpm_200(args):
             per = ms / nl * 1e-3
             out[name] = {"mu": mu, "seconds": wall, "step_us": per * 1e6, "GBs": alg / per / 1e9,
                          "frac_of_hbm": alg / per / 1e9 / peaks()[0]}
+        for prec, name in [(native.FP64, "fp64_doubling"), (native.FP32, "fp32_doubling")]:
+            ctx.kpm_dos(M, nv, SEED, lo, hi, prec=prec, doubling=True)     # warm-up
+            t0 = time.perf_counter()
+            mu_d = ctx.kpm_dos(M, nv, SEED, lo, hi, prec=prec, doubling=True)
+            wall = time.perf_counter() - t0
+            ref = out["fp64"]["mu"]
+            out[name] = {"seconds": wall, "steps": (M + 1) // 2,
+                         "max_moment_diff_vs_fp64_direct_rel_n": float(np.max(np.abs(mu_d - ref)) / A.n)}
         mu1 = ctx.kpm_dos(M, 1, SEED, lo, hi, prec=native.FP64)
     err32 = float(np.max(np.abs(out["fp32"]["mu"] - out["fp64"]["mu"])) / A.n)
     check = {}
@@ -721,7 +729,8 @@ def run_kpm_200(args):
             "dtype": "f32 and f64", "data": "synthetic",
             "fp64": {k2: v for k2, v in out["fp64"].items() if k2 != "mu"},
             "fp32": {k2: v for k2, v in out["fp32"].items() if k2 != "mu"},
-            "fp32_vs_fp64_max_moment_err_rel_n": err32, "dos_l1_fp32_vs_fp64": l1, **check}
+            "fp32_vs_fp64_max_moment_err_rel_n": err32, "dos_l1_fp32_vs_fp64": l1,
+            "doubling": {k2: out[k2] for k2 in ("fp64_doubling", "fp32_doubling")}, **check}
     print(json.dumps(line), flush=True)
     return line
 

@@ -85,6 +85,15 @@ int evsl_bounds(evsl_ctx *ctx, int steps, uint64_t seed, double *lmin, double *l
 int evsl_kpm_dos(evsl_ctx *ctx, int degree, int nvec, uint64_t seed, double lmin, double lmax,
                  evsl_precision prec, double *mu);
 
+/* KPM moments by the doubling identities (the moment-doubling variant the KPM literature uses
+ * with T_{2k} = 2 T_k^2 - T_0 and T_{2k+1} = 2 T_{k+1} T_k - T_1): the same mu[0..degree], same
+ * probes, from ceil(degree/2) recurrence steps instead of degree:
+ * mu_{2k} = (1/nvec) sum_l (2 ||w_k||^2 - n), mu_{2k+1} = (1/nvec) sum_l (2 w_{k+1}^T w_k - v_l^T w_1)
+ * with w_k = T_k(Ahat) v_l.  Results differ from evsl_kpm_dos by rounding only (the identities
+ * are exact); arguments and errors as evsl_kpm_dos. */
+int evsl_kpm_dos_doubling(evsl_ctx *ctx, int degree, int nvec, uint64_t seed, double lmin, double lmax,
+                          evsl_precision prec, double *mu);
+
 /* DOS slicer (Sec. 2.1, Eq. (2.2); spslicer).  Pure host function, no context.  From the
  * Jackson-damped KPM density it places npts evenly spaced points on [xi, eta], and puts the
  * slice ends t_1..t_{ns-1} where the cumulative count crosses i/ns of the total (first crossing,

@@ -216,6 +216,18 @@ int evsl_kpm_dos(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, 
     return drv_kpm(c, degree, nvec, seed, lmin, lmax, prec, mu);
 }
 
+int evsl_kpm_dos_doubling(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax,
+                          evsl_precision prec, double *mu)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!mu || degree < 0 || nvec < 1 || !(lmax > lmin) || (prec != EVSL_FP64 && prec != EVSL_FP32))
+        return ctx_fail(c, EVSL_ERR_ARG, "kpm_dos_doubling: bad arguments");
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "kpm_dos_doubling: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_kpm(c, degree, nvec, seed, lmin, lmax, prec, mu, true);
+}
+
 int evsl_slice_by_dos(const double *mu, int degree, int64_t n, double lmin, double lmax,
                       double xi, double eta, int nslices, int npts, double *sli, double *est)
 {

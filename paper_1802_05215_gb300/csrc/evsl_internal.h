@@ -132,10 +132,12 @@ int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0);
 // index k, per-block partial sums of sum_l sum_i v_l[i] out_l[i] into part + k*nblk.
 int kpm_step_f64(evsl_ctx *c, int mode, int nvec, uint64_t seed, const double *x,
                  const double *xprev, double *out, double cc, double sc, double *part, int k,
-                 int nblk, bool hat);
+                 int nblk, bool hat,
+                 bool dbl = false);
 int kpm_step_f32(evsl_ctx *c, int mode, int nvec, uint64_t seed, const float *x,
                  const float *xprev, float *out, double cc, double sc, double *part, int k,
-                 int nblk, bool hat);
+                 int nblk, bool hat,
+                 bool dbl = false);
 int kpm_nblocks(evsl_ctx *c);
 int convert_f64_to_f32(evsl_ctx *c, int64_t count, const double *x, float *y);
 int convert_f32_to_f64(evsl_ctx *c, int64_t count, const float *x, double *y);
@@ -225,7 +227,8 @@ int drv_filter_apply(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doubl
 int drv_filter_apply_multi(evsl_ctx *c, int npol, const evsl_polfilt *pols, const double *X,
                            double *Y, evsl_precision prec);
 int drv_kpm(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax,
-            evsl_precision prec, double *mu);
+            evsl_precision prec, double *mu,
+            bool doubling = false);
 
 #define EVSL_TRY(expr)                  \
     do {                                \

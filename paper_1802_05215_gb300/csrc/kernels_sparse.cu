@@ -236,26 +236,28 @@ template <> struct VecN<float, 4> { using type = float4; };
 // part[0..gridDim.x).  Each lane sums its share of one slice in the block's precision and adds
 // it to an FP64 partial, so the sums across slices are FP64 in both precisions (FP64 issue is
 // 1/64 of FP32 here).
-template <typename T, bool HAT, int PPL>
+// DBL (the moment-doubling form): instead of the probe-weighted sum the step accumulates
+// sum out.x_row (w_{k+1}^T w_k, into part) and sum out.out (||w_{k+1}||^2, into part2).
+template <typename T, bool HAT, int PPL, bool DBL>
 __global__ void __launch_bounds__(TPB, 4)
 k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
            const int32_t *__restrict__ col, const T *__restrict__ val, const int32_t *__restrict__ rlen,
            int nvec, int ld, const uint32_t *__restrict__ bits, const T *__restrict__ x, const T *xprev,
-           T *out, T cc, T sc, double *__restrict__ part)
+           T *out, T cc, T sc, double *__restrict__ part, double *__restrict__ part2)
 {
     using VL = typename VecN<T, PPL>::type;
     constexpr int LPR = 64 / PPL;   // lanes per row
     constexpr int RPI = 32 / LPR;   // rows per warp at a time
-    __shared__ double red[TPB / 32];
+    __shared__ double red[TPB / 32], red2[TPB / 32];
     const int lane = threadIdx.x & 31;
     const int sub = lane % LPR, rsub = lane / LPR;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nw = (nvec + 31) >> 5;
-    double mom = 0.0;
+    double mom = 0.0, mom2 = 0.0;
     for (int64_t s = warp; s < nslices; s += nwarps) {
         const int64_t sbase = sptr[s];
-        T smom = T(0);  // this lane's share of the slice, in the block's precision
+        T smom = T(0), smom2 = T(0);  // this lane's share of the slice, in the block's precision
         for (int rr0 = 0; rr0 < 32; rr0 += RPI) {
             const int rr = rr0 + rsub;
             const int64_t r = s * 32 + rr;
@@ -310,24 +312,45 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                         }
                     }
                     *reinterpret_cast<VL *>(out + o) = *reinterpret_cast<const VL *>(w);
-                    const uint32_t word = bits[r * nw + (l >> 5)];
-                    const int b = l & 31;
+                    if (DBL) {
+                        T xr[PPL];
+                        *reinterpret_cast<VL *>(xr) = *reinterpret_cast<const VL *>(x + o);
 #pragma unroll
-                    for (int q = 0; q < PPL; q++)
-                        if (l + q < nvec) smom += ((word >> (b + q)) & 1u) ? -w[q] : w[q];
+                        for (int q = 0; q < PPL; q++) {
+                            smom += w[q] * xr[q];     // padding probes are zero on both sides
+                            smom2 += w[q] * w[q];
+                        }
+                    } else {
+                        const uint32_t word = bits[r * nw + (l >> 5)];
+                        const int b = l & 31;
+#pragma unroll
+                        for (int q = 0; q < PPL; q++)
+                            if (l + q < nvec) smom += ((word >> (b + q)) & 1u) ? -w[q] : w[q];
+                    }
                 }
             }
         }
         mom += (double)smom;
+        mom2 += (double)smom2;
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mom += __shfl_xor_sync(0xffffffffu, mom, off);
-    if (lane == 0) red[threadIdx.x >> 5] = mom;
+    for (int off = 16; off > 0; off >>= 1) {
+        mom += __shfl_xor_sync(0xffffffffu, mom, off);
+        if (DBL) mom2 += __shfl_xor_sync(0xffffffffu, mom2, off);
+    }
+    if (lane == 0) {
+        red[threadIdx.x >> 5] = mom;
+        red2[threadIdx.x >> 5] = mom2;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < TPB / 32; i++) t += red[i];
+        double t = 0.0, t2 = 0.0;
+        for (int i = 0; i < TPB / 32; i++) {
+            t += red[i];
+            t2 += red2[i];
+        }
         part[blockIdx.x] = t;
+        if (DBL) part2[blockIdx.x] = t2;
     }
 }
 
@@ -789,40 +812,54 @@ static int kpm_init_t(evsl_ctx *c, int nvec, uint64_t seed, T *W0)
 int kpm_init_f64(evsl_ctx *c, int nvec, uint64_t seed, double *W0) { return kpm_init_t(c, nvec, seed, W0); }
 int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0) { return kpm_init_t(c, nvec, seed, W0); }
 
+template <typename T, bool DBL>
+static void launch_kpm(evsl_ctx *c, bool hat, const T *val, int mode, int nvec, int ld, const uint32_t *bits,
+                       const T *x, const T *xprev, T *out, T cc, T sc, int nblk, double *p1, double *p2)
+{
+    const DevMatrix &A = c->A;
+    constexpr int PPL = sizeof(T) == 8 ? 2 : 4;
+    if (hat)
+        k_kpm_step<T, true, PPL, DBL><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, A.rlen,
+                                                                    nvec, ld, bits, x, xprev, out, cc, sc, p1, p2);
+    else
+        k_kpm_step<T, false, PPL, DBL><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, A.rlen,
+                                                                     nvec, ld, bits, x, xprev, out, cc, sc, p1, p2);
+}
+
+// dbl: the doubling form; the step's partials go to rows 2j-1 (w_j^T w_{j-1}) and 2j
+// (||w_j||^2) of `part` for the step that forms w_j (k = j), else to row k
 template <typename T>
 static int kpm_step_t(evsl_ctx *c, int mode, int nvec, const T *x, const T *xprev, T *out,
-                      double cc, double sc, double *part, int k, int nblk, const T *val, bool hat)
+                      double cc, double sc, double *part, int k, int nblk, const T *val, bool hat,
+                      bool dbl = false)
 {
     int st = EVSL_OK;
     uint32_t *bits = kpm_bits(c, nvec, &st);
     if (st) return st;
     const DevMatrix &A = c->A;
     const int ld = kpm_ld(nvec);
-    constexpr int PPL = sizeof(T) == 8 ? 2 : 4;
-    if (hat && A.vhat) {
-        const T *hv = sizeof(T) == 8 ? (const T *)A.vhat : (const T *)A.vhat32;
-        k_kpm_step<T, true, PPL><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, hv, A.rlen,
-                                                              nvec, ld, bits, x, xprev, out, (T)cc, (T)sc,
-                                                              part + (int64_t)k * nblk);
-    } else {
-        k_kpm_step<T, false, PPL><<<nblk, TPB, 0, c->stream>>>(mode, A.n, A.nslices, A.sptr, A.col, val, A.rlen,
-                                                               nvec, ld, bits, x, xprev, out, (T)cc, (T)sc,
-                                                               part + (int64_t)k * nblk);
-    }
+    const bool h = hat && A.vhat;
+    const T *v = h ? (sizeof(T) == 8 ? (const T *)A.vhat : (const T *)A.vhat32) : val;
+    if (dbl)
+        launch_kpm<T, true>(c, h, v, mode, nvec, ld, bits, x, xprev, out, (T)cc, (T)sc, nblk,
+                            part + (int64_t)(2 * k - 1) * nblk, part + (int64_t)(2 * k) * nblk);
+    else
+        launch_kpm<T, false>(c, h, v, mode, nvec, ld, bits, x, xprev, out, (T)cc, (T)sc, nblk,
+                             part + (int64_t)k * nblk, nullptr);
     c->launches++;
     return check_launch(c, "kpm_step");
 }
 
 int kpm_step_f64(evsl_ctx *c, int mode, int nvec, uint64_t, const double *x, const double *xprev,
-                 double *out, double cc, double sc, double *part, int k, int nblk, bool hat)
+                 double *out, double cc, double sc, double *part, int k, int nblk, bool hat, bool dbl)
 {
-    return kpm_step_t<double>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val, hat);
+    return kpm_step_t<double>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val, hat, dbl);
 }
 
 int kpm_step_f32(evsl_ctx *c, int mode, int nvec, uint64_t, const float *x, const float *xprev,
-                 float *out, double cc, double sc, double *part, int k, int nblk, bool hat)
+                 float *out, double cc, double sc, double *part, int k, int nblk, bool hat, bool dbl)
 {
-    return kpm_step_t<float>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val32, hat);
+    return kpm_step_t<float>(c, mode, nvec, x, xprev, out, cc, sc, part, k, nblk, c->A.val32, hat, dbl);
 }
 
 int convert_f64_to_f32(evsl_ctx *c, int64_t count, const double *x, float *y)

@@ -398,9 +398,12 @@ int drv_filter_apply_multi(evsl_ctx *c, int npol, const evsl_polfilt *pols, cons
     return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, "filter_apply_multi");
 }
 
+// KPM moments mu_0..M.  doubling: only ceil(M/2) recurrence steps; step j yields
+// sum_l w_j^T w_{j-1} and sum_l ||w_j||^2, from which T_{2j} = 2 T_j^2 - T_0 and
+// T_{2j-1} = 2 T_j T_{j-1} - T_1 give mu_{2j} and mu_{2j-1}.
 template <typename T>
 static int kpm_run(evsl_ctx *c, int M, int nvec, uint64_t seed, double lmin, double lmax,
-                   double *mu)
+                   double *mu, bool doubling)
 {
     const int64_t n = c->A.n, N = n * (int64_t)kpm_ld(nvec);   // row-major probe blocks
     const double cc = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
@@ -410,9 +413,11 @@ static int kpm_run(evsl_ctx *c, int M, int nvec, uint64_t seed, double lmin, dou
     T *W1 = (T *)ctx_ws(c, WS_W1, sizeof(T) * N, &st);
     if (st) return st;
     const int nb = kpm_nblocks(c);
-    double *part = (double *)ctx_ws(c, WS_KPM_PART, sizeof(double) * (size_t)(M + 1) * nb, &st);
+    const int K = doubling ? (M + 1) / 2 : M;          // recurrence steps
+    const int rows = doubling ? 2 * K + 1 : M + 1;     // partial-sum rows 0..rows-1
+    double *part = (double *)ctx_ws(c, WS_KPM_PART, sizeof(double) * (size_t)rows * nb, &st);
     if (st) return st;
-    double *dmu = (double *)ctx_ws(c, WS_SCAL, sizeof(double) * (M + 1 + 16), &st);
+    double *dmu = (double *)ctx_ws(c, WS_SCAL, sizeof(double) * (rows + 16), &st);
     if (st) return st;
     const bool hat = ensure_mapped(c, cc, d, &st);
     if (st) return st;
@@ -423,38 +428,46 @@ static int kpm_run(evsl_ctx *c, int M, int nvec, uint64_t seed, double lmin, dou
     ProfGroup g;
     prof_begin(c, EVSL_K_KPM_STEP, &g);
     T *prev = W0, *cur = W1;
-    for (int k = 1; k <= M; k++) {
+    for (int k = 1; k <= K; k++) {
         // k = 1: cur = Ahat W0 ; k >= 2: prev <- 2 Ahat cur - prev, then swap
         if constexpr (sizeof(T) == 8) {
             if (k == 1)
-                EVSL_TRY(kpm_step_f64(c, 0, nvec, seed, (double *)W0, nullptr, (double *)W1, cc, 1.0 / d, part, 1, nb, hat));
+                EVSL_TRY(kpm_step_f64(c, 0, nvec, seed, (double *)W0, nullptr, (double *)W1, cc, 1.0 / d, part, 1, nb, hat, doubling));
             else
-                EVSL_TRY(kpm_step_f64(c, 1, nvec, seed, (double *)cur, (double *)prev, (double *)prev, cc, 2.0 / d, part, k, nb, hat));
+                EVSL_TRY(kpm_step_f64(c, 1, nvec, seed, (double *)cur, (double *)prev, (double *)prev, cc, 2.0 / d, part, k, nb, hat, doubling));
         } else {
             if (k == 1)
-                EVSL_TRY(kpm_step_f32(c, 0, nvec, seed, (float *)W0, nullptr, (float *)W1, cc, 1.0 / d, part, 1, nb, hat));
+                EVSL_TRY(kpm_step_f32(c, 0, nvec, seed, (float *)W0, nullptr, (float *)W1, cc, 1.0 / d, part, 1, nb, hat, doubling));
             else
-                EVSL_TRY(kpm_step_f32(c, 1, nvec, seed, (float *)cur, (float *)prev, (float *)prev, cc, 2.0 / d, part, k, nb, hat));
+                EVSL_TRY(kpm_step_f32(c, 1, nvec, seed, (float *)cur, (float *)prev, (float *)prev, cc, 2.0 / d, part, k, nb, hat, doubling));
         }
         if (k >= 2) std::swap(prev, cur);
     }
-    prof_end(c, &g, M);
-    std::vector<double> hmu(M + 1, 0.0);
-    if (M >= 1) {
-        // moments 1..M: fixed-order sums of the per-block partials
-        EVSL_TRY(reduce_rows(c, M, nb, part + nb, dmu + 1));
-        EVSL_TRY(d2h(c, hmu.data() + 1, dmu + 1, sizeof(double) * M));
+    prof_end(c, &g, K);
+    std::vector<double> hs(rows, 0.0);
+    if (rows > 1) {
+        // fixed-order sums of the per-block partials
+        EVSL_TRY(reduce_rows(c, rows - 1, nb, part + nb, dmu + 1));
+        EVSL_TRY(d2h(c, hs.data() + 1, dmu + 1, sizeof(double) * (rows - 1)));
     }
     mu[0] = (double)n;  // v^T v = n exactly for Rademacher probes
-    for (int k = 1; k <= M; k++) mu[k] = hmu[k] / nvec;
+    if (!doubling) {
+        for (int k = 1; k <= M; k++) mu[k] = hs[k] / nvec;
+        return EVSL_OK;
+    }
+    if (M >= 1) mu[1] = hs[1] / nvec;
+    for (int j = 1; j <= K; j++) {
+        if (2 * j <= M) mu[2 * j] = (2.0 * hs[2 * j] - (double)n * nvec) / nvec;
+        if (j >= 2 && 2 * j - 1 <= M) mu[2 * j - 1] = (2.0 * hs[2 * j - 1] - hs[1]) / nvec;
+    }
     return EVSL_OK;
 }
 
 int drv_kpm(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax,
-            evsl_precision prec, double *mu)
+            evsl_precision prec, double *mu, bool doubling)
 {
-    if (prec == EVSL_FP64) return kpm_run<double>(c, degree, nvec, seed, lmin, lmax, mu);
-    return kpm_run<float>(c, degree, nvec, seed, lmin, lmax, mu);
+    if (prec == EVSL_FP64) return kpm_run<double>(c, degree, nvec, seed, lmin, lmax, mu, doubling);
+    return kpm_run<float>(c, degree, nvec, seed, lmin, lmax, mu, doubling);
 }
 
 // ------------------------------------------------------------------------------------------

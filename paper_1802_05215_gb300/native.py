@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
         "evsl_set_csr": (i32, [P, i64, P, P, P]),
         "evsl_bounds": (i32, [P, i32, u64, P, P]),
         "evsl_kpm_dos": (i32, [P, i32, i32, u64, d, d, i32, P]),
+        "evsl_kpm_dos_doubling": (i32, [P, i32, i32, u64, d, d, i32, P]),
         "evsl_slice_by_dos": (i32, [P, i32, i64, d, d, d, d, i32, i32, P, P]),
         "evsl_cheb_filter_build": (i32, [d, d, d, d, P, P, P, i32]),
         "evsl_filter_apply": (i32, [P, P, i32, P, P, i32]),
@@ -238,10 +239,11 @@ class Context:
         self._check(self.lib.evsl_bounds(self.h, steps, seed, C.byref(lo), C.byref(hi)), "bounds")
         return lo.value, hi.value
 
-    def kpm_dos(self, degree, nvec, seed, lmin, lmax, prec=FP64):
+    def kpm_dos(self, degree, nvec, seed, lmin, lmax, prec=FP64, doubling=False):
+        """KPM moments mu_0..degree (doubling: from ceil(degree/2) recurrence steps)."""
         mu = np.zeros(degree + 1)
-        self._check(self.lib.evsl_kpm_dos(self.h, degree, nvec, seed, lmin, lmax, prec,
-                                          _addr(mu)), "kpm_dos")
+        fn = self.lib.evsl_kpm_dos_doubling if doubling else self.lib.evsl_kpm_dos
+        self._check(fn(self.h, degree, nvec, seed, lmin, lmax, prec, _addr(mu)), "kpm_dos")
         return mu
 
     def filter_apply(self, filt: Filter, X, Y, prec=FP64):

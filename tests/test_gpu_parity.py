@@ -62,6 +62,22 @@ def test_kpm_fp32_matches_oracle(ctx, nat, oracle_mod):
     assert np.max(np.abs(mu - mo)) <= 1e-5 * A.n
 
 
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5)])
+def test_kpm_doubling_matches_oracle(ctx, nat, oracle_mod, prec, tol):
+    # the doubled moments (half the recurrence steps) against the oracle's doubled and direct
+    # moments, same probes; odd and even degrees
+    A = I.anderson_3d(12, 4.0, 0)
+    ctx.set_csr(A)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    for M in (31, 40):
+        mu = ctx.kpm_dos(M, 9, 3, lo, hi, prec=prec, doubling=True)
+        ref = oracle_mod.kpm_moments_doubling(A, M, 9, 3, lo, hi)
+        direct = oracle_mod.kpm_moments(A, M, 9, 3, lo, hi)
+        assert mu[0] == A.n
+        assert np.max(np.abs(mu - ref)) <= tol * A.n
+        assert np.max(np.abs(mu - direct)) <= tol * A.n
+
 def test_kpm_is_deterministic(ctx):
     A = I.laplacian_3d(20)
     ctx.set_csr(A)
