@@ -102,3 +102,29 @@ def test_context_needs_a_gpu(native):
         pytest.skip("a GPU is present")
     with pytest.raises(native.EvslError):
         native.Context(0)
+
+
+
+def test_entry_points_reject_null_context_and_bad_arguments(native):
+    # every context entry point refuses a NULL context with EVSL_ERR_ARG (no device touched), and
+    # the host-only slicer validates its arguments
+    lib = native.load()
+    P, i32 = ctypes.c_void_p, ctypes.c_int
+    nul = P(0)
+    buf = (ctypes.c_double * 8)()
+    ibuf = (ctypes.c_int * 4)()
+    assert lib.evsl_chebLanNr(nul, 0.0, 1.0, nul, nul, 1, ctypes.byref(i32()), buf, nul, buf, nul) == -1
+    assert lib.evsl_chebSI(nul, 0.0, 1.0, nul, nul, 1, ctypes.byref(i32()), buf, nul, buf, nul) == -1
+    assert lib.evsl_landos(nul, 10, 2, 0, buf, buf, ibuf) == -1
+    assert lib.evsl_kpm_dos_doubling(nul, 10, 2, 0, 0.0, 1.0, 0, buf) == -1
+    assert lib.evsl_filter_apply_multi(nul, 1, nul, nul, nul, 0) == -1
+    nodes = np.array([[0.1, 0.5, 0.9]])
+    weights = np.array([[0.2, 0.3, 0.5]])
+    d = dict(nodes=nodes, weights=weights, mused=np.array([3], dtype=np.int32))
+    sli, est = native.slice_by_landos(d, 100, 0.0, 1.0, 2)
+    assert sli[0] == 0.0 and sli[-1] == 1.0 and abs(est.sum() - 100.0) <= 1e-12
+    with pytest.raises(native.EvslError):
+        native.slice_by_landos(d, 100, 1.0, 0.0, 2)           # eta <= xi
+    bad = dict(d, mused=np.array([4], dtype=np.int32))        # more steps than stored
+    with pytest.raises(native.EvslError):
+        native.slice_by_landos(bad, 100, 0.0, 1.0, 2)
