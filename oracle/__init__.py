@@ -68,6 +68,15 @@ def _load():
         _lib.orc_landos.argtypes = [i64, P, P, P, i32, i32, u64, P, P, P]
         _lib.orc_slicer_landos.restype = i32
         _lib.orc_slicer_landos.argtypes = [P, P, P, i32, i32, i64, d, d, i32, P, P]
+        _lib.orc_lspol.restype = i32
+        _lib.orc_lspol.argtypes = [d, d, d, i32, P, P]
+        _lib.orc_polyB_apply.restype = None
+        _lib.orc_polyB_apply.argtypes = [i64, P, P, P, d, d, i32, P, P, P]
+        _lib.orc_bounds_gen.restype = i32
+        _lib.orc_bounds_gen.argtypes = [i64, P, P, P, P, P, P, d, d, i32, P, i32, u64, P, P]
+        _lib.orc_cheblannr_gen.restype = i32
+        _lib.orc_cheblannr_gen.argtypes = [i64, P, P, P, P, P, P, d, d, i32, P, d, d, i32, d, d, i32, P,
+                                           d, i32, i32, d, d, u64, i32, P, P, P, P, P]
         _lib.orc_chebsi.restype = i32
         _lib.orc_chebsi.argtypes = [i64, P, P, P, d, d, i32, d, d, i32, P, d, i32, i32, d, u64,
                                     i32, P, P, P, P, P]
@@ -227,6 +236,49 @@ def slicer_landos(d, n, xi, eta, ns):
     if st != 0:
         raise ValueError("no quadrature node in [xi, eta]")
     return sli, est
+
+
+def lspol(bmin, bmax, eps=1e-13, maxdeg=200):
+    """Chebyshev interpolant p(t) ~ 1/t on [bmin, bmax] (the polynomial B^{-1}); returns a dict."""
+    coef = np.zeros(maxdeg + 1)
+    deg = C.c_int()
+    st = _load().orc_lspol(bmin, bmax, eps, maxdeg, C.byref(deg), _p(coef))
+    return dict(status=st, deg=deg.value, coef=coef[:deg.value + 1].copy(), bmin=bmin, bmax=bmax)
+
+
+def poly_solve(B, lp, x):
+    """p(B) x for an lspol dict."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    _load().orc_polyB_apply(*_csr_args(B), lp["bmin"], lp["bmax"], lp["deg"], _p(lp["coef"]), _p(x), _p(y))
+    return y
+
+
+def bounds_gen(A, B, lp, steps=80, seed=0):
+    """Spectral bounds of the pencil (A, B) by B-Lanczos on B^{-1} A."""
+    lo, hi = C.c_double(), C.c_double()
+    _load().orc_bounds_gen(*_csr_args(A), *_csr_args(B)[1:], lp["bmin"], lp["bmax"], lp["deg"], _p(lp["coef"]),
+                           steps, seed, C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+def cheblannr_gen(A, B, lp, a, b, pol, m=200, ncycle=10, tol=1e-8, tau1=1e-10, seed=0, cap=None,
+                  right_closed=True):
+    """Filtered non-restart Lanczos for A x = lambda B x (B-orthonormal eigenvectors)."""
+    cap = cap or m
+    lam = np.empty(cap)
+    res = np.empty(cap)
+    X = np.empty((A.n, cap), order="F")
+    nev = C.c_int()
+    stats = np.zeros(4, dtype=np.int64)
+    coef = np.ascontiguousarray(pol["coef"], dtype=np.float64)
+    st = _load().orc_cheblannr_gen(*_csr_args(A), *_csr_args(B)[1:], lp["bmin"], lp["bmax"], lp["deg"],
+                                   _p(lp["coef"]), a, b, int(right_closed), pol["lmin"], pol["lmax"],
+                                   len(coef) - 1, _p(coef), pol["bar"], m, ncycle, tol, tau1, seed, cap,
+                                   C.byref(nev), _p(lam), _p(X), _p(res), _p(stats))
+    k = nev.value
+    return dict(status=st, nev=k, lam=lam[:k].copy(), Y=X[:, :k].copy(), res=res[:k].copy(),
+                niter=int(stats[0]), nmv=int(stats[1]))
 
 
 def chebsi(A, a, b, pol, nv, maxit=100, tol=1e-8, seed=0, cap=None, right_closed=True):

@@ -1304,3 +1304,283 @@ int orc_kpm_moments_doubling(int64_t n, const int64_t *rp, const int32_t *ci, co
     free(w0); free(w1); free(w2);
     return 0;
 }
+
+/* ---- Generalized problems A x = lambda B x with B SPD (Sec. 2.4) and the polynomial B^{-1}
+ * of Sec. 4.3 (lsPol: "Chebyshev polynomial expansion" for the solves with a well-conditioned
+ * mass matrix B).  READING: p(t) ~ 1/t on [bmin, bmax] is the Chebyshev interpolant at the
+ * Chebyshev-Gauss points of degree k, k the smallest degree (up to maxdeg) whose relative error
+ * max |t p(t) - 1| on 2001 equispaced points is <= eps. */
+int orc_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef)
+{
+    const double c = 0.5 * (bmax + bmin), h = 0.5 * (bmax - bmin);
+    for (int k = 1; k <= maxdeg; k++) {
+        const int N = k + 1;
+        for (int j = 0; j <= k; j++) {
+            double s = 0.0;
+            for (int q = 0; q < N; q++) {
+                const double th = M_PI * (q + 0.5) / N;
+                s += cos(j * th) / (c + h * cos(th));
+            }
+            coef[j] = (j == 0 ? 1.0 : 2.0) * s / N;
+        }
+        double err = 0.0;
+        for (int q = 0; q <= 2000; q++) {
+            const double t = bmin + (bmax - bmin) * q / 2000.0, u = (t - c) / h;
+            double p = 0.0;
+            for (int j = 0; j <= k; j++) p += coef[j] * orc_chebT(j, u);
+            err = fmax(err, fabs(t * p - 1.0));
+        }
+        if (err <= eps) { *deg = k; return 0; }
+    }
+    *deg = maxdeg;
+    return -4;
+}
+
+/* y = p(B) x with the Chebyshev recurrence on Bhat = (B - c I) / h */
+static void orc_polyB(const orc_csr *B, double c, double h, int deg, const double *coef,
+                      const double *x, double *y, double *w0, double *w1, double *w2)
+{
+    int64_t n = B->n;
+    memcpy(w0, x, sizeof(double) * n);
+    for (int64_t i = 0; i < n; i++) y[i] = coef[0] * x[i];
+    if (deg == 0) return;
+    orc_mapped_matvec(B, c, h, w0, w1);
+    for (int64_t i = 0; i < n; i++) y[i] += coef[1] * w1[i];
+    for (int j = 2; j <= deg; j++) {
+        orc_mapped_matvec(B, c, h, w1, w2);
+        for (int64_t i = 0; i < n; i++) w2[i] = 2.0 * w2[i] - w0[i];
+        for (int64_t i = 0; i < n; i++) y[i] += coef[j] * w2[i];
+        double *t = w0; w0 = w1; w1 = w2; w2 = t;
+    }
+}
+
+/* Public form: y = p(B) x (the approximate solve of Sec. 4.3). */
+void orc_polyB_apply(int64_t n, const int64_t *brp, const int32_t *bci, const double *bv, double bmin,
+                     double bmax, int deg, const double *coef, const double *x, double *y)
+{
+    orc_csr B = {n, brp, bci, bv};
+    double *w = malloc(sizeof(double) * 3 * n);
+    orc_polyB(&B, 0.5 * (bmax + bmin), 0.5 * (bmax - bmin), deg, coef, x, y, w, w + n, w + 2 * n);
+    free(w);
+}
+
+typedef struct {
+    const orc_csr *A, *B;
+    double bc, bh;        /* mapping of B for the polynomial inverse */
+    int bdeg;
+    const double *bcoef;
+    double *t0, *t1, *t2; /* scratch of the polynomial solve */
+} orc_pencil;
+
+static void orc_solveB(orc_pencil *P, const double *x, double *y)
+{
+    orc_polyB(P->B, P->bc, P->bh, P->bdeg, P->bcoef, x, y, P->t0, P->t1, P->t2);
+}
+
+/* One step of the B-inner-product Lanczos (Algorithm 3, "Lanczos algorithm for Ax = lambda Bx"),
+ * with the operator applied to z_i already in `z`: z -= beta_i z_{i-1}; alpha = (z, w_i);
+ * z -= alpha z_i; full reorthogonalisation z -= sum_j (z, w_j) z_j (two passes); w = B^{-1} z;
+ * beta = (w, z)^{1/2}; w_{i+1} = w / beta, z_{i+1} = z / beta.  Returns alpha, *beta_out. */
+static double orc_lanab_step(orc_pencil *P, int i, double *W, double *Z, double *z, double beta_i,
+                             double *wtmp, double *beta_out)
+{
+    const int64_t n = P->A->n;
+    double *zi = Z + (size_t)i * n, *wi = W + (size_t)i * n;
+    if (i > 0)
+        for (int64_t r = 0; r < n; r++) z[r] -= beta_i * Z[(size_t)(i - 1) * n + r];
+    const double alpha = orc_dot(n, z, wi);
+    for (int64_t r = 0; r < n; r++) z[r] -= alpha * zi[r];
+    for (int pass = 0; pass < 2; pass++)
+        for (int j = 0; j <= i; j++) {
+            const double h = orc_dot(n, z, W + (size_t)j * n);
+            const double *zj = Z + (size_t)j * n;
+            for (int64_t r = 0; r < n; r++) z[r] -= h * zj[r];
+        }
+    orc_solveB(P, z, wtmp);
+    const double beta = sqrt(fmax(0.0, orc_dot(n, wtmp, z)));
+    if (beta > 0.0) {
+        for (int64_t r = 0; r < n; r++) W[(size_t)(i + 1) * n + r] = wtmp[r] / beta;
+        for (int64_t r = 0; r < n; r++) Z[(size_t)(i + 1) * n + r] = z[r] / beta;
+    }
+    *beta_out = beta;
+    return alpha;
+}
+
+/* seeded start: w_1 uniform(-1,1) (stream 3, index 0), z_1 = B w_1, both scaled to (w_1, z_1) = 1 */
+static void orc_lanab_start(orc_pencil *P, uint64_t seed, double *W, double *Z)
+{
+    const int64_t n = P->A->n;
+    for (int64_t i = 0; i < n; i++) W[i] = 2.0 * orc_unit(orc_draw(seed, ORC_STREAM_LANCZOS, (uint64_t)i)) - 1.0;
+    orc_matvec(P->B, W, Z);
+    const double s = sqrt(orc_dot(n, W, Z));
+    for (int64_t i = 0; i < n; i++) { W[i] /= s; Z[i] /= s; }
+}
+
+/* Bounds of the pencil's spectrum: `steps` B-Lanczos steps on B^{-1} A (unfiltered),
+ * lmin = theta_1 - |beta s_{m,1}|, lmax = theta_m + |beta s_{m,m}| (as orc_bounds). */
+int orc_bounds_gen(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                   const int64_t *brp, const int32_t *bci, const double *bv, double bmin, double bmax,
+                   int bdeg, const double *bcoef, int steps, uint64_t seed, double *lmin, double *lmax)
+{
+    orc_csr A = {n, rp, ci, v}, B = {n, brp, bci, bv};
+    double *t = malloc(sizeof(double) * 3 * n);
+    orc_pencil P = {&A, &B, 0.5 * (bmax + bmin), 0.5 * (bmax - bmin), bdeg, bcoef, t, t + n, t + 2 * n};
+    if (steps > n) steps = (int)n;
+    double *W = calloc((size_t)n * (steps + 1), sizeof(double)), *Z = calloc((size_t)n * (steps + 1), sizeof(double));
+    double *z = malloc(sizeof(double) * n), *wt = malloc(sizeof(double) * n);
+    double *T = calloc((size_t)steps * steps, sizeof(double)), *S = malloc(sizeof(double) * (size_t)steps * steps);
+    double *th = malloc(sizeof(double) * steps);
+    orc_lanab_start(&P, seed, W, Z);
+    double beta = 0.0;
+    int m = 0;
+    for (int i = 0; i < steps; i++) {
+        orc_matvec(&A, W + (size_t)i * n, z);
+        double bn = 0.0;
+        const double alpha = orc_lanab_step(&P, i, W, Z, z, beta, wt, &bn);
+        AT(T, i, i, steps) = alpha;
+        m = i + 1;
+        beta = bn;
+        if (i + 1 < steps) { AT(T, i, i + 1, steps) = beta; AT(T, i + 1, i, steps) = beta; }
+        if (!(beta > 0.0)) break;
+    }
+    double *Tm = malloc(sizeof(double) * (size_t)m * m);
+    for (int j = 0; j < m; j++)
+        for (int i = 0; i < m; i++) AT(Tm, i, j, m) = AT(T, i, j, steps);
+    orc_syev(m, Tm, th, S);
+    *lmin = th[0] - fabs(beta * AT(S, m - 1, 0, m));
+    *lmax = th[m - 1] + fabs(beta * AT(S, m - 1, m - 1, m));
+    free(t); free(W); free(Z); free(z); free(wt); free(T); free(S); free(th); free(Tm);
+    return 0;
+}
+
+/* Filtered non-restart Lanczos for A x = lambda B x (ChebLanNr with Algorithm 3 on the pencil
+ * (K, B), K = B rho(B^{-1} Ahat), Sec. 2.5): the operator applied to z_i is
+ * rho(Ahat B^{-1}) z_i, a Chebyshev recurrence on Mhat = (A B^{-1} - c I) / d (B^{-1} the
+ * polynomial solve).  Reorthogonalisation and the sum test as orc_cheblannr (two passes,
+ * reading of Algorithm 3's single pass).  Candidates: Ritz values >= bar; x = W y (B-orthonormal),
+ * lambda = x^T A x / x^T B x, dropped outside the slice, converged if
+ * ||A x - lambda B x|| <= tol ||B|| max(|lmin|, |lmax|) (||B|| by bmax).  stats: its, nmv (A), 0, 0.
+ */
+int orc_cheblannr_gen(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                      const int64_t *brp, const int32_t *bci, const double *bv, double bmin, double bmax,
+                      int bdeg, const double *bcoef, double a, double b, int right_closed, double lmin,
+                      double lmax, int deg, const double *coef, double bar, int m, int ncycle, double tol,
+                      double tau1, uint64_t seed, int cap, int *nev, double *lam, double *X, double *res,
+                      long *stats)
+{
+    orc_csr A = {n, rp, ci, v}, B = {n, brp, bci, bv};
+    double *t = malloc(sizeof(double) * 3 * n);
+    orc_pencil P = {&A, &B, 0.5 * (bmax + bmin), 0.5 * (bmax - bmin), bdeg, bcoef, t, t + n, t + 2 * n};
+    const double cc = 0.5 * (lmax + lmin), dd = 0.5 * (lmax - lmin);
+    const double scale = bmax * fmax(fabs(lmin), fabs(lmax));
+    if (m > n) m = (int)n;
+    double *W = calloc((size_t)n * (m + 1), sizeof(double)), *Z = calloc((size_t)n * (m + 1), sizeof(double));
+    double *T = calloc((size_t)(m + 1) * (m + 1), sizeof(double)), *Tk = malloc(sizeof(double) * (size_t)m * m);
+    double *S = malloc(sizeof(double) * (size_t)m * m), *th = malloc(sizeof(double) * m);
+    double *z = malloc(sizeof(double) * n), *wt = malloc(sizeof(double) * n);
+    double *f0 = malloc(sizeof(double) * n), *f1 = malloc(sizeof(double) * n), *f2 = malloc(sizeof(double) * n);
+    double *u = malloc(sizeof(double) * n), *Au = malloc(sizeof(double) * n), *Bu = malloc(sizeof(double) * n);
+    long nmv = 0;
+    int its = 0, status = 0, found = 0, done = 0, have_old = 0, prev_nabove = 0;
+    double t_old = 0.0, beta = 0.0;
+    orc_lanab_start(&P, seed, W, Z);
+    for (int i = 0; i < m && !done; i++) {
+        its++;
+        /* z = rho(Mhat) z_i: f0 = z_i, f1 = Mhat f0, f_{j+1} = 2 Mhat f_j - f_{j-1} */
+        const double *zi = Z + (size_t)i * n;
+        double *p0 = f0, *p1 = f1, *p2 = f2;
+        memcpy(p0, zi, sizeof(double) * n);
+        for (int64_t r = 0; r < n; r++) z[r] = coef[0] * p0[r];
+        for (int j = 1; j <= deg; j++) {
+            const double *src = (j == 1) ? p0 : p1;                 /* f_{j-1} */
+            double *dst = (j == 1) ? p1 : p2;                       /* f_j */
+            orc_solveB(&P, src, u);                                 /* u = B^{-1} f_{j-1} */
+            orc_matvec(&A, u, Au);
+            nmv++;
+            for (int64_t r = 0; r < n; r++) {
+                const double mf = (Au[r] - cc * src[r]) / dd;
+                dst[r] = (j == 1) ? mf : 2.0 * mf - p0[r];
+            }
+            for (int64_t r = 0; r < n; r++) z[r] += coef[j] * dst[r];
+            if (j >= 2) { double *tmp = p0; p0 = p1; p1 = p2; p2 = tmp; }
+        }
+        double bn = 0.0;
+        const double alpha = orc_lanab_step(&P, i, W, Z, z, beta, wt, &bn);
+        AT(T, i, i, m + 1) = alpha;
+        beta = bn;
+        AT(T, i, i + 1, m + 1) = beta;
+        AT(T, i + 1, i, m + 1) = beta;
+        const int k = i + 1;
+        int extract = (k == m) || !(beta > 0.0);
+        if (!extract && k % ncycle == 0) {
+            for (int jj = 0; jj < k; jj++)
+                for (int ii = 0; ii < k; ii++) AT(Tk, ii, jj, k) = AT(T, ii, jj, m + 1);
+            orc_syev(k, Tk, th, NULL);
+            double t_new = 0.0;
+            int nabove = 0;
+            for (int jj = 0; jj < k; jj++)
+                if (th[jj] >= bar) { t_new += th[jj]; nabove++; }
+            int min_empty = (2 * ncycle > m / 4) ? 2 * ncycle : m / 4;
+            if (have_old && nabove == 0 && prev_nabove == 0 && k >= min_empty) { done = 1; break; }
+            if (have_old && nabove > 0 && fabs(t_new - t_old) < tau1 * fmax(1.0, fabs(t_new))) extract = 1;
+            t_old = t_new;
+            prev_nabove = nabove;
+            have_old = 1;
+        }
+        if (!extract) continue;
+        for (int jj = 0; jj < k; jj++)
+            for (int ii = 0; ii < k; ii++) AT(Tk, ii, jj, k) = AT(T, ii, jj, m + 1);
+        orc_syev(k, Tk, th, S);
+        int nconv = 0, nunconv = 0;
+        for (int jj = k - 1; jj >= 0; jj--) {
+            if (th[jj] < bar) break;
+            for (int64_t r = 0; r < n; r++) {
+                double acc = 0.0;
+                for (int p = 0; p < k; p++) acc += W[(size_t)p * n + r] * AT(S, p, jj, k);
+                u[r] = acc;
+            }
+            orc_matvec(&B, u, Bu);
+            const double nb = sqrt(orc_dot(n, u, Bu));
+            for (int64_t r = 0; r < n; r++) { u[r] /= nb; Bu[r] /= nb; }
+            orc_matvec(&A, u, Au);
+            const double lamj = orc_dot(n, u, Au);
+            int inside = (lamj >= a) && (right_closed ? (lamj <= b) : (lamj < b));
+            if (!inside) continue;
+            for (int64_t r = 0; r < n; r++) Au[r] -= lamj * Bu[r];
+            const double rj = orc_nrm2(n, Au) / scale;
+            if (rj > tol) { nunconv++; continue; }
+            if (nconv >= cap) { status = -5; break; }
+            if (X) memcpy(X + (size_t)nconv * n, u, sizeof(double) * n);
+            lam[nconv] = lamj;
+            res[nconv] = rj;
+            nconv++;
+        }
+        found = nconv;
+        if (status == -5) break;
+        if (nunconv == 0 || k == m || !(beta > 0.0)) {
+            if (nunconv > 0) status = -4;
+            break;
+        }
+        have_old = 0;
+    }
+    for (int i = 0; i < found; i++) {                  /* ascending */
+        int best = i;
+        for (int j = i + 1; j < found; j++)
+            if (lam[j] < lam[best]) best = j;
+        if (best != i) {
+            double tt = lam[i]; lam[i] = lam[best]; lam[best] = tt;
+            tt = res[i]; res[i] = res[best]; res[best] = tt;
+            if (X)
+                for (int64_t r = 0; r < n; r++) {
+                    tt = X[(size_t)i * n + r];
+                    X[(size_t)i * n + r] = X[(size_t)best * n + r];
+                    X[(size_t)best * n + r] = tt;
+                }
+        }
+    }
+    *nev = found;
+    if (stats) { stats[0] = its; stats[1] = nmv; stats[2] = 0; stats[3] = 0; }
+    free(t); free(W); free(Z); free(T); free(Tk); free(S); free(th); free(z); free(wt);
+    free(f0); free(f1); free(f2); free(u); free(Au); free(Bu);
+    return status;
+}

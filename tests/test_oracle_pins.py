@@ -487,6 +487,60 @@ def test_slicer_landos_balances_within_one_node(oracle_mod):
                       for i in range(ns)])
     assert exact.max() / exact.min() <= 1.3
 
+
+# ---------------------------------------------------------------- generalized problems (Sec. 2.4)
+def _pencil_eigs(nx):
+    # A = T (x) I + I (x) T, B = M (x) M with M = tridiag(1, 4, 1) / 6: shared sine eigenvectors,
+    # lambda_ij = (t_i + t_j) / (m_i m_j)
+    k = np.arange(1, nx + 1)
+    t = 2.0 - 2.0 * np.cos(k * np.pi / (nx + 1))
+    m = (4.0 + 2.0 * np.cos(k * np.pi / (nx + 1))) / 6.0
+    return np.sort(((t[:, None] + t[None, :]) / (m[:, None] * m[None, :])).ravel())
+
+
+def test_pencil_generator_closed_form():
+    A, B = I.laplacian_2d(7), I.mass_matrix_2d(7)
+    import scipy.linalg as sl
+    w = sl.eigh(A.to_dense(), B.to_dense(), eigvals_only=True)
+    assert np.max(np.abs(w - _pencil_eigs(7))) <= 1e-12 * w.max()
+
+
+def test_lspol_is_a_polynomial_inverse(oracle_mod):
+    # |t p(t) - 1| <= eps on an independent fine grid, and p(B) x solves B y = x
+    lp = oracle_mod.lspol(0.11, 0.99, 1e-13)
+    assert lp["status"] == 0
+    tt = np.linspace(0.11, 0.99, 10001)
+    p = npcheb.chebval((tt - 0.55) / 0.44, lp["coef"])
+    assert np.max(np.abs(tt * p - 1.0)) <= 1.5e-13
+    B = I.mass_matrix_2d(12)
+    lo, hi = oracle_mod.bounds(B, 80, 0)
+    lp = oracle_mod.lspol(lo, hi, 1e-13)
+    x = np.random.default_rng(0).standard_normal(B.n)
+    y = oracle_mod.poly_solve(B, lp, x)
+    assert np.linalg.norm(B.to_dense() @ y - x) <= 1e-12 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("a,b", [(2.0, 3.0), (10.0, 11.0), (40.0, 42.0)])
+def test_cheblannr_gen_against_closed_form(oracle_mod, a, b):
+    # A x = lambda B x with B^{-1} by lsPol: exact count (multiplicity 2), eigenvalues, residuals
+    # ||A x - lambda B x|| and B-orthonormality against the closed form and dense products
+    nx = 20
+    A, B = I.laplacian_2d(nx), I.mass_matrix_2d(nx)
+    lam = _pencil_eigs(nx)
+    blo, bhi = oracle_mod.bounds(B, 80, 0)
+    lp = oracle_mod.lspol(blo, bhi, 1e-13)
+    lo, hi = oracle_mod.bounds_gen(A, B, lp, 80, 0)
+    assert lo <= lam[0] and hi >= lam[-1] - 1e-9 * lam[-1]
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    ex = lam[(lam >= a) & (lam <= b)]
+    r = oracle_mod.cheblannr_gen(A, B, lp, a, b, pol, m=max(6 * len(ex), 200))
+    assert r["status"] == 0 and r["nev"] == len(ex)
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.maximum(1.0, ex))
+    X, Ad, Bd = r["Y"], A.to_dense(), B.to_dense()
+    R = Ad @ X - (Bd @ X) * r["lam"]
+    assert np.max(np.linalg.norm(R, axis=0)) <= 1e-8 * bhi * hi
+    assert np.max(np.abs(X.T @ Bd @ X - np.eye(len(ex)))) <= 1e-10
+
 def test_cheblantr_half_open_slices_partition(oracle_mod):
     # adjacent half-open slices [a, cut) and [cut, b] neither lose nor duplicate eigenvalues
     # (cut midway between two distinct eigenvalues, so rounding cannot decide membership)
