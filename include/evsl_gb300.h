@@ -314,6 +314,56 @@ int evsl_batch_step(evsl_batch *batch, int *nactive, int *nfinished);
 void evsl_batch_destroy(evsl_batch *batch);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Generalized problems A x = lambda B x (Sec. 2.4-2.5) with B symmetric positive definite and
+ * well conditioned, whose inverse is replaced by a polynomial (Sec. 4.3, the lsPol solve).
+ *
+ * evsl_lspol (host only): Chebyshev coefficients c_0..c_deg of p(t) ~ 1/t on [bmin, bmax]
+ * (0 < bmin < bmax) in the variable (t - (bmax + bmin)/2) / ((bmax - bmin)/2): the interpolant at
+ * the deg + 1 Chebyshev-Gauss points, deg the smallest degree <= maxdeg whose relative error
+ * max |t p(t) - 1| over 2001 equispaced points of [bmin, bmax] is <= eps.  coef: host array of
+ * cap >= maxdeg + 1 doubles; *err (may be NULL) receives that error.  Errors: EVSL_ERR_ARG;
+ * EVSL_ERR_CAPACITY if cap < maxdeg + 1; EVSL_ERR_NOCONV if maxdeg was reached (the degree-maxdeg
+ * interpolant is returned). */
+int evsl_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, int cap,
+               double *err);
+
+/* Mass matrix B (host CSR, same conventions and errors as evsl_set_csr) with its spectrum inside
+ * [bmin, bmax], and its polynomial inverse p(B) (evsl_lspol with eps, maxdeg; *deg and *err may be
+ * NULL).  Replaces any previous B; evsl_set_csr leaves B in place.  The solvers below need B and
+ * A of the same order.  Errors: those of evsl_set_csr; EVSL_ERR_ARG if not 0 < bmin < bmax,
+ * eps <= 0 or maxdeg < 1; EVSL_ERR_NOCONV if maxdeg did not reach eps (B and the degree-maxdeg
+ * polynomial are set all the same). */
+int evsl_set_csr_b(evsl_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                   const double *val, double bmin, double bmax, double eps, int maxdeg, int *deg,
+                   double *err);
+
+/* y = p(B) x (the approximate solve with B): x, y DEVICE pointers to n doubles, y distinct from
+ * x.  Synchronous.  Errors: EVSL_ERR_ARG, EVSL_ERR_STATE without B. */
+int evsl_polyB_apply(evsl_ctx *ctx, const double *x, double *y);
+
+/* Spectral bounds of the pencil: `steps` unfiltered steps of the B-inner-product Lanczos
+ * (Algorithm 3) on B^{-1} A from a seeded start (Lanczos stream, index 0), with p(B) for B^{-1};
+ * lmin = theta_1 - |beta s_{m,1}|, lmax = theta_m + |beta s_{m,m}|.  Errors: EVSL_ERR_ARG,
+ * EVSL_ERR_STATE without A or B or with orders that differ. */
+int evsl_bounds_gen(evsl_ctx *ctx, int steps, uint64_t seed, double *lmin, double *lmax);
+
+/* Filtered non-restart Lanczos for the pencil on [a, b] (Sec. 2.5 with Algorithm 3): the
+ * operator rho((A B^{-1} - c I) / d) (pol built on the pencil's bounds; every filter degree is
+ * one solve with p(B) and one product with A) applied in the B-inner product with two full
+ * reorthogonalisation passes, at most opts->m steps.  Every opts->ncycle steps the sum of the
+ * Ritz values >= pol->bar is compared with the previous one (relative change < opts->tau1
+ * triggers an extraction); a run with no Ritz value >= bar for max(2 ncycle, m/4) steps ends
+ * with none.  Extraction: x = W y with (x, B x) = 1, lambda = x^T A x, kept in the slice,
+ * converged when ||A x - lambda B x|| <= tol * bmax * max(|lmin|, |lmax|); unconverged candidates
+ * continue the basis.  Outputs as evsl_chebLanNr (ascending; Y host or device, n x cap, the
+ * eigenvectors B-orthonormal); stats: niter, nmv (products with A), t_total.  FP64 only.
+ * Errors: EVSL_ERR_ARG, EVSL_ERR_STATE (as evsl_bounds_gen), EVSL_ERR_NOCONV (basis limit with
+ * unconverged candidates; the converged ones are returned), EVSL_ERR_CAPACITY. */
+int evsl_chebLanNr_gen(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol,
+                       const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
+                       double *res, evsl_stats *stats);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Instrumentation (no counterpart in the paper).
  * evsl_launch_count: kernels launched by this context since its creation.
  * evsl_profile: 1 starts timing the launch groups of each kernel family with CUDA events on

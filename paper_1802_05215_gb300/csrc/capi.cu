@@ -167,6 +167,7 @@ void evsl_destroy(evsl_ctx *c)
     cudaStreamSynchronize(c->stream);
     prof_resolve(c);
     sell_free(c);
+    dev_matrix_free(c, c->B);
     filter_graphs_clear(c);
     for (size_t i = 0; i < c->ws_ptr.size(); i++) ctx_free(c, c->ws_ptr[i], c->ws_bytes[i]);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -413,3 +414,68 @@ int evsl_profile_get(evsl_ctx *c, int kernel, int64_t *launches, double *ms)
 }
 
 }  // extern "C"
+
+// ---- generalized problems A x = lambda B x
+int evsl_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, int cap, double *err)
+{
+    if (!(bmin > 0.0) || !(bmax > bmin) || !(eps > 0.0) || maxdeg < 1 || !deg || !coef) return EVSL_ERR_ARG;
+    if (cap < maxdeg + 1) {
+        *deg = maxdeg;
+        return EVSL_ERR_CAPACITY;
+    }
+    return host_lspol(bmin, bmax, eps, maxdeg, deg, coef, err);
+}
+
+int evsl_set_csr_b(evsl_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *val,
+                   double bmin, double bmax, double eps, int maxdeg, int *deg, double *err)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!(bmin > 0.0) || !(bmax > bmin) || !(eps > 0.0) || maxdeg < 1)
+        return ctx_fail(c, EVSL_ERR_ARG, "set_csr_b: need 0 < bmin < bmax, eps > 0 and maxdeg >= 1");
+    std::vector<double> coef((size_t)maxdeg + 1);
+    int d = 0;
+    double e = 0.0;
+    const int pst = host_lspol(bmin, bmax, eps, maxdeg, &d, coef.data(), &e);
+    cudaSetDevice(c->device);
+    EVSL_TRY(sell_upload_b(c, n, row_ptr, col_idx, val));
+    coef.resize((size_t)d + 1);
+    c->b_coef = coef;
+    c->b_min = bmin;
+    c->b_max = bmax;
+    if (deg) *deg = d;
+    if (err) *err = e;
+    if (pst != EVSL_OK) return ctx_fail(c, pst, "set_csr_b: degree %d reached with error %g > eps %g", d, e, eps);
+    return EVSL_OK;
+}
+
+int evsl_polyB_apply(evsl_ctx *c, const double *x, double *y)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!x || !y || x == y) return ctx_fail(c, EVSL_ERR_ARG, "polyB_apply: bad arguments");
+    cudaSetDevice(c->device);
+    return drv_polyB_apply(c, x, y);
+}
+
+int evsl_bounds_gen(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!lmin || !lmax || steps < 2) return ctx_fail(c, EVSL_ERR_ARG, "bounds_gen: bad arguments");
+    cudaSetDevice(c->device);
+    return drv_bounds_gen(c, steps, seed, lmin, lmax);
+}
+
+int evsl_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *opts,
+                       int cap, int *nev, double *lam, double *Y, double *res, evsl_stats *stats)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!pol || !pol->coef || pol->deg < 0 || !opts || !nev || !lam || !res || cap < 1 || !(b > a) || opts->m < 2 ||
+        !(pol->lmax > pol->lmin))
+        return ctx_fail(c, EVSL_ERR_ARG, "chebLanNr_gen: bad arguments");
+    if (opts->prec != EVSL_FP64) return ctx_fail(c, EVSL_ERR_ARG, "chebLanNr_gen: only the FP64 filter is supported");
+    cudaSetDevice(c->device);
+    return drv_chebLanNr_gen(c, a, b, pol, opts, cap, nev, lam, Y, res, stats);
+}

@@ -49,6 +49,11 @@ struct evsl_ctx {
     std::string err;
     int64_t launches = 0;
     DevMatrix A;
+    // generalized problems A x = lambda B x: the mass matrix and p(t) ~ 1/t on [b_min, b_max]
+    // (Chebyshev coefficients, degree b_coef.size() - 1)
+    DevMatrix B;
+    double b_min = 0.0, b_max = 0.0;
+    std::vector<double> b_coef;
     // grow-only workspaces, indexed by WS_* slots
     std::vector<void *> ws_ptr;
     std::vector<size_t> ws_bytes;
@@ -85,6 +90,7 @@ enum WsSlot {
     WS_PARTIAL = 0, WS_SCAL, WS_W0, WS_W1, WS_W2, WS_KPM_PART, WS_F32_X, WS_F32_Y,
     WS_LAN_U, WS_LAN_Q, WS_LAN_Y, WS_LAN_Z, WS_LAN_VEC, WS_LAN_T, WS_LAN_S, WS_LAN_IDX,
     WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_POL_V, WS_POL_W, WS_POL_B, WS_POL_S, WS_POL_Y, WS_POL_R, WS_TUNE, WS_POL_H,
+    WS_GEN_BASIS, WS_GEN_VEC, WS_GEN_SCAL,
     WS_COUNT
 };
 
@@ -103,6 +109,10 @@ int check_launch(evsl_ctx *c, const char *what);
 int sell_upload(evsl_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col,
                 const double *val);
 void sell_free(evsl_ctx *c);
+// the mass matrix B of a generalized problem, in the same layout (c->B)
+int sell_upload_b(evsl_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                  const double *val);
+void dev_matrix_free(evsl_ctx *c, DevMatrix &M);
 // One fused Chebyshev step on nvec columns (ld = n).  mode 0: out = sc (A x - cc x),
 // y = c0 x + cj out.  mode 1: out = sc (A x - cc x) - xprev, y += cj out.  out may alias xprev.
 // hat = true uses the mapped values made current by ensure_mapped(c, cc, d) (same result up to
@@ -226,6 +236,12 @@ int drv_filter_apply(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doubl
                      double *Y, evsl_precision prec);
 int drv_filter_apply_multi(evsl_ctx *c, int npol, const evsl_polfilt *pols, const double *X,
                            double *Y, evsl_precision prec);
+// generalized problems (generalized.cu)
+int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, double *err);
+int drv_polyB_apply(evsl_ctx *c, const double *x, double *y);
+int drv_bounds_gen(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax);
+int drv_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *o,
+                      int cap, int *nev, double *lam, double *Y, double *res, evsl_stats *st);
 int drv_kpm(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax,
             evsl_precision prec, double *mu,
             bool doubling = false);

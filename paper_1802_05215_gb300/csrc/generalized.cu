@@ -1,0 +1,465 @@
+// Generalized symmetric-definite problems A x = lambda B x (Sec. 2.4-2.5) with a well-conditioned
+// mass matrix B whose inverse is replaced by a polynomial (Sec. 4.3, lsPol): p(t) ~ 1/t on
+// [bmin, bmax], applied to a vector with the Chebyshev three-term recurrence on
+// Bhat = (B - bc I) / bh.  The filter is rho((A B^{-1} - c I) / d): every degree of its
+// recurrence is one polynomial solve with B followed by one product with A, fused with the
+// recurrence update and the coefficient accumulation.  Lanczos runs in the B-inner product
+// (Algorithm 3) with two full reorthogonalisation passes; the eigenvectors come out
+// B-orthonormal.
+//
+// Kernels: one sliced-ELLPACK step (k_gen_step, a warp per 32-row slice, lane = row) whose
+// sparse operand u is separate from the shifted vector x, so that the same kernel serves the
+// solve with B (u = x) and the filter degree with A (u = p(B) x).  The Lanczos vector updates,
+// reorthogonalisation GEMVs, dot products and the small eigensolves are the dense helpers of
+// the standard path.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "evsl_internal.h"
+
+namespace {
+
+constexpr int GTPB = 256;
+constexpr double PI = 3.14159265358979323846;
+
+// Sparse step with M in sliced ELLPACK:
+//   MODE 0: out = sc (M u - cc x);          y = c0 x + cj out
+//   MODE 1: out = sc (M u - cc x) - xprev;  y += cj out
+//   MODE 2: out = M u
+// out may alias xprev (each row reads xprev[r] before writing out[r]); u is gathered across
+// rows and must not alias out or y.
+template <int MODE>
+__global__ void __launch_bounds__(GTPB)
+k_gen_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr, const int32_t *__restrict__ col,
+           const double *__restrict__ val, const double *u, const double *x, const double *xprev,
+           double *out, double *y, double cc, double sc, double c0, double cj)
+{
+    const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (s >= nslices) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t b0 = sptr[s];
+    const int w = (int)((sptr[s + 1] - b0) >> 5);
+    double acc = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < w; j++) {
+        const int64_t p = b0 + 32 * (int64_t)j + lane;
+        acc = fma(val[p], u[col[p]], acc);
+    }
+    const int64_t r = s * 32 + lane;
+    if (r >= n) return;
+    if (MODE == 2) {
+        out[r] = acc;
+        return;
+    }
+    const double xr = x[r];
+    double wv = sc * (acc - cc * xr);
+    if (MODE == 1) wv -= xprev[r];
+    out[r] = wv;
+    y[r] = (MODE == 0) ? c0 * xr + cj * wv : y[r] + cj * wv;
+}
+
+template <int MODE>
+int gen_step(evsl_ctx *c, const DevMatrix &M, const double *u, const double *x, const double *xprev,
+             double *out, double *y, double cc, double sc, double c0, double cj)
+{
+    const unsigned grid = (unsigned)((M.nslices * 32 + GTPB - 1) / GTPB);
+    k_gen_step<MODE><<<grid, GTPB, 0, c->stream>>>(M.n, M.nslices, M.sptr, M.col, M.val, u, x, xprev, out, y,
+                                                    cc, sc, c0, cj);
+    c->launches++;
+    return check_launch(c, "generalized sparse step");
+}
+
+int d2h(evsl_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, "device-to-host copy");
+}
+
+// device scalars: alpha, a scratch norm, beta^2, (x, Bx), lambda, then the projections h
+enum { S_ALPHA = 0, S_TMP = 1, S_BETA2 = 2, S_NB2 = 3, S_LAM = 4, S_RES2 = 5, S_H = 8 };
+
+// n-vectors of the generalized drivers (one workspace, carved)
+struct Vecs {
+    double *u, *t1, *t2, *f1, *f2, *z, *wt, *x, *ax, *bx;
+    static constexpr int COUNT = 10;
+};
+
+int get_vecs(evsl_ctx *c, Vecs &v)
+{
+    const int64_t n = c->A.n;
+    int st = EVSL_OK;
+    double *p = (double *)ctx_ws(c, WS_GEN_VEC, sizeof(double) * (size_t)n * Vecs::COUNT, &st);
+    if (st) return st;
+    double **slots[Vecs::COUNT] = {&v.u, &v.t1, &v.t2, &v.f1, &v.f2, &v.z, &v.wt, &v.x, &v.ax, &v.bx};
+    for (int i = 0; i < Vecs::COUNT; i++) *slots[i] = p + (int64_t)i * n;
+    return EVSL_OK;
+}
+
+// y = p(B) x: y = c_0 x + c_1 w_1 + ..., w_1 = Bhat x, w_j = 2 Bhat w_{j-1} - w_{j-2}.
+// t1, t2: temporaries; y must not alias x, t1 or t2 (x is only read).
+int solve_b(evsl_ctx *c, const double *x, double *y, double *t1, double *t2)
+{
+    const DevMatrix &B = c->B;
+    const std::vector<double> &cf = c->b_coef;
+    const int deg = (int)cf.size() - 1;
+    const double bc = 0.5 * (c->b_max + c->b_min), bh = 0.5 * (c->b_max - c->b_min);
+    if (deg == 0) return scale_vec(c, B.n, const_cast<double *>(x), cf[0], y);
+    EVSL_TRY(gen_step<0>(c, B, x, x, nullptr, t1, y, bc, 1.0 / bh, cf[0], cf[1]));
+    const double *prev = x, *cur = t1;
+    bool prev_tmp = false;  // prev is a temporary that the next term may overwrite
+    for (int j = 2; j <= deg; j++) {
+        double *out = prev_tmp ? const_cast<double *>(prev) : t2;
+        EVSL_TRY(gen_step<1>(c, B, cur, cur, prev, out, y, bc, 2.0 / bh, 0.0, cf[j]));
+        prev = cur;
+        cur = out;
+        prev_tmp = true;
+    }
+    return EVSL_OK;
+}
+
+// z = rho(Mhat) zi with Mhat = (A p(B) - cc I) / dd: f_1 = Mhat zi, f_j = 2 Mhat f_{j-1} - f_{j-2},
+// z = sum_j c_j f_j.  z must not alias zi or the temporaries.  Counts deg products with A.
+int filter_gen(evsl_ctx *c, const evsl_polfilt *pol, const double *zi, double *z, const Vecs &v, int64_t *nmv)
+{
+    const DevMatrix &A = c->A;
+    const double cc = 0.5 * (pol->lmax + pol->lmin), dd = 0.5 * (pol->lmax - pol->lmin);
+    const double *cf = pol->coef;
+    const int deg = pol->deg;
+    if (deg == 0) return scale_vec(c, A.n, const_cast<double *>(zi), cf[0], z);
+    EVSL_TRY(solve_b(c, zi, v.u, v.t1, v.t2));
+    EVSL_TRY(gen_step<0>(c, A, v.u, zi, nullptr, v.f1, z, cc, 1.0 / dd, cf[0], cf[1]));
+    const double *prev = zi, *cur = v.f1;
+    bool prev_tmp = false;
+    for (int j = 2; j <= deg; j++) {
+        EVSL_TRY(solve_b(c, cur, v.u, v.t1, v.t2));
+        double *out = prev_tmp ? const_cast<double *>(prev) : v.f2;
+        EVSL_TRY(gen_step<1>(c, A, v.u, cur, prev, out, z, cc, 2.0 / dd, 0.0, cf[j]));
+        prev = cur;
+        cur = out;
+        prev_tmp = true;
+    }
+    *nmv += deg;
+    return EVSL_OK;
+}
+
+// Seeded start of Algorithm 3: w_1 uniform(-1, 1) (Lanczos stream, index 0), z_1 = B w_1, both
+// scaled so that (w_1, z_1) = 1.
+int lanab_start(evsl_ctx *c, uint64_t seed, double *W, double *Z, double *sc)
+{
+    const int64_t n = c->A.n;
+    EVSL_TRY(fill_uniform_f64(c, n, seed, SM_STREAM_LANCZOS, 0, W));
+    EVSL_TRY(gen_step<2>(c, c->B, W, nullptr, nullptr, Z, nullptr, 0.0, 0.0, 0.0, 0.0));
+    EVSL_TRY(coldot(c, n, 1, W, n, Z, n, sc + S_NB2));
+    double s2 = 0.0;
+    EVSL_TRY(d2h(c, &s2, sc + S_NB2, sizeof(double)));
+    if (!(s2 > 0.0)) return ctx_fail(c, EVSL_ERR_ARG, "generalized Lanczos: (w, B w) = %g; B is not positive definite", s2);
+    const double inv = 1.0 / std::sqrt(s2);
+    EVSL_TRY(scale_vec(c, n, W, inv, nullptr));
+    return scale_vec(c, n, Z, inv, nullptr);
+}
+
+// One step of Algorithm 3 on z = Op w_i (already in z): z -= beta_i z_{i-1}; alpha = (z, w_i);
+// z -= alpha z_i; two passes of z -= Z_{0..i} (W_{0..i}^T z); w = p(B) z;
+// beta = (w, z)^{1/2}; w_{i+1} = w / beta, z_{i+1} = z / beta (skipped when beta = 0).
+int lanab_step(evsl_ctx *c, int i, double *W, double *Z, double *z, double beta_i, const Vecs &v, double *sc,
+               double *alpha, double *beta)
+{
+    const int64_t n = c->A.n;
+    EVSL_TRY(lan_three_term(c, n, z, i > 0 ? Z + (int64_t)(i - 1) * n : nullptr, beta_i, W + (int64_t)i * n, z,
+                            sc + S_ALPHA));
+    EVSL_TRY(lan_sub_alpha(c, n, z, Z + (int64_t)i * n, sc + S_ALPHA, sc + S_TMP));
+    for (int pass = 0; pass < 2; pass++) {
+        EVSL_TRY(gemv_t2(c, n, W, i + 1, nullptr, 0, z, sc + S_H));
+        EVSL_TRY(gemv_n2(c, n, Z, i + 1, nullptr, 0, sc + S_H, z, sc + S_TMP));
+    }
+    EVSL_TRY(solve_b(c, z, v.wt, v.t1, v.t2));
+    EVSL_TRY(coldot(c, n, 1, v.wt, n, z, n, sc + S_BETA2));
+    double hs[S_BETA2 + 1];
+    EVSL_TRY(d2h(c, hs, sc, sizeof(hs)));
+    *alpha = hs[S_ALPHA];
+    const double b = std::sqrt(std::max(0.0, hs[S_BETA2]));
+    if (b > 0.0) {
+        EVSL_TRY(scale_vec(c, n, v.wt, 1.0 / b, W + (int64_t)(i + 1) * n));
+        EVSL_TRY(scale_vec(c, n, z, 1.0 / b, Z + (int64_t)(i + 1) * n));
+    }
+    *beta = b;
+    return EVSL_OK;
+}
+
+// bases W, Z (n x (k+1) each) and the device scalars
+int get_basis(evsl_ctx *c, int k, int extra_cols, double **W, double **Z, double **X, double **sc)
+{
+    const int64_t n = c->A.n;
+    int st = EVSL_OK;
+    double *p = (double *)ctx_ws(c, WS_GEN_BASIS, sizeof(double) * (size_t)n * (2 * (size_t)(k + 1) + extra_cols), &st);
+    if (st) return st;
+    *W = p;
+    *Z = p + (int64_t)(k + 1) * n;
+    if (X) *X = p + 2 * (int64_t)(k + 1) * n;
+    *sc = (double *)ctx_ws(c, WS_GEN_SCAL, sizeof(double) * (S_H + (size_t)k + 8), &st);
+    return st;
+}
+
+// eigenpairs of the leading k x k block of the tridiagonal (ld ldt, column-major, host):
+// eigenvalues to w (host, unordered), vectors to the device buffer *V (ld *ldv)
+int tri_eig(evsl_ctx *c, int k, const std::vector<double> &T, int ldt, std::vector<double> &w, double **V, int *ldv)
+{
+    std::vector<double> Tk((size_t)k * k);
+    for (int j = 0; j < k; j++)
+        for (int i = 0; i < k; i++) Tk[(size_t)j * k + i] = T[(size_t)j * ldt + i];
+    const int M = std::max(2, k + (k & 1));
+    int st = EVSL_OK;
+    *V = (double *)ctx_ws(c, WS_LAN_T, sizeof(double) * (size_t)M * M, &st);
+    if (st) return st;
+    w.assign(k, 0.0);
+    int sweeps = 0;
+    return jacobi_eig(c, k, Tk.data(), w.data(), *V, ldv, &sweeps);
+}
+
+int check_pencil(evsl_ctx *c, const char *what)
+{
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "%s: no matrix A set", what);
+    if (c->B.n == 0 || c->b_coef.empty()) return ctx_fail(c, EVSL_ERR_STATE, "%s: no matrix B set", what);
+    if (c->B.n != c->A.n)
+        return ctx_fail(c, EVSL_ERR_STATE, "%s: A has %lld rows, B %lld", what, (long long)c->A.n, (long long)c->B.n);
+    return EVSL_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Chebyshev interpolant of 1/t on [bmin, bmax] at the N = k + 1 Chebyshev-Gauss points
+// theta_q = pi (q + 1/2) / N: c_j = (2 - [j = 0]) / N sum_q cos(j theta_q) / t(theta_q),
+// t(theta) = bc + bh cos(theta).  The degree is the smallest k <= maxdeg with
+// max |t p(t) - 1| <= eps over 2001 equispaced points of [bmin, bmax] (p by Clenshaw's sum).
+int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, double *err)
+{
+    const double bc = 0.5 * (bmax + bmin), bh = 0.5 * (bmax - bmin);
+    const int NPTS = 2001;
+    double e = 0.0;
+    for (int k = 1; k <= maxdeg; k++) {
+        const int N = k + 1;
+        std::vector<double> th(N), f(N);
+        for (int q = 0; q < N; q++) {
+            th[q] = PI * (q + 0.5) / N;
+            f[q] = 1.0 / (bc + bh * std::cos(th[q]));
+        }
+        for (int j = 0; j <= k; j++) {
+            double s = 0.0;
+            for (int q = 0; q < N; q++) s += std::cos(j * th[q]) * f[q];
+            coef[j] = s * (j == 0 ? 1.0 : 2.0) / N;
+        }
+        e = 0.0;
+        for (int q = 0; q < NPTS; q++) {
+            const double t = bmin + (bmax - bmin) * q / (NPTS - 1);
+            const double x = (t - bc) / bh;
+            double b1 = 0.0, b2 = 0.0;  // Clenshaw: b_j = c_j + 2 x b_{j+1} - b_{j+2}
+            for (int j = k; j >= 1; j--) {
+                const double b0 = coef[j] + 2.0 * x * b1 - b2;
+                b2 = b1;
+                b1 = b0;
+            }
+            const double p = coef[0] + x * b1 - b2;
+            e = std::max(e, std::fabs(t * p - 1.0));
+        }
+        if (e <= eps) {
+            *deg = k;
+            if (err) *err = e;
+            return EVSL_OK;
+        }
+    }
+    *deg = maxdeg;
+    if (err) *err = e;
+    return EVSL_ERR_NOCONV;
+}
+
+int drv_polyB_apply(evsl_ctx *c, const double *x, double *y)
+{
+    if (c->B.n == 0 || c->b_coef.empty()) return ctx_fail(c, EVSL_ERR_STATE, "polyB_apply: no matrix B set");
+    const int64_t n = c->B.n;
+    int st = EVSL_OK;
+    double *t = (double *)ctx_ws(c, WS_GEN_VEC, sizeof(double) * (size_t)n * Vecs::COUNT, &st);
+    if (st) return st;
+    EVSL_TRY(solve_b(c, x, y, t, t + n));
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, "polyB_apply");
+}
+
+// Bounds of the pencil's spectrum from `steps` unfiltered steps of Algorithm 3 on B^{-1} A:
+// lmin = theta_1 - |beta s_{m,1}|, lmax = theta_m + |beta s_{m,m}|.
+int drv_bounds_gen(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax)
+{
+    EVSL_TRY(check_pencil(c, "bounds_gen"));
+    const int64_t n = c->A.n;
+    if (steps > n) steps = (int)n;
+    double *W, *Z, *sc;
+    EVSL_TRY(get_basis(c, steps, 0, &W, &Z, nullptr, &sc));
+    Vecs v;
+    EVSL_TRY(get_vecs(c, v));
+    EVSL_TRY(lanab_start(c, seed, W, Z, sc));
+    std::vector<double> T((size_t)steps * steps, 0.0);
+    double beta = 0.0;
+    int m = 0;
+    for (int i = 0; i < steps; i++) {
+        EVSL_TRY(gen_step<2>(c, c->A, W + (int64_t)i * n, nullptr, nullptr, v.z, nullptr, 0.0, 0.0, 0.0, 0.0));
+        double alpha = 0.0, bn = 0.0;
+        EVSL_TRY(lanab_step(c, i, W, Z, v.z, beta, v, sc, &alpha, &bn));
+        T[(size_t)i * steps + i] = alpha;
+        m = i + 1;
+        beta = bn;
+        if (i + 1 < steps) {
+            T[(size_t)(i + 1) * steps + i] = beta;
+            T[(size_t)i * steps + i + 1] = beta;
+        }
+        if (!(beta > 0.0)) break;
+    }
+    std::vector<double> w;
+    double *V = nullptr;
+    int ldv = 0;
+    EVSL_TRY(tri_eig(c, m, T, steps, w, &V, &ldv));
+    const int imin = (int)(std::min_element(w.begin(), w.end()) - w.begin());
+    const int imax = (int)(std::max_element(w.begin(), w.end()) - w.begin());
+    double smin = 0.0, smax = 0.0;
+    EVSL_TRY(d2h(c, &smin, V + (int64_t)imin * ldv + (m - 1), sizeof(double)));
+    EVSL_TRY(d2h(c, &smax, V + (int64_t)imax * ldv + (m - 1), sizeof(double)));
+    *lmin = w[imin] - std::fabs(beta * smin);
+    *lmax = w[imax] + std::fabs(beta * smax);
+    return EVSL_OK;
+}
+
+// Filtered non-restart Lanczos for A x = lambda B x: Algorithm 3 on the pencil (B rho, B) with
+// the operator rho((A B^{-1} - c I) / d) applied to z_i.  Every ncycle steps the Ritz values
+// >= bar of T_k are summed; extraction when the sum is stable (relative change < tau1), at the
+// basis limit m, or on breakdown; a run whose Ritz values stayed below bar for
+// max(2 ncycle, m / 4) steps ends with none.  Extraction: for Ritz values >= bar (largest
+// first), x = W y scaled to (x, B x) = 1, lambda = x^T A x, kept inside the slice, converged if
+// ||A x - lambda B x|| <= tol ||B|| max(|lmin|, |lmax|) (||B|| by bmax).  Unconverged
+// candidates continue the basis.  Eigenpairs are returned in ascending order.
+int drv_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *o, int cap,
+                      int *nev, double *lam, double *Y, double *res, evsl_stats *stats)
+{
+    EVSL_TRY(check_pencil(c, "chebLanNr_gen"));
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t n = c->A.n;
+    int m = o->m;
+    if (m > n) m = (int)n;
+    const int ncycle = o->ncycle > 0 ? o->ncycle : 10;
+    const double bar = pol->bar;
+    const double scale = c->b_max * std::max(std::fabs(pol->lmin), std::fabs(pol->lmax));
+    double *W, *Z, *Xc, *sc;
+    EVSL_TRY(get_basis(c, m, cap, &W, &Z, &Xc, &sc));
+    Vecs v;
+    EVSL_TRY(get_vecs(c, v));
+    EVSL_TRY(lanab_start(c, o->seed, W, Z, sc));
+    const int ldt = m + 1;
+    std::vector<double> T((size_t)ldt * ldt, 0.0), w;
+    std::vector<double> lam_c(cap), res_c(cap);
+    int64_t nmv = 0;
+    int its = 0, status = EVSL_OK, found = 0, prev_nabove = 0;
+    bool have_old = false;
+    double t_old = 0.0, beta = 0.0;
+    for (int i = 0; i < m; i++) {
+        its++;
+        EVSL_TRY(filter_gen(c, pol, Z + (int64_t)i * n, v.z, v, &nmv));
+        double alpha = 0.0, bn = 0.0;
+        EVSL_TRY(lanab_step(c, i, W, Z, v.z, beta, v, sc, &alpha, &bn));
+        T[(size_t)i * ldt + i] = alpha;
+        beta = bn;
+        T[(size_t)(i + 1) * ldt + i] = beta;
+        T[(size_t)i * ldt + i + 1] = beta;
+        const int k = i + 1;
+        bool extract = (k == m) || !(beta > 0.0);
+        double *V = nullptr;
+        int ldv = 0;
+        if (!extract && k % ncycle == 0) {
+            EVSL_TRY(tri_eig(c, k, T, ldt, w, &V, &ldv));
+            double t_new = 0.0;
+            int nabove = 0;
+            for (double th : w)
+                if (th >= bar) {
+                    t_new += th;
+                    nabove++;
+                }
+            const int min_empty = std::max(2 * ncycle, m / 4);
+            if (have_old && nabove == 0 && prev_nabove == 0 && k >= min_empty) break;
+            if (have_old && nabove > 0 && std::fabs(t_new - t_old) < o->tau1 * std::max(1.0, std::fabs(t_new)))
+                extract = true;
+            t_old = t_new;
+            prev_nabove = nabove;
+            have_old = true;
+        }
+        if (!extract) continue;
+        EVSL_TRY(tri_eig(c, k, T, ldt, w, &V, &ldv));
+        std::vector<int> order(k);
+        for (int j = 0; j < k; j++) order[j] = j;
+        std::sort(order.begin(), order.end(), [&](int p, int q) { return w[p] > w[q]; });
+        int nconv = 0, nunconv = 0;
+        for (int jj : order) {
+            if (w[jj] < bar) break;
+            EVSL_TRY(gemm_nn(c, n, 1, k, W, n, V + (int64_t)jj * ldv, ldv, v.x, n));
+            EVSL_TRY(gen_step<2>(c, c->B, v.x, nullptr, nullptr, v.bx, nullptr, 0.0, 0.0, 0.0, 0.0));
+            EVSL_TRY(coldot(c, n, 1, v.x, n, v.bx, n, sc + S_NB2));
+            double nb2 = 0.0;
+            EVSL_TRY(d2h(c, &nb2, sc + S_NB2, sizeof(double)));
+            if (!(nb2 > 0.0)) return ctx_fail(c, EVSL_ERR_ARG, "chebLanNr_gen: (x, B x) = %g; B is not positive definite", nb2);
+            const double inv = 1.0 / std::sqrt(nb2);
+            EVSL_TRY(scale_vec(c, n, v.x, inv, nullptr));
+            EVSL_TRY(scale_vec(c, n, v.bx, inv, nullptr));
+            EVSL_TRY(gen_step<2>(c, c->A, v.x, nullptr, nullptr, v.ax, nullptr, 0.0, 0.0, 0.0, 0.0));
+            EVSL_TRY(coldot(c, n, 1, v.x, n, v.ax, n, sc + S_LAM));
+            EVSL_TRY(colres2(c, n, 1, v.ax, v.bx, n, sc + S_LAM, sc + S_RES2));
+            double lr[2];
+            EVSL_TRY(d2h(c, lr, sc + S_LAM, sizeof(lr)));
+            const double lamj = lr[0];
+            const bool inside = lamj >= a && (o->right_closed ? lamj <= b : lamj < b);
+            if (!inside) continue;
+            const double rj = std::sqrt(std::max(0.0, lr[1])) / scale;
+            if (rj > o->tol) {
+                nunconv++;
+                continue;
+            }
+            if (nconv >= cap) {
+                status = EVSL_ERR_CAPACITY;
+                break;
+            }
+            cudaError_t e = cudaMemcpyAsync(Xc + (int64_t)nconv * n, v.x, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                            c->stream);
+            if (e != cudaSuccess) return ctx_cuda(c, e, "chebLanNr_gen eigenvector copy");
+            lam_c[nconv] = lamj;
+            res_c[nconv] = rj;
+            nconv++;
+        }
+        found = nconv;
+        if (status == EVSL_ERR_CAPACITY) break;
+        if (nunconv == 0 || k == m || !(beta > 0.0)) {
+            if (nunconv > 0) status = EVSL_ERR_NOCONV;
+            break;
+        }
+        have_old = false;
+    }
+    std::vector<int> perm(found);
+    for (int i = 0; i < found; i++) perm[i] = i;
+    std::sort(perm.begin(), perm.end(), [&](int p, int q) { return lam_c[p] < lam_c[q]; });
+    for (int i = 0; i < found; i++) {
+        lam[i] = lam_c[perm[i]];
+        res[i] = res_c[perm[i]];
+        if (Y) {
+            cudaError_t e = cudaMemcpyAsync(Y + (int64_t)i * n, Xc + (int64_t)perm[i] * n, sizeof(double) * n,
+                                            cudaMemcpyDefault, c->stream);
+            if (e != cudaSuccess) return ctx_cuda(c, e, "chebLanNr_gen eigenvector readback");
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "chebLanNr_gen outputs");
+    *nev = found;
+    if (stats) {
+        *stats = evsl_stats();
+        stats->niter = its;
+        stats->nmv = nmv;
+        stats->t_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
+}

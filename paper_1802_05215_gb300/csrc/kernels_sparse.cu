@@ -402,13 +402,21 @@ inline unsigned blocks_for(int64_t threads, int tpb) { return (unsigned)((thread
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, const double *cv)
+// Builds the sliced-ELLPACK copy of a CSR matrix in M.  primary: M is the context's operator
+// A (its cached graphs and tile choices are dropped with it); otherwise M is a second matrix
+// (the mass matrix B of a generalized problem).  The old M survives a failed validation.
+static int sell_build(evsl_ctx *c, DevMatrix &M, bool primary, const char *what, int64_t n,
+                      const int64_t *rp, const int32_t *ci, const double *cv)
 {
-    if (n < 1 || !rp || !ci || !cv) return ctx_fail(c, EVSL_ERR_ARG, "set_csr: bad arguments");
-    if (rp[0] != 0) return ctx_fail(c, EVSL_ERR_ARG, "set_csr: row_ptr[0] != 0");
+    auto release = [&]() {
+        if (primary) sell_free(c);
+        else dev_matrix_free(c, M);
+    };
+    if (n < 1 || !rp || !ci || !cv) return ctx_fail(c, EVSL_ERR_ARG, "%s: bad arguments", what);
+    if (rp[0] != 0) return ctx_fail(c, EVSL_ERR_ARG, "%s: row_ptr[0] != 0", what);
     int64_t nnz = rp[n];
     if (nnz < 1 || nnz >= (int64_t(1) << 31))
-        return ctx_fail(c, EVSL_ERR_ARG, "set_csr: nnz %lld out of range", (long long)nnz);
+        return ctx_fail(c, EVSL_ERR_ARG, "%s: nnz %lld out of range", what, (long long)nnz);
     int64_t nslices = (n + 31) / 32;
     std::vector<int64_t> sptr(nslices + 1);
     sptr[0] = 0;
@@ -417,7 +425,7 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, co
         int w = 0;
         for (int64_t r = s * 32; r < std::min(n, s * 32 + 32); r++) {
             int64_t len = rp[r + 1] - rp[r];
-            if (len < 0) return ctx_fail(c, EVSL_ERR_ARG, "set_csr: row_ptr decreases at %lld", (long long)r);
+            if (len < 0) return ctx_fail(c, EVSL_ERR_ARG, "%s: row_ptr decreases at %lld", what, (long long)r);
             if (len > w) w = (int)len;
         }
         if (w > maxw) maxw = w;
@@ -425,7 +433,7 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, co
     }
     for (int64_t p = 0; p < nnz; p++)
         if (ci[p] < 0 || ci[p] >= n)
-            return ctx_fail(c, EVSL_ERR_ARG, "set_csr: column index %d out of range at %lld", ci[p], (long long)p);
+            return ctx_fail(c, EVSL_ERR_ARG, "%s: column index %d out of range at %lld", what, ci[p], (long long)p);
     std::vector<int32_t> rlen(n);
     bool has_diag = true;
     for (int64_t r = 0; r < n; r++) {
@@ -434,33 +442,34 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, co
         for (int64_t p = rp[r]; p < rp[r + 1] && !found; p++) found = (ci[p] == r);
         has_diag = has_diag && found;
     }
-    sell_free(c);
-    DevMatrix &A = c->A;
+    release();
+    DevMatrix &A = M;
     int64_t ns = sptr[nslices];
     int64_t *d_rp = nullptr;
     int32_t *d_ci = nullptr;
     double *d_cv = nullptr;
     int st = EVSL_OK;
+    // sizes first, so that a failed allocation releases what was taken with the right sizes
+    A.n = n;
+    A.nslices = nslices;
+    A.nstored = ns;
     if ((st = ctx_alloc(c, (void **)&A.sptr, sizeof(int64_t) * (nslices + 1))) ||
         (st = ctx_alloc(c, (void **)&A.col, sizeof(int32_t) * ns)) ||
         (st = ctx_alloc(c, (void **)&A.val, sizeof(double) * ns)) ||
         (st = ctx_alloc(c, (void **)&A.val32, sizeof(float) * ns)) ||
         (st = ctx_alloc(c, (void **)&A.rlen, sizeof(int32_t) * n))) {
-        sell_free(c);
+        release();
         return st;
     }
     A.has_diag = has_diag;
-    A.n = n;
     A.nnz = nnz;
-    A.nslices = nslices;
-    A.nstored = ns;
     A.maxw = maxw;
     if ((st = ctx_alloc(c, (void **)&d_rp, sizeof(int64_t) * (n + 1))) ||
         (st = ctx_alloc(c, (void **)&d_ci, sizeof(int32_t) * nnz)) ||
         (st = ctx_alloc(c, (void **)&d_cv, sizeof(double) * nnz))) {
         ctx_free(c, d_rp, sizeof(int64_t) * (n + 1));
         ctx_free(c, d_ci, sizeof(int32_t) * nnz);
-        sell_free(c);
+        release();
         return st;
     }
     cudaStream_t s = c->stream;
@@ -481,17 +490,31 @@ int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, co
     ctx_free(c, d_ci, sizeof(int32_t) * nnz);
     ctx_free(c, d_cv, sizeof(double) * nnz);
     if (e != cudaSuccess) {
-        sell_free(c);
-        return ctx_cuda(c, e, "set_csr upload");
+        release();
+        return ctx_cuda(c, e, what);
     }
     return EVSL_OK;
+}
+
+int sell_upload(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, const double *cv)
+{
+    return sell_build(c, c->A, true, "set_csr", n, rp, ci, cv);
+}
+
+int sell_upload_b(evsl_ctx *c, int64_t n, const int64_t *rp, const int32_t *ci, const double *cv)
+{
+    return sell_build(c, c->B, false, "set_csr_b", n, rp, ci, cv);
 }
 
 void sell_free(evsl_ctx *c)
 {
     filter_graphs_clear(c);
     c->tune.clear();
-    DevMatrix &A = c->A;
+    dev_matrix_free(c, c->A);
+}
+
+void dev_matrix_free(evsl_ctx *c, DevMatrix &A)
+{
     ctx_free(c, A.sptr, sizeof(int64_t) * (A.nslices + 1));
     ctx_free(c, A.col, sizeof(int32_t) * A.nstored);
     ctx_free(c, A.val, sizeof(double) * A.nstored);

@@ -103,6 +103,11 @@ def load(build_if_missing: bool = True):
         "evsl_batch_add": (i32, [P, P]),
         "evsl_batch_step": (i32, [P, P, P]),
         "evsl_batch_destroy": (None, [P]),
+        "evsl_lspol": (i32, [d, d, d, i32, P, P, i32, P]),
+        "evsl_set_csr_b": (i32, [P, i64, P, P, P, d, d, d, i32, P, P]),
+        "evsl_polyB_apply": (i32, [P, P, P]),
+        "evsl_bounds_gen": (i32, [P, i32, u64, P, P]),
+        "evsl_chebLanNr_gen": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_launch_count": (i64, [P]),
         "evsl_profile": (i32, [P, i32]),
         "evsl_profile_get": (i32, [P, i32, P, P]),
@@ -143,6 +148,18 @@ class Filter:
     boundary = property(lambda s: s.pol.boundary)
     lmin = property(lambda s: s.pol.lmin)
     lmax = property(lambda s: s.pol.lmax)
+
+
+def lspol(bmin, bmax, eps=1e-13, maxdeg=200):
+    """Chebyshev coefficients of p(t) ~ 1/t on [bmin, bmax] (the polynomial B^{-1}):
+    dict(status, deg, coef, err)."""
+    lib = load()
+    coef = np.zeros(maxdeg + 1)
+    deg, err = C.c_int(), C.c_double()
+    st = lib.evsl_lspol(bmin, bmax, eps, maxdeg, C.byref(deg), _addr(coef), len(coef), C.byref(err))
+    if st not in (EVSL_OK, -4):
+        raise EvslError(st, "lspol")
+    return dict(status=st, deg=deg.value, coef=coef[:deg.value + 1].copy(), err=err.value)
 
 
 def cheb_filter_build(a, b, lmin, lmax, tau=0.8, tau_ext=0.4, damping=DAMP_JACKSON,
@@ -233,6 +250,44 @@ class Context:
         self._check(self.lib.evsl_set_csr(self.h, A.n, _addr(A.row_ptr), _addr(A.col_idx),
                                           _addr(A.val)), "set_csr")
         self.n = A.n
+
+    def set_csr_b(self, B, bmin, bmax, eps=1e-13, maxdeg=200):
+        """Mass matrix of a generalized problem with its spectrum in [bmin, bmax]; builds the
+        polynomial inverse.  Returns (degree, relative error) of p(t) ~ 1/t."""
+        deg, err = C.c_int(), C.c_double()
+        self._check(self.lib.evsl_set_csr_b(self.h, B.n, _addr(B.row_ptr), _addr(B.col_idx), _addr(B.val),
+                                            bmin, bmax, eps, maxdeg, C.byref(deg), C.byref(err)), "set_csr_b")
+        return deg.value, err.value
+
+    def polyB_apply(self, x, y):
+        """y = p(B) x for device vectors of n doubles (synchronous)."""
+        self._check(self.lib.evsl_polyB_apply(self.h, _addr(x), _addr(y)), "polyB_apply")
+
+    def bounds_gen(self, steps=80, seed=0):
+        """Spectral bounds of the pencil (A, B) by B-Lanczos on B^{-1} A."""
+        lo, hi = C.c_double(), C.c_double()
+        self._check(self.lib.evsl_bounds_gen(self.h, steps, seed, C.byref(lo), C.byref(hi)), "bounds_gen")
+        return lo.value, hi.value
+
+    def chebLanNr_gen(self, a, b, filt: Filter, m=200, ncycle=10, tol=1e-8, tau1=1e-10, seed=0,
+                      right_closed=True, cap=None, Y=None, allow_partial=False):
+        """Filtered non-restart Lanczos for A x = lambda B x on [a, b]; same outputs as chebLanNr
+        (the eigenvectors are B-orthonormal)."""
+        cap = cap or m
+        opts = LanOpts(m, 0, ncycle, tol, tau1, seed, FP64, int(right_closed))
+        lam = np.zeros(cap)
+        res = np.zeros(cap)
+        if Y is None:
+            Y = np.zeros((cap, self.n))
+        nev = C.c_int()
+        stats = Stats()
+        st = self.lib.evsl_chebLanNr_gen(self.h, a, b, C.byref(filt.pol), C.byref(opts), cap,
+                                         C.byref(nev), _addr(lam), _addr(Y), _addr(res), C.byref(stats))
+        if st != EVSL_OK and not (allow_partial and st in (-4, -5)):
+            self._check(st, "chebLanNr_gen")
+        k = nev.value
+        return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
+                    stats=stats.as_dict())
 
     def bounds(self, steps=80, seed=0):
         lo, hi = C.c_double(), C.c_double()

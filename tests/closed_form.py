@@ -26,3 +26,13 @@ def count_in(e, a, b, right_closed=True):
 
 def nnz_formula(dim, nx):
     return nx ** 2 + 4 * nx * (nx - 1) if dim == 2 else nx ** 3 + 6 * nx ** 2 * (nx - 1)
+
+
+def pencil_eigs(nx):
+    """Eigenvalues of the pencil (laplacian_2d(nx), mass_matrix_2d(nx)): A = T (x) I + I (x) T and
+    B = M (x) M with M = tridiag(1, 4, 1) / 6 share the sine eigenvectors, so
+    lambda_ij = (t_i + t_j) / (m_i m_j) with t_i = 2 - 2 cos(i pi/(nx+1)), m_i = (4 + 2 cos(i pi/(nx+1))) / 6."""
+    k = np.arange(1, nx + 1)
+    t = 2.0 - 2.0 * np.cos(k * np.pi / (nx + 1))
+    m = (4.0 + 2.0 * np.cos(k * np.pi / (nx + 1))) / 6.0
+    return np.sort(((t[:, None] + t[None, :]) / (m[:, None] * m[None, :])).ravel())

@@ -118,6 +118,10 @@ def test_entry_points_reject_null_context_and_bad_arguments(native):
     assert lib.evsl_landos(nul, 10, 2, 0, buf, buf, ibuf) == -1
     assert lib.evsl_kpm_dos_doubling(nul, 10, 2, 0, 0.0, 1.0, 0, buf) == -1
     assert lib.evsl_filter_apply_multi(nul, 1, nul, nul, nul, 0) == -1
+    assert lib.evsl_set_csr_b(nul, 4, nul, nul, nul, 0.5, 1.0, 1e-13, 50, nul, nul) == -1
+    assert lib.evsl_polyB_apply(nul, nul, nul) == -1
+    assert lib.evsl_bounds_gen(nul, 10, 0, buf, buf) == -1
+    assert lib.evsl_chebLanNr_gen(nul, 0.0, 1.0, nul, nul, 1, ctypes.byref(i32()), buf, nul, buf, nul) == -1
     nodes = np.array([[0.1, 0.5, 0.9]])
     weights = np.array([[0.2, 0.3, 0.5]])
     d = dict(nodes=nodes, weights=weights, mused=np.array([3], dtype=np.int32))
@@ -128,3 +132,19 @@ def test_entry_points_reject_null_context_and_bad_arguments(native):
     bad = dict(d, mused=np.array([4], dtype=np.int32))        # more steps than stored
     with pytest.raises(native.EvslError):
         native.slice_by_landos(bad, 100, 0.0, 1.0, 2)
+
+def test_lspol_matches_oracle(native, oracle_mod):
+    # the library's host lsPol (polynomial B^{-1}) and the oracle's: same degree, same
+    # coefficients; the reported error is within eps; too small a maxdeg is reported
+    for bmin, bmax, eps in [(0.11, 0.99, 1e-13), (1.0 / 9.0, 1.0, 1e-10), (0.5, 4.0, 1e-13), (2.0, 3.0, 1e-6)]:
+        lp = native.lspol(bmin, bmax, eps)
+        lo = oracle_mod.lspol(bmin, bmax, eps)
+        assert lp["status"] == 0 and lo["status"] == 0
+        assert lp["deg"] == lo["deg"]
+        assert np.max(np.abs(lp["coef"] - lo["coef"])) <= 1e-14 * np.abs(lo["coef"]).max()
+        assert lp["err"] <= eps
+    lp = native.lspol(0.01, 1.0, 1e-13, maxdeg=5)
+    assert lp["status"] == -4 and lp["deg"] == 5 and lp["err"] > 1e-13
+    for bad in [(0.0, 1.0, 1e-13), (1.0, 0.5, 1e-13), (0.5, 1.0, 0.0)]:
+        with pytest.raises(native.EvslError):
+            native.lspol(*bad)

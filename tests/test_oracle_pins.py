@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 from numpy.polynomial import chebyshev as npcheb
 
-from closed_form import count_in, lap_eigs, nnz_formula
+from closed_form import count_in, lap_eigs, nnz_formula, pencil_eigs
 from conftest import golden
 from paper_1802_05215_gb300 import inputs as I
 
@@ -490,12 +490,7 @@ def test_slicer_landos_balances_within_one_node(oracle_mod):
 
 # ---------------------------------------------------------------- generalized problems (Sec. 2.4)
 def _pencil_eigs(nx):
-    # A = T (x) I + I (x) T, B = M (x) M with M = tridiag(1, 4, 1) / 6: shared sine eigenvectors,
-    # lambda_ij = (t_i + t_j) / (m_i m_j)
-    k = np.arange(1, nx + 1)
-    t = 2.0 - 2.0 * np.cos(k * np.pi / (nx + 1))
-    m = (4.0 + 2.0 * np.cos(k * np.pi / (nx + 1))) / 6.0
-    return np.sort(((t[:, None] + t[None, :]) / (m[:, None] * m[None, :])).ravel())
+    return pencil_eigs(nx)
 
 
 def test_pencil_generator_closed_form():
