@@ -666,6 +666,114 @@ def run_si_49(args):
     return line
 
 
+def gen_step_bytes(n: int, nnz: int, mode: int, separate_u: bool) -> float:
+    # algorithmic bytes of one k_gen_step launch: matrix values + column indices, row pointers,
+    # the SpMV operand u (when it is not x), x, and per mode: out written (and y written, mode
+    # 0), or xprev read, out written, y read and written (mode 1)
+    vec = (1 if separate_u else 0) + 1 + (2 if mode == 0 else 4)
+    return nnz * 12 + 8 * (n + 1) + 8 * vec * n
+
+
+def run_gen_2d(args):
+    """Generalized problem A x = lambda B x with B^{-1} by the lsPol polynomial, on the pencil
+    (2-D 5-point Laplacian, 2-D linear-element mass matrix M (x) M).  Two legs:
+    (1) the solve y = p(B) x on the 1000^2 mass matrix (n = 1e6, 9e6 nonzeros; matrix and
+        vectors above L2 size): per-launch time of k_gen_step from CUDA events, its roofline;
+    (2) filtered non-restart Lanczos (ChebLanNr with B-inner products) on the 200^2 pencil over
+        a slice cut between distinct closed-form eigenvalues: eigenpairs/s with the filter's
+        CUDA graph and with direct launches (bitwise-equal results), counts checked against the
+        closed form.  B's bounds come from the library's Lanczos bounds on B."""
+    import torch
+
+    from paper_1802_05215_gb300 import native
+    hbm, src = peaks()
+    out = {}
+    with native.Context(0) as ctx:
+        # (1) the solve with B
+        B = inputs.mass_matrix_2d(1000)
+        ctx.set_csr(B)
+        blo, bhi = ctx.bounds(BOUNDS_STEPS, SEED)
+        ctx.set_csr(inputs.laplacian_2d(1000))
+        q, err = ctx.set_csr_b(B, blo, bhi, 1e-13)
+        x = torch.randn(B.n, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            ctx.polyB_apply(x, y)
+        reps = 30
+        ctx.profile(True)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ctx.polyB_apply(x, y)
+        wall = time.perf_counter() - t0
+        nl, ms = ctx.profile_get(native.K_GEN_STEP)
+        ctx.profile(False)
+        alg = reps * (gen_step_bytes(B.n, B.nnz, 0, False) + (q - 1) * gen_step_bytes(B.n, B.nnz, 1, False))
+        per_launch_us = ms / nl * 1e3
+        achieved = alg / (ms * 1e-3) / 1e9
+        out["solve_B"] = {"n": B.n, "nnz": B.nnz, "lspol_deg": q, "lspol_err": err, "applies": reps,
+                          "launches": nl, "us_per_launch": per_launch_us, "wall_s": wall,
+                          "alg_bytes_per_apply": alg / reps}
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "kernel": "k_gen_step (solve with p(B), 1000^2 mass matrix)", "peak_source": src}
+        # (2) ChebLanNr for the pencil
+        nx = 200
+        A, B = inputs.laplacian_2d(nx), inputs.mass_matrix_2d(nx)
+        k = np.arange(1, nx + 1)
+        t = 2.0 - 2.0 * np.cos(k * np.pi / (nx + 1))
+        mm = (4.0 + 2.0 * np.cos(k * np.pi / (nx + 1))) / 6.0
+        lam = np.sort(((t[:, None] + t[None, :]) / (mm[:, None] * mm[None, :])).ravel())
+        dist = np.unique(lam)
+
+        def cut(v):
+            i = int(np.searchsorted(dist, v))
+            return 0.5 * (dist[i - 1] + dist[i])
+
+        a, b = cut(68.0), cut(68.5)
+        exact = int(np.count_nonzero((lam >= a) & (lam <= b)))
+        ctx.set_csr(B)
+        blo, bhi = ctx.bounds(BOUNDS_STEPS, SEED)
+        ctx.set_csr(A)
+        q2, _ = ctx.set_csr_b(B, blo, bhi, 1e-13)
+        lo, hi = ctx.bounds_gen(BOUNDS_STEPS, SEED)
+        f = native.cheb_filter_build(a, b, lo, hi)
+        m = max(6 * exact, 200)
+        cap = exact + 16
+        Y = torch.empty(cap * A.n, dtype=torch.float64, device="cuda")
+        fw = native.cheb_filter_build(60.0, 61.0, lo, hi)
+        ctx.chebLanNr_gen(60.0, 61.0, fw, m=20, cap=cap, Y=Y, allow_partial=True)   # warm-up
+        runs = {}
+        for graphs in (True, False):
+            ctx.set_graphs(graphs)
+            ctx.profile(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = ctx.chebLanNr_gen(a, b, f, m=m, cap=cap, Y=Y, tol=TOL, seed=SEED)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            nl2, ms2 = ctx.profile_get(native.K_GEN_STEP)
+            ctx.profile(False)
+            st = r["stats"]
+            runs["graphs" if graphs else "direct"] = {
+                "eigenpairs": r["nev"], "seconds": dt, "eigenpairs_per_s": r["nev"] / dt,
+                "niter": st["niter"], "nmv": st["nmv"], "gen_step_launches": nl2,
+                "gen_step_ms": ms2, "max_res": float(r["res"].max()) if r["nev"] else 0.0,
+                "lam": r["lam"]}
+        ctx.set_graphs(True)
+    same = bool(np.array_equal(runs["graphs"]["lam"], runs["direct"]["lam"]))
+    for v in runs.values():
+        v.pop("lam")
+    line = {"metric": "eigenpairs/s at resid<=1e-8, generalized pencil A x = lambda B x (polynomial B^{-1})",
+            "value": runs["graphs"]["eigenpairs_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic (closed-form pencil: 2-D Laplacian, 2-D linear-element mass matrix)",
+            "config": {"workload": f"2-D pencil {nx}^2 on [{a:.6f}, {b:.6f}], ChebLanNr with B-inner products; "
+                                   "solve leg on the 1000^2 mass matrix"},
+            "exact_count": exact, "deg": f.deg, "lspol_deg": q2, "bounds": [lo, hi], "b_bounds": [blo, bhi],
+            "runs": runs, "graph_equals_direct": same, "roofline": roof, **out}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def run_kpm_200(args):
     """KPM density of the Anderson 200^3 model (W = 2, n = 8e6, nnz = 5.576e7): degree 300 with
     64 Rademacher probes in one block, FP64 and FP32; the FP64 moments of the first probe are
@@ -737,7 +845,7 @@ def run_kpm_200(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["lap3d_100", "serving", "anderson3d_80", "kpm_200", "table2_nr", "table4_nr", "si_49"],
+    ap.add_argument("--workload", choices=["lap3d_100", "serving", "anderson3d_80", "kpm_200", "table2_nr", "table4_nr", "si_49", "gen_2d"],
                     default="lap3d_100")
     ap.add_argument("--slices", type=int, default=4,
                     help="anderson3d_80: how many of the 16 slices to solve (<= 0: all)")
@@ -761,6 +869,8 @@ def main():
         run_table4_nr(args)
     elif args.workload == "si_49":
         run_si_49(args)
+    elif args.workload == "gen_2d":
+        run_gen_2d(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -375,10 +375,15 @@ typedef enum {
     EVSL_K_REORTH = 2,      /* Gram-Schmidt projections against the basis               */
     EVSL_K_RITZ_GEMM = 3,   /* Ritz vectors Y = Q S                                     */
     EVSL_K_SMALL_EIG = 4,   /* Jacobi / bisection on the projected matrix               */
-    EVSL_K_COUNT = 5
+    EVSL_K_GEN_STEP = 5,    /* generalized filter degree steps (solve with B, product with A) */
+    EVSL_K_COUNT = 6
 } evsl_kernel_family;
 
 int64_t evsl_launch_count(const evsl_ctx *ctx);
+/* evsl_set_graphs: 1 (the default) lets single-vector filter applications replay cached CUDA
+ * graphs; 0 drops the cached graphs and makes every application launch its kernels directly.
+ * Both give bitwise the same results. */
+int evsl_set_graphs(evsl_ctx *ctx, int enable);
 int evsl_profile(evsl_ctx *ctx, int enable);
 int evsl_profile_get(evsl_ctx *ctx, int kernel, int64_t *launches, double *ms);
 

@@ -413,8 +413,6 @@ int evsl_profile_get(evsl_ctx *c, int kernel, int64_t *launches, double *ms)
     return EVSL_OK;
 }
 
-}  // extern "C"
-
 // ---- generalized problems A x = lambda B x
 int evsl_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, int cap, double *err)
 {
@@ -435,6 +433,7 @@ int evsl_set_csr_b(evsl_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t
         return ctx_fail(c, EVSL_ERR_ARG, "set_csr_b: need 0 < bmin < bmax, eps > 0 and maxdeg >= 1");
     std::vector<double> coef((size_t)maxdeg + 1);
     int d = 0;
+    filter_graphs_clear(c);  // cached generalized-filter graphs hold B's device addresses
     double e = 0.0;
     const int pst = host_lspol(bmin, bmax, eps, maxdeg, &d, coef.data(), &e);
     cudaSetDevice(c->device);
@@ -479,3 +478,16 @@ int evsl_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
     cudaSetDevice(c->device);
     return drv_chebLanNr_gen(c, a, b, pol, opts, cap, nev, lam, Y, res, stats);
 }
+
+int evsl_set_graphs(evsl_ctx *c, int enable)
+{
+    if (!c) return EVSL_ERR_ARG;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "set_graphs");
+    if (!enable) filter_graphs_clear(c);
+    c->graphs_off = !enable;
+    return EVSL_OK;
+}
+
+}  // extern "C"

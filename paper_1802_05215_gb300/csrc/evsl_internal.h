@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <map>
 #include <vector>
@@ -85,6 +86,13 @@ int tune_lookup(evsl_ctx *c, int nvec, int bytes);
 
 // drop the cached filter graphs (they hold device addresses of the matrix and workspaces)
 void filter_graphs_clear(evsl_ctx *c);
+// Replays the cached graph `key` (capturing the kernel launches of issue() on the context's
+// stream the first time), timed as one group of `launches` launches of `family`.  Returns 1
+// when graphs cannot be used (the stream is being captured by the caller, or capture failed):
+// the caller then launches directly.
+int graph_replay(evsl_ctx *c, uint64_t key, int family, int launches, const std::function<int()> &issue);
+// FNV-1a step for graph keys
+uint64_t graph_key_hash(uint64_t h, const void *p, size_t len);
 
 enum WsSlot {
     WS_PARTIAL = 0, WS_SCAL, WS_W0, WS_W1, WS_W2, WS_KPM_PART, WS_F32_X, WS_F32_Y,

@@ -81,10 +81,11 @@ int d2h(evsl_ctx *c, void *dst, const void *src, size_t bytes)
 // device scalars: alpha, a scratch norm, beta^2, (x, Bx), lambda, then the projections h
 enum { S_ALPHA = 0, S_TMP = 1, S_BETA2 = 2, S_NB2 = 3, S_LAM = 4, S_RES2 = 5, S_H = 8 };
 
-// n-vectors of the generalized drivers (one workspace, carved)
+// n-vectors of the generalized drivers (one workspace, carved); zs: fixed input of the
+// filter graphs
 struct Vecs {
-    double *u, *t1, *t2, *f1, *f2, *z, *wt, *x, *ax, *bx;
-    static constexpr int COUNT = 10;
+    double *u, *t1, *t2, *f1, *f2, *z, *wt, *x, *ax, *bx, *zs;
+    static constexpr int COUNT = 11;
 };
 
 int get_vecs(evsl_ctx *c, Vecs &v)
@@ -93,7 +94,7 @@ int get_vecs(evsl_ctx *c, Vecs &v)
     int st = EVSL_OK;
     double *p = (double *)ctx_ws(c, WS_GEN_VEC, sizeof(double) * (size_t)n * Vecs::COUNT, &st);
     if (st) return st;
-    double **slots[Vecs::COUNT] = {&v.u, &v.t1, &v.t2, &v.f1, &v.f2, &v.z, &v.wt, &v.x, &v.ax, &v.bx};
+    double **slots[Vecs::COUNT] = {&v.u, &v.t1, &v.t2, &v.f1, &v.f2, &v.z, &v.wt, &v.x, &v.ax, &v.bx, &v.zs};
     for (int i = 0; i < Vecs::COUNT; i++) *slots[i] = p + (int64_t)i * n;
     return EVSL_OK;
 }
@@ -142,6 +143,52 @@ int filter_gen(evsl_ctx *c, const evsl_polfilt *pol, const double *zi, double *z
         prev_tmp = true;
     }
     *nmv += deg;
+    return EVSL_OK;
+}
+
+// k_gen_step launches of one filter application: deg solves of deg(p) steps each, deg steps with A
+int filter_gen_launches(const evsl_ctx *c, const evsl_polfilt *pol)
+{
+    return pol->deg * ((int)c->b_coef.size() - 1 + 1);
+}
+
+// z (= v.z) = rho(Mhat) zi.  Filters of degree >= 2 copy zi into v.zs and replay a cached CUDA
+// graph of the launches (keyed by the filter, the polynomial inverse, both matrices and the
+// buffers), which removes the host launch cost of the deg (deg(p) + 1) small launches; the
+// kernels and their arguments are those of the direct path, so the results are bitwise equal.
+int filter_gen_run(evsl_ctx *c, const evsl_polfilt *pol, const double *zi, const Vecs &v, int64_t *nmv)
+{
+    const int nl = filter_gen_launches(c, pol);
+    if (pol->deg >= 2 && !c->graphs_off) {
+        uint64_t h = 1469598103934665603ull;
+        const char tag[] = "generalized filter";
+        h = graph_key_hash(h, tag, sizeof tag);
+        h = graph_key_hash(h, &pol->deg, sizeof pol->deg);
+        h = graph_key_hash(h, &pol->lmin, sizeof pol->lmin);
+        h = graph_key_hash(h, &pol->lmax, sizeof pol->lmax);
+        h = graph_key_hash(h, pol->coef, sizeof(double) * (pol->deg + 1));
+        h = graph_key_hash(h, c->b_coef.data(), sizeof(double) * c->b_coef.size());
+        h = graph_key_hash(h, &c->b_min, sizeof c->b_min);
+        h = graph_key_hash(h, &c->b_max, sizeof c->b_max);
+        const void *ptrs[] = {c->A.sptr, c->A.col, c->A.val, c->B.sptr, c->B.col, c->B.val,
+                              v.zs, v.z, v.u, v.t1, v.t2, v.f1, v.f2};
+        h = graph_key_hash(h, ptrs, sizeof ptrs);
+        h = graph_key_hash(h, &c->A.n, sizeof c->A.n);
+        cudaError_t e = cudaMemcpyAsync(v.zs, zi, sizeof(double) * c->A.n, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "generalized filter input copy");
+        const int r = graph_replay(c, h, EVSL_K_GEN_STEP, nl, [&]() {
+            int64_t unused = 0;
+            return filter_gen(c, pol, v.zs, v.z, v, &unused);
+        });
+        if (r != 1) {
+            if (r == EVSL_OK) *nmv += pol->deg;
+            return r;
+        }
+    }
+    ProfGroup g;
+    prof_begin(c, EVSL_K_GEN_STEP, &g);
+    EVSL_TRY(filter_gen(c, pol, zi, v.z, v, nmv));
+    prof_end(c, &g, nl);
     return EVSL_OK;
 }
 
@@ -283,7 +330,10 @@ int drv_polyB_apply(evsl_ctx *c, const double *x, double *y)
     int st = EVSL_OK;
     double *t = (double *)ctx_ws(c, WS_GEN_VEC, sizeof(double) * (size_t)n * Vecs::COUNT, &st);
     if (st) return st;
+    ProfGroup g;
+    prof_begin(c, EVSL_K_GEN_STEP, &g);
     EVSL_TRY(solve_b(c, x, y, t, t + n));
+    prof_end(c, &g, (int)c->b_coef.size() - 1);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, "polyB_apply");
 }
@@ -363,7 +413,7 @@ int drv_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, 
     double t_old = 0.0, beta = 0.0;
     for (int i = 0; i < m; i++) {
         its++;
-        EVSL_TRY(filter_gen(c, pol, Z + (int64_t)i * n, v.z, v, &nmv));
+        EVSL_TRY(filter_gen_run(c, pol, Z + (int64_t)i * n, v, &nmv));
         double alpha = 0.0, bn = 0.0;
         EVSL_TRY(lanab_step(c, i, W, Z, v.z, beta, v, sc, &alpha, &bn));
         T[(size_t)i * ldt + i] = alpha;

@@ -82,7 +82,7 @@ int issue_filter_staged(evsl_ctx *c, const evsl_polfilt *pol, double *Y, evsl_pr
 // on the context's stream) the first time.  The launches are timed as one filter group of
 // `degree` steps.  Returns 1 if graphs cannot be used here (the caller then launches directly).
 template <typename F>
-int launch_graph(evsl_ctx *c, uint64_t h, int degree, F issue)
+int launch_graph(evsl_ctx *c, uint64_t h, int degree, F issue, int family = EVSL_K_CHEB_STEP)
 {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -130,7 +130,7 @@ int launch_graph(evsl_ctx *c, uint64_t h, int degree, F issue)
         c->fgraphs.push_back({h, exec, nl});
     }
     ProfGroup g;
-    prof_begin(c, EVSL_K_CHEB_STEP, &g);
+    prof_begin(c, family, &g);
     cudaError_t e = cudaGraphLaunch(exec, c->stream);
     if (e != cudaSuccess) return ctx_cuda(c, e, "filter graph launch");
     c->launches += nl;
@@ -206,6 +206,13 @@ int issue_filter_multi(evsl_ctx *c, int npol, const std::vector<int> &active, in
 }
 
 }  // namespace
+
+int graph_replay(evsl_ctx *c, uint64_t key, int family, int launches, const std::function<int()> &issue)
+{
+    return launch_graph(c, key, launches, [&]() { return issue(); }, family);
+}
+
+uint64_t graph_key_hash(uint64_t h, const void *p, size_t len) { return fnv1a(h, p, len); }
 
 void filter_graphs_clear(evsl_ctx *c)
 {

@@ -164,26 +164,22 @@ def laplacian_3d(nx: int, ny: int | None = None, nz: int | None = None) -> CSR:
 def mass_matrix_2d(nx: int) -> CSR:
     """Linear finite-element mass matrix on an nx x nx grid, M (x) M with the 1-D mass matrix
     M = tridiag(1, 4, 1) / 6 (SPD, condition number below 3): the B of a generalized pencil
-    (A, B) with A = laplacian_2d(nx).  Rows ordered like laplacian_2d (x fastest)."""
+    (A, B) with A = laplacian_2d(nx).  Rows ordered like laplacian_2d (x fastest), columns
+    sorted; entry ((y, x), (y', x')) = M[x, x'] M[y, y']."""
+    k = np.arange(nx, dtype=np.int64)
+    # 1-D entries (i, j, M[i, j])
+    i1 = np.concatenate([k, k[1:], k[:-1]])
+    j1 = np.concatenate([k, k[:-1], k[1:]])
+    v1 = np.concatenate([np.full(nx, 4.0 / 6.0), np.full(2 * (nx - 1), 1.0 / 6.0)])
+    # 2-D entries: y-part along the first axis, x-part along the second
+    rows = (i1[:, None] * nx + i1[None, :]).ravel()
+    cols = (j1[:, None] * nx + j1[None, :]).ravel()
+    vals = (v1[None, :] * v1[:, None]).ravel()
+    order = np.lexsort((cols, rows))
     n = nx * nx
-    rows, cols, vals = [], [], []
-    m1 = {-1: 1.0 / 6.0, 0: 4.0 / 6.0, 1: 1.0 / 6.0}
-    for y in range(nx):
-        for x in range(nx):
-            r = y * nx + x
-            for dy in (-1, 0, 1):
-                for dx in (-1, 0, 1):
-                    xx, yy = x + dx, y + dy
-                    if 0 <= xx < nx and 0 <= yy < nx:
-                        rows.append(r)
-                        cols.append(yy * nx + xx)
-                        vals.append(m1[dx] * m1[dy])
-    rows = np.asarray(rows)
-    order = np.lexsort((np.asarray(cols), rows))
     row_ptr = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(row_ptr, rows + 1, 1)
-    return CSR(n, np.cumsum(row_ptr), np.asarray(cols)[order], np.asarray(vals)[order],
-               name=f"mass2d_{nx}")
+    row_ptr[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    return CSR(n, row_ptr, cols[order].astype(np.int32), vals[order], name=f"mass2d_{nx}")
 
 
 def anderson_diagonal(n: int, W: float, seed: int) -> np.ndarray:

@@ -18,7 +18,7 @@ ERRORS = {-1: "EVSL_ERR_ARG", -2: "EVSL_ERR_NOMEM", -3: "EVSL_ERR_CUDA", -4: "EV
           -5: "EVSL_ERR_CAPACITY", -6: "EVSL_ERR_TIMEOUT", -7: "EVSL_ERR_STATE"}
 DAMP_NONE, DAMP_JACKSON, DAMP_SIGMA = 0, 1, 2
 FP64, FP32 = 0, 1
-K_CHEB_STEP, K_KPM_STEP, K_REORTH, K_RITZ_GEMM, K_SMALL_EIG = range(5)
+K_CHEB_STEP, K_KPM_STEP, K_REORTH, K_RITZ_GEMM, K_SMALL_EIG, K_GEN_STEP = range(6)
 NOALLOC_MAX_ELEMS = 1 << 21
 
 
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
         "evsl_bounds_gen": (i32, [P, i32, u64, P, P]),
         "evsl_chebLanNr_gen": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_launch_count": (i64, [P]),
+        "evsl_set_graphs": (i32, [P, i32]),
         "evsl_profile": (i32, [P, i32]),
         "evsl_profile_get": (i32, [P, i32, P, P]),
     }
@@ -419,6 +420,10 @@ class Context:
             out.append(dict(status=jobs[j].status, nev=k, lam=lam[:k].copy(), res=res[:k].copy(),
                             Y=Y, stats=st.as_dict()))
         return out
+
+    def set_graphs(self, enable: bool):
+        """Allow (default) or forbid CUDA-graph replay of single-vector filter applications."""
+        self._check(self.lib.evsl_set_graphs(self.h, int(enable)), "set_graphs")
 
     def launch_count(self) -> int:
         return int(self.lib.evsl_launch_count(self.h))

@@ -117,3 +117,25 @@ def test_generalized_state_errors(nat, oracle_mod):
         assert lo < pencil_eigs(12)[0] + 1e-9 and hi > 0.9 * pencil_eigs(12)[-1]
     finally:
         c.close()
+
+
+def test_cheblannr_gen_graph_replay_bitwise_equals_direct(ctx, nat, oracle_mod):
+    # the filter's CUDA graph (captured once, replayed every step) and direct launches run the
+    # same kernels with the same arguments: identical eigenpairs; the profiler sees
+    # deg (deg(p) + 1) generalized steps per Lanczos step either way
+    A, B, lp = _pencil(ctx, oracle_mod, 20)
+    lo, hi = oracle_mod.bounds_gen(A, B, lp, 80, 0)
+    f = nat.cheb_filter_build(10.0, 11.0, lo, hi)
+    out = []
+    for graphs in (True, False):
+        ctx.set_graphs(graphs)
+        ctx.profile(True)
+        r = ctx.chebLanNr_gen(10.0, 11.0, f, m=200)
+        nl, ms = ctx.profile_get(nat.K_GEN_STEP)
+        ctx.profile(False)
+        assert nl == f.deg * (lp["deg"] + 1) * r["stats"]["niter"] and ms > 0
+        out.append(r)
+    ctx.set_graphs(True)
+    assert out[0]["nev"] == out[1]["nev"] > 0
+    assert np.array_equal(out[0]["lam"], out[1]["lam"]) and np.array_equal(out[0]["res"], out[1]["res"])
+    assert np.array_equal(out[0]["Y"][:out[0]["nev"]], out[1]["Y"][:out[1]["nev"]])
