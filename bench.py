@@ -72,27 +72,28 @@ def cheb_step_bytes(n: int, nnz: int, nvec: int = 1, b: int = 8) -> float:
     return nnz * (b + 4) + 8 * (n + 1) + 5 * nvec * n * b
 
 
-def kernel_source_hash() -> str:
-    """Fingerprint of the fused filter-step kernel source (the marked region of
-    kernels_sparse.cu), so that a profile summary is used only for the kernel it measured."""
-    with open(os.path.join(ROOT, "paper_1802_05215_gb300", "csrc", "kernels_sparse.cu")) as f:
+def kernel_source_hash(src: str = "kernels_sparse.cu", region: str = "cheb_step1") -> str:
+    """Fingerprint of a marked kernel source region (// [region begin] ... // [region end] in
+    csrc/src), so that a profile summary is used only for the kernel it measured."""
+    with open(os.path.join(ROOT, "paper_1802_05215_gb300", "csrc", src)) as f:
         text = f.read()
-    m = re.search(r"// \[cheb_step1 begin\](.*)// \[cheb_step1 end\]", text, re.S)
-    region = m.group(1) if m else text
-    return hashlib.sha1(region.encode()).hexdigest()[:12]
+    m = re.search(r"// \[" + region + r" begin\](.*)// \[" + region + r" end\]", text, re.S)
+    region_text = m.group(1) if m else text
+    return hashlib.sha1(region_text.encode()).hexdigest()[:12]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the filter step from the committed ncu summary, if it was
-    taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "cheb_step_lap3d_100.md")
+def profiled_traffic(profile: str = "cheb_step_lap3d_100.md", src: str = "kernels_sparse.cu",
+                     region: str = "cheb_step1"):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, if that was taken on
+    the current kernel source."""
+    path = os.path.join(ROOT, "profiles", profile)
     try:
         text = open(path).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    if not m or not t or m.group(1) != kernel_source_hash(src, region):
         return None
     return float(t.group(1))
 
@@ -714,7 +715,8 @@ def run_gen_2d(args):
                           "launches": nl, "us_per_launch": per_launch_us, "wall_s": wall,
                           "alg_bytes_per_apply": alg / reps}
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm,
+                "traffic": profiled_traffic("gen_step_mass2d_1000.md", "generalized.cu", "gen_step"),
                 "kernel": "k_gen_step (solve with p(B), 1000^2 mass matrix)", "peak_source": src}
         # (2) ChebLanNr for the pencil
         nx = 200

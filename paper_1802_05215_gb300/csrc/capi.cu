@@ -442,6 +442,7 @@ int evsl_set_csr_b(evsl_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t
     c->b_coef = coef;
     c->b_min = bmin;
     c->b_max = bmax;
+    EVSL_TRY(gen_map_b(c));
     if (deg) *deg = d;
     if (err) *err = e;
     if (pst != EVSL_OK) return ctx_fail(c, pst, "set_csr_b: degree %d reached with error %g > eps %g", d, e, eps);

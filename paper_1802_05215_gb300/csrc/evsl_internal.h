@@ -246,6 +246,7 @@ int drv_filter_apply_multi(evsl_ctx *c, int npol, const evsl_polfilt *pols, cons
                            double *Y, evsl_precision prec);
 // generalized problems (generalized.cu)
 int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, double *err);
+int gen_map_b(evsl_ctx *c);
 int drv_polyB_apply(evsl_ctx *c, const double *x, double *y);
 int drv_bounds_gen(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax);
 int drv_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *o,

@@ -24,13 +24,16 @@ namespace {
 constexpr int GTPB = 256;
 constexpr double PI = 3.14159265358979323846;
 
+// [gen_step begin] -- source region fingerprinted by the profile summaries
 // Sparse step with M in sliced ELLPACK:
 //   MODE 0: out = sc (M u - cc x);          y = c0 x + cj out
 //   MODE 1: out = sc (M u - cc x) - xprev;  y += cj out
 //   MODE 2: out = M u
+// HAT: val holds the mapped (2/h)(M - c I) and u = x, so acc is already 2 Mhat x and the
+// epilogue is out = acc / 2 (MODE 0) or out = acc - xprev (MODE 1); cc and sc are unused.
 // out may alias xprev (each row reads xprev[r] before writing out[r]); u is gathered across
 // rows and must not alias out or y.
-template <int MODE>
+template <int MODE, bool HAT>
 __global__ void __launch_bounds__(GTPB)
 k_gen_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr, const int32_t *__restrict__ col,
            const double *__restrict__ val, const double *u, const double *x, const double *xprev,
@@ -53,20 +56,44 @@ k_gen_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr, const i
         out[r] = acc;
         return;
     }
-    const double xr = x[r];
-    double wv = sc * (acc - cc * xr);
-    if (MODE == 1) wv -= xprev[r];
+    double wv;
+    if (HAT) {
+        wv = (MODE == 0) ? 0.5 * acc : acc - xprev[r];
+    } else {
+        wv = sc * (acc - cc * x[r]);
+        if (MODE == 1) wv -= xprev[r];
+    }
     out[r] = wv;
-    y[r] = (MODE == 0) ? c0 * xr + cj * wv : y[r] + cj * wv;
+    y[r] = (MODE == 0) ? c0 * x[r] + cj * wv : y[r] + cj * wv;
+}
+// [gen_step end]
+
+// vhat = (2/h)(M - c I) on the stored entries (padding stays 0); rows must store their diagonal
+__global__ void k_gen_map(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr, const int32_t *__restrict__ col,
+                          const double *__restrict__ val, const int32_t *__restrict__ rlen, double c, double s2,
+                          double *__restrict__ vhat)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t sl = r >> 5;
+    if (sl >= nslices) return;
+    const int lane = (int)(r & 31);
+    const int w = (int)((sptr[sl + 1] - sptr[sl]) >> 5);
+    const int len = (r < n) ? rlen[r] : 0;
+    for (int j = 0; j < w; j++) {
+        const int64_t e = sptr[sl] + 32 * (int64_t)j + lane;
+        double v = 0.0;
+        if (j < len) v = s2 * (val[e] - (col[e] == r ? c : 0.0));
+        vhat[e] = v;
+    }
 }
 
-template <int MODE>
+template <int MODE, bool HAT = false>
 int gen_step(evsl_ctx *c, const DevMatrix &M, const double *u, const double *x, const double *xprev,
              double *out, double *y, double cc, double sc, double c0, double cj)
 {
     const unsigned grid = (unsigned)((M.nslices * 32 + GTPB - 1) / GTPB);
-    k_gen_step<MODE><<<grid, GTPB, 0, c->stream>>>(M.n, M.nslices, M.sptr, M.col, M.val, u, x, xprev, out, y,
-                                                    cc, sc, c0, cj);
+    k_gen_step<MODE, HAT><<<grid, GTPB, 0, c->stream>>>(M.n, M.nslices, M.sptr, M.col, HAT ? M.vhat : M.val, u, x,
+                                                         xprev, out, y, cc, sc, c0, cj);
     c->launches++;
     return check_launch(c, "generalized sparse step");
 }
@@ -108,12 +135,15 @@ int solve_b(evsl_ctx *c, const double *x, double *y, double *t1, double *t2)
     const int deg = (int)cf.size() - 1;
     const double bc = 0.5 * (c->b_max + c->b_min), bh = 0.5 * (c->b_max - c->b_min);
     if (deg == 0) return scale_vec(c, B.n, const_cast<double *>(x), cf[0], y);
-    EVSL_TRY(gen_step<0>(c, B, x, x, nullptr, t1, y, bc, 1.0 / bh, cf[0], cf[1]));
+    const bool hat = B.vhat != nullptr;  // mapped values (2/bh)(B - bc I), made by set_csr_b
+    if (hat) EVSL_TRY((gen_step<0, true>(c, B, x, x, nullptr, t1, y, bc, 1.0 / bh, cf[0], cf[1])));
+    else EVSL_TRY(gen_step<0>(c, B, x, x, nullptr, t1, y, bc, 1.0 / bh, cf[0], cf[1]));
     const double *prev = x, *cur = t1;
     bool prev_tmp = false;  // prev is a temporary that the next term may overwrite
     for (int j = 2; j <= deg; j++) {
         double *out = prev_tmp ? const_cast<double *>(prev) : t2;
-        EVSL_TRY(gen_step<1>(c, B, cur, cur, prev, out, y, bc, 2.0 / bh, 0.0, cf[j]));
+        if (hat) EVSL_TRY((gen_step<1, true>(c, B, cur, cur, prev, out, y, bc, 2.0 / bh, 0.0, cf[j])));
+        else EVSL_TRY(gen_step<1>(c, B, cur, cur, prev, out, y, bc, 2.0 / bh, 0.0, cf[j]));
         prev = cur;
         cur = out;
         prev_tmp = true;
@@ -170,7 +200,7 @@ int filter_gen_run(evsl_ctx *c, const evsl_polfilt *pol, const double *zi, const
         h = graph_key_hash(h, c->b_coef.data(), sizeof(double) * c->b_coef.size());
         h = graph_key_hash(h, &c->b_min, sizeof c->b_min);
         h = graph_key_hash(h, &c->b_max, sizeof c->b_max);
-        const void *ptrs[] = {c->A.sptr, c->A.col, c->A.val, c->B.sptr, c->B.col, c->B.val,
+        const void *ptrs[] = {c->A.sptr, c->A.col, c->A.val, c->B.sptr, c->B.col, c->B.val, c->B.vhat,
                               v.zs, v.z, v.u, v.t1, v.t2, v.f1, v.f2};
         h = graph_key_hash(h, ptrs, sizeof ptrs);
         h = graph_key_hash(h, &c->A.n, sizeof c->A.n);
@@ -321,6 +351,22 @@ int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, doubl
     *deg = maxdeg;
     if (err) *err = e;
     return EVSL_ERR_NOCONV;
+}
+
+// Mapped values (2/bh)(B - bc I) of the current B for the solve's recurrence, when every row
+// of B stores its diagonal (else the solve uses B's values and the explicit shift).
+int gen_map_b(evsl_ctx *c)
+{
+    DevMatrix &B = c->B;
+    if (!B.has_diag || B.n == 0) return EVSL_OK;
+    if (!B.vhat) EVSL_TRY(ctx_alloc(c, (void **)&B.vhat, sizeof(double) * B.nstored));
+    const double bc = 0.5 * (c->b_max + c->b_min), bh = 0.5 * (c->b_max - c->b_min);
+    k_gen_map<<<(unsigned)((B.nslices * 32 + 255) / 256), 256, 0, c->stream>>>(B.n, B.nslices, B.sptr, B.col, B.val,
+                                                                               B.rlen, bc, 2.0 / bh, B.vhat);
+    c->launches++;
+    EVSL_TRY(check_launch(c, "generalized value mapping"));
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, "generalized value mapping");
 }
 
 int drv_polyB_apply(evsl_ctx *c, const double *x, double *y)

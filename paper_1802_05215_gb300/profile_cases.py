@@ -5,9 +5,11 @@
     python -m paper_1802_05215_gb300.profile_cases kpm       # KPM moment step, FP64 then FP32
     python -m paper_1802_05215_gb300.profile_cases multi     # 16-slice batched filter step, FP32
     python -m paper_1802_05215_gb300.profile_cases fp64rate  # dense FP64 vs FP32 GEMM rate (cuBLAS)
+    python -m paper_1802_05215_gb300.profile_cases gen       # generalized step: solves with p(B)
 
-Each case runs on the 100^3 7-point Laplacian (n = 1e6, nnz = 6.94e6) and prints the number of
-kernels the library launched.
+Each case but `gen` runs on the 100^3 7-point Laplacian (n = 1e6, nnz = 6.94e6); `gen` uses the
+1000^2 linear-element mass matrix (n = 1e6, nnz = 8.99e6).  Each prints the number of kernels
+the library launched.
 """
 from __future__ import annotations
 
@@ -89,7 +91,25 @@ def fp64rate():
     return None
 
 
-CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "fp64rate": fp64rate}
+def gen():
+    """Two solves y = p(B) x with the lsPol polynomial on [0.11, 1] (which holds the spectrum of
+    the 1000^2 mass matrix M (x) M, M = tridiag(1, 4, 1)/6): 2 x deg(p) launches of k_gen_step,
+    each solve one MODE 0 launch and then MODE 1 launches."""
+    import torch
+    from . import inputs, native
+    B = inputs.mass_matrix_2d(1000)
+    ctx = native.Context(0)
+    deg, _ = ctx.set_csr_b(B, 0.11, 1.0, 1e-13)
+    x = torch.randn(B.n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    ctx.polyB_apply(x, y)
+    ctx.polyB_apply(x, y)
+    torch.cuda.synchronize()
+    print(f"gen: p(B) degree {deg}")
+    return ctx
+
+
+CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "fp64rate": fp64rate, "gen": gen}
 
 if __name__ == "__main__":
     name = sys.argv[1] if len(sys.argv) > 1 else "cheb"
