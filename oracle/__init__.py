@@ -70,6 +70,10 @@ def _load():
         _lib.orc_slicer_landos.argtypes = [P, P, P, i32, i32, i64, d, d, i32, P, P]
         _lib.orc_lspol.restype = i32
         _lib.orc_lspol.argtypes = [d, d, d, i32, P, P]
+        _lib.orc_lspol_isqrt.restype = i32
+        _lib.orc_lspol_isqrt.argtypes = [d, d, d, i32, P, P]
+        _lib.orc_kpm_moments_gen.restype = i32
+        _lib.orc_kpm_moments_gen.argtypes = [i64, P, P, P, P, P, P, d, d, i32, P, i32, P, i32, i32, u64, d, d, P]
         _lib.orc_polyB_apply.restype = None
         _lib.orc_polyB_apply.argtypes = [i64, P, P, P, d, d, i32, P, P, P]
         _lib.orc_bounds_gen.restype = i32
@@ -244,6 +248,23 @@ def lspol(bmin, bmax, eps=1e-13, maxdeg=200):
     deg = C.c_int()
     st = _load().orc_lspol(bmin, bmax, eps, maxdeg, C.byref(deg), _p(coef))
     return dict(status=st, deg=deg.value, coef=coef[:deg.value + 1].copy(), bmin=bmin, bmax=bmax)
+
+
+def lspol_isqrt(bmin, bmax, eps=1e-13, maxdeg=200):
+    """Chebyshev interpolant q(t) ~ t^{-1/2} on [bmin, bmax] (the polynomial B^{-1/2}); a dict."""
+    coef = np.zeros(maxdeg + 1)
+    deg = C.c_int()
+    st = _load().orc_lspol_isqrt(bmin, bmax, eps, maxdeg, C.byref(deg), _p(coef))
+    return dict(status=st, deg=deg.value, coef=coef[:deg.value + 1].copy(), bmin=bmin, bmax=bmax)
+
+
+def kpm_moments_gen(A, B, lp, lq, M, nvec, seed, lmin, lmax):
+    """KPM moments mu_0..M of the pencil (A, B): p(B) ~ B^{-1} from lp, q(B) ~ B^{-1/2} from lq
+    (both on the same [bmin, bmax])."""
+    mu = np.zeros(M + 1)
+    _load().orc_kpm_moments_gen(*_csr_args(A), *_csr_args(B)[1:], lp["bmin"], lp["bmax"], lp["deg"], _p(lp["coef"]),
+                                lq["deg"], _p(lq["coef"]), M, nvec, seed, lmin, lmax, _p(mu))
+    return mu
 
 
 def poly_solve(B, lp, x):

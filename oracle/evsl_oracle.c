@@ -1336,6 +1336,37 @@ int orc_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double
     return -4;
 }
 
+/* lsPol for B^{-1/2} (Sec. 2.1: the DOS of a pencil needs starting vectors built with B^{1/2}
+ * or the Cholesky factor; for a well-conditioned mass matrix a polynomial replaces the
+ * factorisation).  READING: as orc_lspol with f(t) = t^{-1/2}: the Chebyshev interpolant at the
+ * Chebyshev-Gauss points, of the smallest degree k (up to maxdeg) whose relative error
+ * max |sqrt(t) p(t) - 1| on 2001 equispaced points is <= eps. */
+int orc_lspol_isqrt(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef)
+{
+    const double c = 0.5 * (bmax + bmin), h = 0.5 * (bmax - bmin);
+    for (int k = 1; k <= maxdeg; k++) {
+        const int N = k + 1;
+        for (int j = 0; j <= k; j++) {
+            double s = 0.0;
+            for (int q = 0; q < N; q++) {
+                const double th = M_PI * (q + 0.5) / N;
+                s += cos(j * th) / sqrt(c + h * cos(th));
+            }
+            coef[j] = (j == 0 ? 1.0 : 2.0) * s / N;
+        }
+        double err = 0.0;
+        for (int q = 0; q <= 2000; q++) {
+            const double t = bmin + (bmax - bmin) * q / 2000.0, u = (t - c) / h;
+            double p = 0.0;
+            for (int j = 0; j <= k; j++) p += coef[j] * orc_chebT(j, u);
+            err = fmax(err, fabs(sqrt(t) * p - 1.0));
+        }
+        if (err <= eps) { *deg = k; return 0; }
+    }
+    *deg = maxdeg;
+    return -4;
+}
+
 /* y = p(B) x with the Chebyshev recurrence on Bhat = (B - c I) / h */
 static void orc_polyB(const orc_csr *B, double c, double h, int deg, const double *coef,
                       const double *x, double *y, double *w0, double *w1, double *w2)
@@ -1583,4 +1614,50 @@ int orc_cheblannr_gen(int64_t n, const int64_t *rp, const int32_t *ci, const dou
     free(t); free(W); free(Z); free(T); free(Tk); free(S); free(th); free(z); free(wt);
     free(f0); free(f1); free(f2); free(u); free(Au); free(Bu);
     return status;
+}
+
+/* KPM moments of the pencil (A, B) (Sec. 2.1's DOS extended to A x = lambda B x): the moments of
+ * the DOS of S = B^{-1/2} A B^{-1/2}, whose eigenvalues are the pencil's.  With
+ * Shat = (S - cI)/d, Rademacher probes v_l (stream 2, k = l*n+i, as orc_kpm_moments),
+ * u_l = q(B) v_l ~ B^{-1/2} v_l (q: orc_lspol_isqrt) and y_0 = B u_l (~ B^{1/2} v_l):
+ *   mu_k = (1/nvec) sum_l v_l^T T_k(Shat) v_l = (1/nvec) sum_l u_l^T T_k(Mhat) y_0,
+ * with Mhat = (A B^{-1} - cI)/d and B^{-1} by p(B) (orc_lspol): T_k(Shat) = B^{1/2} T_k((B^{-1}A - cI)/d)
+ * B^{-1/2} and B T_k((B^{-1}A - cI)/d) = T_k(Mhat) B.  Recurrence y_1 = Mhat y_0,
+ * y_{k+1} = 2 Mhat y_k - y_{k-1}, each Mhat y = (A p(B) y - c y)/d. */
+int orc_kpm_moments_gen(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                        const int64_t *brp, const int32_t *bci, const double *bv, double bmin, double bmax,
+                        int bdeg, const double *bcoef, int sdeg, const double *scoef, int M, int nvec,
+                        uint64_t seed, double lmin, double lmax, double *mu)
+{
+    orc_csr A = {n, rp, ci, v}, B = {n, brp, bci, bv};
+    double *t = malloc(sizeof(double) * 3 * n);
+    orc_pencil P = {&A, &B, 0.5 * (bmax + bmin), 0.5 * (bmax - bmin), bdeg, bcoef, t, t + n, t + 2 * n};
+    const double c = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+    double *vl = malloc(sizeof(double) * n), *u = malloc(sizeof(double) * n);
+    double *y0 = malloc(sizeof(double) * n), *y1 = malloc(sizeof(double) * n), *y2 = malloc(sizeof(double) * n);
+    double *s = malloc(sizeof(double) * n), *As = malloc(sizeof(double) * n);
+    for (int k = 0; k <= M; k++) mu[k] = 0.0;
+    for (int l = 0; l < nvec; l++) {
+        for (int64_t i = 0; i < n; i++)
+            vl[i] = orc_sign(orc_draw(seed, ORC_STREAM_KPM, (uint64_t)l * (uint64_t)n + (uint64_t)i));
+        orc_polyB(&B, P.bc, P.bh, sdeg, scoef, vl, u, t, t + n, t + 2 * n);      /* u = q(B) v */
+        orc_matvec(&B, u, y0);                                                   /* y_0 = B u */
+        mu[0] += orc_dot(n, u, y0);
+        double *p0 = y0, *p1 = y1, *p2 = y2;
+        for (int k = 1; k <= M; k++) {
+            const double *src = (k == 1) ? p0 : p1;                              /* y_{k-1} */
+            double *dst = (k == 1) ? p1 : p2;                                    /* y_k */
+            orc_solveB(&P, src, s);
+            orc_matvec(&A, s, As);
+            for (int64_t i = 0; i < n; i++) {
+                const double mf = (As[i] - c * src[i]) / d;
+                dst[i] = (k == 1) ? mf : 2.0 * mf - p0[i];
+            }
+            mu[k] += orc_dot(n, u, dst);
+            if (k >= 2) { double *tmp = p0; p0 = p1; p1 = p2; p2 = tmp; }
+        }
+    }
+    for (int k = 0; k <= M; k++) mu[k] /= nvec;
+    free(t); free(vl); free(u); free(y0); free(y1); free(y2); free(s); free(As);
+    return 0;
 }

@@ -566,3 +566,74 @@ def test_cheblantr_config_2d_100(oracle_mod):
     assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * ex)
     assert r["res"].max() <= 1e-8
     assert np.max(np.abs(r["Y"].T @ r["Y"] - np.eye(69))) <= 1e-10
+
+
+def test_lspol_isqrt_is_a_polynomial_inverse_square_root(oracle_mod):
+    # |sqrt(t) q(t) - 1| <= eps on an independent fine grid, and q(B)^2 is B^{-1} on a vector
+    lq = oracle_mod.lspol_isqrt(0.11, 0.99, 1e-13)
+    assert lq["status"] == 0
+    tt = np.linspace(0.11, 0.99, 10001)
+    q = npcheb.chebval((tt - 0.55) / 0.44, lq["coef"])
+    assert np.max(np.abs(np.sqrt(tt) * q - 1.0)) <= 1.5e-13
+    B = I.mass_matrix_2d(12)
+    lo, hi = oracle_mod.bounds(B, 80, 0)
+    lq = oracle_mod.lspol_isqrt(lo, hi, 1e-13)
+    x = np.random.default_rng(1).standard_normal(B.n)
+    y = oracle_mod.poly_solve(B, lq, oracle_mod.poly_solve(B, lq, x))
+    assert np.linalg.norm(B.to_dense() @ y - x) <= 1e-12 * np.linalg.norm(x)
+
+
+def _pencil_lsp(oracle_mod, A, B):
+    blo, bhi = oracle_mod.bounds(B, 80, 0)
+    return oracle_mod.lspol(blo, bhi, 1e-13), oracle_mod.lspol_isqrt(blo, bhi, 1e-13)
+
+
+def test_kpm_gen_matches_dense_pencil_formula(oracle_mod):
+    # mu_k = mean_l v_l^T T_k(Shat) v_l with S = B^{-1/2} A B^{-1/2} from dense eigensolves and the
+    # same Rademacher probes; mu_0 = n up to the polynomials' 1e-13
+    nx = 6
+    A, B = I.laplacian_2d(nx), I.mass_matrix_2d(nx)
+    lp, lq = _pencil_lsp(oracle_mod, A, B)
+    lam = pencil_eigs(nx)
+    lo, hi = lam[0] - 0.5, lam[-1] * 1.01
+    M, nv, seed = 30, 4, 5
+    mu = oracle_mod.kpm_moments_gen(A, B, lp, lq, M, nv, seed, lo, hi)
+    wb, Qb = np.linalg.eigh(B.to_dense())
+    Bm12 = Qb @ np.diag(wb ** -0.5) @ Qb.T
+    w, Z = np.linalg.eigh(Bm12 @ A.to_dense() @ Bm12)
+    assert np.max(np.abs(w - lam)) <= 1e-12 * lam[-1]
+    lh = (w - 0.5 * (hi + lo)) / (0.5 * (hi - lo))
+    P = Z.T @ I.rademacher_block(A.n, nv, seed)
+    want = np.array([np.mean(np.sum(P * P * np.cos(k * np.arccos(lh))[:, None], axis=0))
+                     for k in range(M + 1)])
+    assert abs(mu[0] - A.n) <= 1e-12 * A.n
+    assert np.max(np.abs(mu - want)) <= 1e-11 * A.n
+
+
+def test_kpm_gen_with_scaled_identity_is_standard_kpm(oracle_mod):
+    # B = 2I: the pencil's eigenvalues are lambda(A)/2, q(B) v = v / sqrt 2 and B u = sqrt 2 v, so
+    # the moments on [lmin/2, lmax/2] are the standard ones on [lmin, lmax]
+    A = I.anderson_3d(6, 3.0, 1)
+    n = A.n
+    B2 = I.CSR(n, np.arange(n + 1), np.arange(n, dtype=np.int32), np.full(n, 2.0))
+    lp, lq = oracle_mod.lspol(1.5, 2.5, 1e-13), oracle_mod.lspol_isqrt(1.5, 2.5, 1e-13)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    mg = oracle_mod.kpm_moments_gen(A, B2, lp, lq, 40, 3, 7, lo / 2, hi / 2)
+    ms = oracle_mod.kpm_moments(A, 40, 3, 7, lo, hi)
+    assert np.max(np.abs(mg - ms)) <= 1e-12 * n
+
+
+def test_kpm_gen_statistics_against_closed_form_trace(oracle_mod):
+    # E[mu_k] = sum_ij T_k(lambda_hat_ij) over the pencil's closed-form eigenvalues; the
+    # stochastic error is below 6 sqrt(2 ||T_k||_F^2 / nvec)
+    nx, M, nv = 30, 40, 20
+    A, B = I.laplacian_2d(nx), I.mass_matrix_2d(nx)
+    lp, lq = _pencil_lsp(oracle_mod, A, B)
+    lam = pencil_eigs(nx)
+    lo, hi = 0.0, lam[-1] * 1.01
+    mu = oracle_mod.kpm_moments_gen(A, B, lp, lq, M, nv, 0, lo, hi)
+    lh = (lam - 0.5 * (hi + lo)) / (0.5 * (hi - lo))
+    for k in range(M + 1):
+        tk = np.cos(k * np.arccos(lh))
+        sig = np.sqrt(2.0 * np.sum(tk * tk) / nv)
+        assert abs(mu[k] - tk.sum()) <= 6 * sig + 1e-9
