@@ -680,7 +680,9 @@ def run_gen_2d(args):
     (2-D 5-point Laplacian, 2-D linear-element mass matrix M (x) M).  Two legs:
     (1) the solve y = p(B) x on the 1000^2 mass matrix (n = 1e6, 9e6 nonzeros; matrix and
         vectors above L2 size): per-launch time of k_gen_step from CUDA events, its roofline;
-    (2) filtered non-restart Lanczos (ChebLanNr with B-inner products) on the 200^2 pencil over
+    (2) the pencil's KPM density (degree 120, 20 probes, starting vectors by q(B) ~ B^{-1/2}) on
+        the 200^2 pencil, sliced into 4 parts of [60, 70] (closed-form counts per slice);
+    (3) filtered non-restart Lanczos (ChebLanNr with B-inner products) on the 200^2 pencil over
         a slice cut between distinct closed-form eigenvalues: eigenpairs/s with the filter's
         CUDA graph and with direct launches (bitwise-equal results), counts checked against the
         closed form.  B's bounds come from the library's Lanczos bounds on B."""
@@ -738,6 +740,17 @@ def run_gen_2d(args):
         ctx.set_csr(A)
         q2, _ = ctx.set_csr_b(B, blo, bhi, 1e-13)
         lo, hi = ctx.bounds_gen(BOUNDS_STEPS, SEED)
+        # the pencil's density (KPM with q(B) ~ B^{-1/2} starting vectors) and its slicing
+        ctx.kpm_dos_gen(4, 1, SEED, lo, hi)                                        # warm-up
+        t0 = time.perf_counter()
+        mu = ctx.kpm_dos_gen(KPM_DEG, 20, SEED, lo, hi)
+        t_dos = time.perf_counter() - t0
+        xi, eta, ns = 60.0, 70.0, 4
+        sli, est = native.slice_by_dos(mu, A.n, lo, hi, xi, eta, ns, 0)
+        counts = [int(np.count_nonzero((lam >= sli[i]) & (lam < sli[i + 1]))) for i in range(ns)]
+        out["dos"] = {"degree": KPM_DEG, "probes": 20, "seconds": t_dos, "interval": [xi, eta],
+                      "slices": [float(x) for x in sli], "estimated_counts": [float(x) for x in est],
+                      "closed_form_counts": counts, "mu0_over_n": float(mu[0] / A.n)}
         f = native.cheb_filter_build(a, b, lo, hi)
         m = max(6 * exact, 200)
         cap = exact + 16

@@ -327,9 +327,15 @@ void evsl_batch_destroy(evsl_batch *batch);
 int evsl_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, int cap,
                double *err);
 
+/* evsl_lspol_isqrt (host only): as evsl_lspol for q(t) ~ t^{-1/2} (relative error
+ * max |sqrt(t) q(t) - 1|): the polynomial B^{-1/2} that builds the starting vectors of the
+ * pencil's density (Sec. 2.1). */
+int evsl_lspol_isqrt(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef,
+                     int cap, double *err);
+
 /* Mass matrix B (host CSR, same conventions and errors as evsl_set_csr) with its spectrum inside
  * [bmin, bmax], and its polynomial inverse p(B) (evsl_lspol with eps, maxdeg; *deg and *err may be
- * NULL).  Replaces any previous B; evsl_set_csr leaves B in place.  The solvers below need B and
+ * NULL, and report p) and inverse square root q(B) (evsl_lspol_isqrt, same eps and maxdeg).  Replaces any previous B; evsl_set_csr leaves B in place.  The solvers below need B and
  * A of the same order.  Errors: those of evsl_set_csr; EVSL_ERR_ARG if not 0 < bmin < bmax,
  * eps <= 0 or maxdeg < 1; EVSL_ERR_NOCONV if maxdeg did not reach eps (B and the degree-maxdeg
  * polynomial are set all the same). */
@@ -340,6 +346,16 @@ int evsl_set_csr_b(evsl_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32
 /* y = p(B) x (the approximate solve with B): x, y DEVICE pointers to n doubles, y distinct from
  * x.  Synchronous.  Errors: EVSL_ERR_ARG, EVSL_ERR_STATE without B. */
 int evsl_polyB_apply(evsl_ctx *ctx, const double *x, double *y);
+
+/* KPM moments of the pencil (Sec. 2.1's density extended to A x = lambda B x): the moments of the
+ * density of S = B^{-1/2} A B^{-1/2} on [lmin, lmax] (the pencil's bounds, evsl_bounds_gen),
+ * mu[k] = (1/nvec) sum_l v_l^T T_k((S - cI)/d) v_l for the Rademacher probes of evsl_kpm_dos, so
+ * mu[0] = n up to the polynomials' accuracy.  Computed as u_l^T T_k((A B^{-1} - cI)/d) B u_l with
+ * u_l = q(B) v_l and B^{-1} by p(B) (every degree one solve with B and one product with A).  mu:
+ * host array of degree + 1 doubles; FP64; the moments feed evsl_slice_by_dos unchanged.  Errors:
+ * EVSL_ERR_ARG, EVSL_ERR_STATE (as evsl_bounds_gen). */
+int evsl_kpm_dos_gen(evsl_ctx *ctx, int degree, int nvec, uint64_t seed, double lmin, double lmax,
+                     double *mu);
 
 /* Spectral bounds of the pencil: `steps` unfiltered steps of the B-inner-product Lanczos
  * (Algorithm 3) on B^{-1} A from a seeded start (Lanczos stream, index 0), with p(B) for B^{-1};

@@ -424,6 +424,25 @@ int evsl_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, doubl
     return host_lspol(bmin, bmax, eps, maxdeg, deg, coef, err);
 }
 
+int evsl_lspol_isqrt(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, int cap, double *err)
+{
+    if (!(bmin > 0.0) || !(bmax > bmin) || !(eps > 0.0) || maxdeg < 1 || !deg || !coef) return EVSL_ERR_ARG;
+    if (cap < maxdeg + 1) {
+        *deg = maxdeg;
+        return EVSL_ERR_CAPACITY;
+    }
+    return host_lspol(bmin, bmax, eps, maxdeg, deg, coef, err, 1);
+}
+
+int evsl_kpm_dos_gen(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax, double *mu)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (degree < 0 || nvec < 1 || !mu || !(lmax > lmin)) return ctx_fail(c, EVSL_ERR_ARG, "kpm_dos_gen: bad arguments");
+    cudaSetDevice(c->device);
+    return drv_kpm_gen(c, degree, nvec, seed, lmin, lmax, mu);
+}
+
 int evsl_set_csr_b(evsl_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *val,
                    double bmin, double bmax, double eps, int maxdeg, int *deg, double *err)
 {
@@ -431,21 +450,26 @@ int evsl_set_csr_b(evsl_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t
     c->err.clear();
     if (!(bmin > 0.0) || !(bmax > bmin) || !(eps > 0.0) || maxdeg < 1)
         return ctx_fail(c, EVSL_ERR_ARG, "set_csr_b: need 0 < bmin < bmax, eps > 0 and maxdeg >= 1");
-    std::vector<double> coef((size_t)maxdeg + 1);
-    int d = 0;
+    std::vector<double> coef((size_t)maxdeg + 1), coef_s((size_t)maxdeg + 1);
+    int d = 0, ds = 0;
     filter_graphs_clear(c);  // cached generalized-filter graphs hold B's device addresses
-    double e = 0.0;
+    double e = 0.0, es = 0.0;
     const int pst = host_lspol(bmin, bmax, eps, maxdeg, &d, coef.data(), &e);
+    const int sst = host_lspol(bmin, bmax, eps, maxdeg, &ds, coef_s.data(), &es, 1);
     cudaSetDevice(c->device);
     EVSL_TRY(sell_upload_b(c, n, row_ptr, col_idx, val));
     coef.resize((size_t)d + 1);
+    coef_s.resize((size_t)ds + 1);
     c->b_coef = coef;
+    c->b_coef_isqrt = coef_s;
     c->b_min = bmin;
     c->b_max = bmax;
     EVSL_TRY(gen_map_b(c));
     if (deg) *deg = d;
     if (err) *err = e;
     if (pst != EVSL_OK) return ctx_fail(c, pst, "set_csr_b: degree %d reached with error %g > eps %g", d, e, eps);
+    if (sst != EVSL_OK)
+        return ctx_fail(c, sst, "set_csr_b: B^{-1/2} polynomial degree %d reached with error %g > eps %g", ds, es, eps);
     return EVSL_OK;
 }
 

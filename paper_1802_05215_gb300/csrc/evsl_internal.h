@@ -55,6 +55,7 @@ struct evsl_ctx {
     DevMatrix B;
     double b_min = 0.0, b_max = 0.0;
     std::vector<double> b_coef;
+    std::vector<double> b_coef_isqrt;  // q(t) ~ t^{-1/2} on the same interval (density of the pencil)
     // grow-only workspaces, indexed by WS_* slots
     std::vector<void *> ws_ptr;
     std::vector<size_t> ws_bytes;
@@ -98,7 +99,7 @@ enum WsSlot {
     WS_PARTIAL = 0, WS_SCAL, WS_W0, WS_W1, WS_W2, WS_KPM_PART, WS_F32_X, WS_F32_Y,
     WS_LAN_U, WS_LAN_Q, WS_LAN_Y, WS_LAN_Z, WS_LAN_VEC, WS_LAN_T, WS_LAN_S, WS_LAN_IDX,
     WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_POL_V, WS_POL_W, WS_POL_B, WS_POL_S, WS_POL_Y, WS_POL_R, WS_TUNE, WS_POL_H,
-    WS_GEN_BASIS, WS_GEN_VEC, WS_GEN_SCAL,
+    WS_GEN_BASIS, WS_GEN_VEC, WS_GEN_SCAL, WS_GEN_MU,
     WS_COUNT
 };
 
@@ -161,6 +162,9 @@ int convert_f64_to_f32(evsl_ctx *c, int64_t count, const double *x, float *y);
 int convert_f32_to_f64(evsl_ctx *c, int64_t count, const float *x, double *y);
 int fill_uniform_f64(evsl_ctx *c, int64_t n, uint64_t seed, int stream, uint64_t index,
                      double *x);
+// x[i] = +-1 by the top bit of draw(seed, stream, index*n + i) (KPM probe `index`)
+int fill_rademacher_f64(evsl_ctx *c, int64_t n, uint64_t seed, int stream, uint64_t index,
+                        double *x);
 
 // ---- dense kernels (kernels_dense.cu)
 // Deterministic reductions: partial sums per row chunk, then a fixed-order sum per output.
@@ -245,9 +249,11 @@ int drv_filter_apply(evsl_ctx *c, const evsl_polfilt *pol, int nvec, const doubl
 int drv_filter_apply_multi(evsl_ctx *c, int npol, const evsl_polfilt *pols, const double *X,
                            double *Y, evsl_precision prec);
 // generalized problems (generalized.cu)
-int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, double *err);
+// kind 0: p(t) ~ 1/t; kind 1: p(t) ~ t^{-1/2}
+int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, double *err, int kind = 0);
 int gen_map_b(evsl_ctx *c);
 int drv_polyB_apply(evsl_ctx *c, const double *x, double *y);
+int drv_kpm_gen(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax, double *mu);
 int drv_bounds_gen(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax);
 int drv_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *o,
                       int cap, int *nev, double *lam, double *Y, double *res, evsl_stats *st);

@@ -126,12 +126,12 @@ int get_vecs(evsl_ctx *c, Vecs &v)
     return EVSL_OK;
 }
 
-// y = p(B) x: y = c_0 x + c_1 w_1 + ..., w_1 = Bhat x, w_j = 2 Bhat w_{j-1} - w_{j-2}.
-// t1, t2: temporaries; y must not alias x, t1 or t2 (x is only read).
-int solve_b(evsl_ctx *c, const double *x, double *y, double *t1, double *t2)
+// y = p(B) x for a Chebyshev series p on [b_min, b_max]: y = c_0 x + c_1 w_1 + ...,
+// w_1 = Bhat x, w_j = 2 Bhat w_{j-1} - w_{j-2}.  t1, t2: temporaries; y must not alias x, t1 or t2
+// (x is only read).
+int apply_poly_b(evsl_ctx *c, const std::vector<double> &cf, const double *x, double *y, double *t1, double *t2)
 {
     const DevMatrix &B = c->B;
-    const std::vector<double> &cf = c->b_coef;
     const int deg = (int)cf.size() - 1;
     const double bc = 0.5 * (c->b_max + c->b_min), bh = 0.5 * (c->b_max - c->b_min);
     if (deg == 0) return scale_vec(c, B.n, const_cast<double *>(x), cf[0], y);
@@ -149,6 +149,12 @@ int solve_b(evsl_ctx *c, const double *x, double *y, double *t1, double *t2)
         prev_tmp = true;
     }
     return EVSL_OK;
+}
+
+// y = p(B) x with the lsPol polynomial p ~ B^{-1} (the approximate solve with B)
+int solve_b(evsl_ctx *c, const double *x, double *y, double *t1, double *t2)
+{
+    return apply_poly_b(c, c->b_coef, x, y, t1, t2);
 }
 
 // z = rho(Mhat) zi with Mhat = (A p(B) - cc I) / dd: f_1 = Mhat zi, f_j = 2 Mhat f_{j-1} - f_{j-2},
@@ -308,11 +314,12 @@ int check_pencil(evsl_ctx *c, const char *what)
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// Chebyshev interpolant of 1/t on [bmin, bmax] at the N = k + 1 Chebyshev-Gauss points
-// theta_q = pi (q + 1/2) / N: c_j = (2 - [j = 0]) / N sum_q cos(j theta_q) / t(theta_q),
+// Chebyshev interpolant of f(t) = 1/t (kind 0, the solve with B) or f(t) = t^{-1/2} (kind 1, the
+// starting vectors of the pencil's density) on [bmin, bmax] at the N = k + 1 Chebyshev-Gauss points
+// theta_q = pi (q + 1/2) / N: c_j = (2 - [j = 0]) / N sum_q cos(j theta_q) f(t(theta_q)),
 // t(theta) = bc + bh cos(theta).  The degree is the smallest k <= maxdeg with
-// max |t p(t) - 1| <= eps over 2001 equispaced points of [bmin, bmax] (p by Clenshaw's sum).
-int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, double *err)
+// max |p(t) / f(t) - 1| <= eps over 2001 equispaced points of [bmin, bmax] (p by Clenshaw's sum).
+int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, double *coef, double *err, int kind)
 {
     const double bc = 0.5 * (bmax + bmin), bh = 0.5 * (bmax - bmin);
     const int NPTS = 2001;
@@ -322,7 +329,8 @@ int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, doubl
         std::vector<double> th(N), f(N);
         for (int q = 0; q < N; q++) {
             th[q] = PI * (q + 0.5) / N;
-            f[q] = 1.0 / (bc + bh * std::cos(th[q]));
+            const double t = bc + bh * std::cos(th[q]);
+            f[q] = (kind == 0) ? 1.0 / t : 1.0 / std::sqrt(t);
         }
         for (int j = 0; j <= k; j++) {
             double s = 0.0;
@@ -340,7 +348,7 @@ int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, doubl
                 b1 = b0;
             }
             const double p = coef[0] + x * b1 - b2;
-            e = std::max(e, std::fabs(t * p - 1.0));
+            e = std::max(e, std::fabs((kind == 0 ? t : std::sqrt(t)) * p - 1.0));
         }
         if (e <= eps) {
             *deg = k;
@@ -558,4 +566,61 @@ int drv_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, 
         stats->t_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return status;
+}
+
+// KPM moments of the pencil (the density of S = B^{-1/2} A B^{-1/2}, whose eigenvalues are the
+// pencil's): for Rademacher probes v_l (the KPM stream and indexing of the standard moments),
+// u_l = q(B) v_l ~ B^{-1/2} v_l and y_0 = B u_l, mu_k = (1/nvec) sum_l u_l^T y_k with
+// y_1 = Mhat y_0, y_{k+1} = 2 Mhat y_k - y_{k-1}, Mhat = (A p(B) - cI)/d -- the generalized
+// filter's step, since v^T T_k(Shat) v = u^T B T_k((B^{-1}A - cI)/d) u = u^T T_k(Mhat) B u.
+// Each probe's moments go to a device row (deterministic dot products); the host adds the rows
+// in probe order.  The recurrence steps write their unused y accumulator into a scratch vector.
+int drv_kpm_gen(evsl_ctx *c, int M, int nvec, uint64_t seed, double lmin, double lmax, double *mu)
+{
+    EVSL_TRY(check_pencil(c, "kpm_dos_gen"));
+    if (c->b_coef_isqrt.empty()) return ctx_fail(c, EVSL_ERR_STATE, "kpm_dos_gen: no B^{-1/2} polynomial");
+    const int64_t n = c->A.n;
+    int st = EVSL_OK;
+    double *p = (double *)ctx_ws(c, WS_GEN_VEC, sizeof(double) * (size_t)n * Vecs::COUNT, &st);
+    if (st) return st;
+    double *v = p, *u = p + n, *ya = p + 2 * n, *yb = p + 3 * n, *sv = p + 4 * n, *t1 = p + 5 * n,
+           *t2 = p + 6 * n, *scr = p + 7 * n;
+    const size_t rows = (size_t)nvec * (M + 1);
+    double *mud = (double *)ctx_ws(c, WS_GEN_MU, sizeof(double) * rows, &st);
+    if (st) return st;
+    const double cc = 0.5 * (lmax + lmin), dd = 0.5 * (lmax - lmin);
+    const DevMatrix &A = c->A;
+    for (int l = 0; l < nvec; l++) {
+        double *row = mud + (size_t)l * (M + 1);
+        EVSL_TRY(fill_rademacher_f64(c, n, seed, SM_STREAM_KPM, (uint64_t)l, v));
+        EVSL_TRY(apply_poly_b(c, c->b_coef_isqrt, v, u, t1, t2));                       // u = q(B) v
+        EVSL_TRY(gen_step<2>(c, c->B, u, nullptr, nullptr, ya, nullptr, 0.0, 0.0, 0.0, 0.0));  // y_0 = B u
+        EVSL_TRY(coldot(c, n, 1, u, n, ya, n, row));
+        const double *prev = nullptr;
+        double *cur = ya;
+        for (int k = 1; k <= M; k++) {
+            EVSL_TRY(solve_b(c, cur, sv, t1, t2));                                           // p(B) y_{k-1}
+            double *out;
+            if (k == 1) {
+                out = yb;
+                EVSL_TRY(gen_step<0>(c, A, sv, cur, nullptr, out, scr, cc, 1.0 / dd, 0.0, 0.0));
+            } else {
+                out = const_cast<double *>(prev);  // y_{k-2}'s buffer, read before it is written
+                EVSL_TRY(gen_step<1>(c, A, sv, cur, prev, out, scr, cc, 2.0 / dd, 0.0, 0.0));
+            }
+            prev = cur;
+            cur = out;
+            EVSL_TRY(coldot(c, n, 1, u, n, cur, n, row + k));
+        }
+    }
+    std::vector<double> h(rows);
+    cudaError_t e = cudaMemcpyAsync(h.data(), mud, sizeof(double) * rows, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "kpm_dos_gen readback");
+    for (int k = 0; k <= M; k++) {
+        double sum = 0.0;
+        for (int l = 0; l < nvec; l++) sum += h[(size_t)l * (M + 1) + k];
+        mu[k] = sum / nvec;
+    }
+    return EVSL_OK;
 }

@@ -397,6 +397,13 @@ __global__ void k_fill_uniform(int64_t n, uint64_t key, uint64_t index, double *
     }
 }
 
+// +-1 from the top bit of draw(key, index*n + i): probe `index` of the KPM convention
+__global__ void k_fill_sign(int64_t n, uint64_t key, uint64_t index, double *x)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = (sm_draw(key, index * (uint64_t)n + (uint64_t)i) >> 63) ? -1.0 : 1.0;
+}
+
 inline unsigned blocks_for(int64_t threads, int tpb) { return (unsigned)((threads + tpb - 1) / tpb); }
 
 }  // namespace
@@ -904,6 +911,13 @@ int fill_uniform_f64(evsl_ctx *c, int64_t n, uint64_t seed, int stream, uint64_t
     k_fill_uniform<<<blocks_for(n, 256), 256, 0, c->stream>>>(n, sm_key(seed, (uint64_t)stream), index, x);
     c->launches++;
     return check_launch(c, "fill_uniform");
+}
+
+int fill_rademacher_f64(evsl_ctx *c, int64_t n, uint64_t seed, int stream, uint64_t index, double *x)
+{
+    k_fill_sign<<<blocks_for(n, 256), 256, 0, c->stream>>>(n, sm_key(seed, (uint64_t)stream), index, x);
+    c->launches++;
+    return check_launch(c, "fill_rademacher");
 }
 
 // ------------------------------------------------------------------------------------------

@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
         "evsl_batch_destroy": (None, [P]),
         "evsl_lspol": (i32, [d, d, d, i32, P, P, i32, P]),
         "evsl_set_csr_b": (i32, [P, i64, P, P, P, d, d, d, i32, P, P]),
+        "evsl_lspol_isqrt": (i32, [d, d, d, i32, P, P, i32, P]),
+        "evsl_kpm_dos_gen": (i32, [P, i32, i32, u64, d, d, P]),
         "evsl_polyB_apply": (i32, [P, P, P]),
         "evsl_bounds_gen": (i32, [P, i32, u64, P, P]),
         "evsl_chebLanNr_gen": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
@@ -151,13 +153,14 @@ class Filter:
     lmax = property(lambda s: s.pol.lmax)
 
 
-def lspol(bmin, bmax, eps=1e-13, maxdeg=200):
-    """Chebyshev coefficients of p(t) ~ 1/t on [bmin, bmax] (the polynomial B^{-1}):
-    dict(status, deg, coef, err)."""
+def lspol(bmin, bmax, eps=1e-13, maxdeg=200, isqrt=False):
+    """Chebyshev coefficients of p(t) ~ 1/t (or ~ t^{-1/2} with isqrt) on [bmin, bmax] (the
+    polynomial B^{-1} or B^{-1/2}): dict(status, deg, coef, err)."""
     lib = load()
     coef = np.zeros(maxdeg + 1)
     deg, err = C.c_int(), C.c_double()
-    st = lib.evsl_lspol(bmin, bmax, eps, maxdeg, C.byref(deg), _addr(coef), len(coef), C.byref(err))
+    fn = lib.evsl_lspol_isqrt if isqrt else lib.evsl_lspol
+    st = fn(bmin, bmax, eps, maxdeg, C.byref(deg), _addr(coef), len(coef), C.byref(err))
     if st not in (EVSL_OK, -4):
         raise EvslError(st, "lspol")
     return dict(status=st, deg=deg.value, coef=coef[:deg.value + 1].copy(), err=err.value)
@@ -263,6 +266,12 @@ class Context:
     def polyB_apply(self, x, y):
         """y = p(B) x for device vectors of n doubles (synchronous)."""
         self._check(self.lib.evsl_polyB_apply(self.h, _addr(x), _addr(y)), "polyB_apply")
+
+    def kpm_dos_gen(self, degree, nvec, seed, lmin, lmax):
+        """KPM moments mu_0..degree of the pencil (the density of B^{-1/2} A B^{-1/2})."""
+        mu = np.zeros(degree + 1)
+        self._check(self.lib.evsl_kpm_dos_gen(self.h, degree, nvec, seed, lmin, lmax, _addr(mu)), "kpm_dos_gen")
+        return mu
 
     def bounds_gen(self, steps=80, seed=0):
         """Spectral bounds of the pencil (A, B) by B-Lanczos on B^{-1} A."""

@@ -121,6 +121,7 @@ def test_entry_points_reject_null_context_and_bad_arguments(native):
     assert lib.evsl_set_csr_b(nul, 4, nul, nul, nul, 0.5, 1.0, 1e-13, 50, nul, nul) == -1
     assert lib.evsl_polyB_apply(nul, nul, nul) == -1
     assert lib.evsl_bounds_gen(nul, 10, 0, buf, buf) == -1
+    assert lib.evsl_kpm_dos_gen(nul, 10, 2, 0, 0.0, 1.0, buf) == -1
     assert lib.evsl_chebLanNr_gen(nul, 0.0, 1.0, nul, nul, 1, ctypes.byref(i32()), buf, nul, buf, nul) == -1
     nodes = np.array([[0.1, 0.5, 0.9]])
     weights = np.array([[0.2, 0.3, 0.5]])
@@ -148,3 +149,15 @@ def test_lspol_matches_oracle(native, oracle_mod):
     for bad in [(0.0, 1.0, 1e-13), (1.0, 0.5, 1e-13), (0.5, 1.0, 0.0)]:
         with pytest.raises(native.EvslError):
             native.lspol(*bad)
+
+
+def test_lspol_isqrt_matches_oracle(native, oracle_mod):
+    # the library's host q(t) ~ t^{-1/2} and the oracle's: same degree and coefficients
+    for bmin, bmax, eps in [(0.11, 0.99, 1e-13), (1.0 / 9.0, 1.0, 1e-10), (0.5, 4.0, 1e-13)]:
+        lq = native.lspol(bmin, bmax, eps, isqrt=True)
+        lo = oracle_mod.lspol_isqrt(bmin, bmax, eps)
+        assert lq["status"] == 0 and lo["status"] == 0 and lq["deg"] == lo["deg"]
+        assert np.max(np.abs(lq["coef"] - lo["coef"])) <= 1e-14 * np.abs(lo["coef"]).max()
+        assert lq["err"] <= eps
+    with pytest.raises(native.EvslError):
+        native.lspol(-1.0, 1.0, 1e-13, isqrt=True)

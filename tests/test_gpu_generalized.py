@@ -139,3 +139,34 @@ def test_cheblannr_gen_graph_replay_bitwise_equals_direct(ctx, nat, oracle_mod):
     assert out[0]["nev"] == out[1]["nev"] > 0
     assert np.array_equal(out[0]["lam"], out[1]["lam"]) and np.array_equal(out[0]["res"], out[1]["res"])
     assert np.array_equal(out[0]["Y"][:out[0]["nev"]], out[1]["Y"][:out[1]["nev"]])
+
+
+def test_kpm_gen_matches_oracle_and_slices(ctx, nat, oracle_mod):
+    # the pencil's KPM moments against the oracle's (same probes, p and q from the same interval),
+    # mu_0 = n, and the DOS slicer on them gives the oracle's slices
+    A, B, lp = _pencil(ctx, oracle_mod, 20)
+    lq = oracle_mod.lspol_isqrt(lp["bmin"], lp["bmax"], 1e-13)
+    lo, hi = oracle_mod.bounds_gen(A, B, lp, 80, 0)
+    for M, nv, seed in [(50, 7, 0), (1, 1, 3), (0, 2, 1)]:
+        mu = ctx.kpm_dos_gen(M, nv, seed, lo, hi)
+        mo = oracle_mod.kpm_moments_gen(A, B, lp, lq, M, nv, seed, lo, hi)
+        assert abs(mu[0] - A.n) <= 1e-12 * A.n
+        assert np.max(np.abs(mu - mo)) <= 1e-11 * A.n
+    mu = ctx.kpm_dos_gen(60, 10, 0, lo, hi)
+    mo = oracle_mod.kpm_moments_gen(A, B, lp, lq, 60, 10, 0, lo, hi)
+    s, e = nat.slice_by_dos(mu, A.n, lo, hi, 1.0, 60.0, 5, 0)
+    so, eo = oracle_mod.slicer(mo, lo, hi, 1.0, 60.0, 5, None)
+    assert np.max(np.abs(s - so)) <= 1e-8 * (hi - lo) and np.max(np.abs(e - eo)) <= 1e-6 * A.n
+
+
+def test_kpm_gen_scaled_identity_equals_standard_kpm(ctx, nat, oracle_mod):
+    # B = 2I: the pencil's moments on [lmin/2, lmax/2] are the standard moments on [lmin, lmax]
+    A = I.anderson_3d(9, 3.0, 1)
+    n = A.n
+    B2 = I.CSR(n, np.arange(n + 1), np.arange(n, dtype=np.int32), np.full(n, 2.0))
+    ctx.set_csr(A)
+    ctx.set_csr_b(B2, 1.5, 2.5, 1e-13)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    mg = ctx.kpm_dos_gen(40, 3, 7, lo / 2, hi / 2)
+    ms = ctx.kpm_dos(40, 3, 7, lo, hi)
+    assert np.max(np.abs(mg - ms)) <= 1e-12 * n
