@@ -72,6 +72,9 @@ def _load():
         _lib.orc_lspol.argtypes = [d, d, d, i32, P, P]
         _lib.orc_lspol_isqrt.restype = i32
         _lib.orc_lspol_isqrt.argtypes = [d, d, d, i32, P, P]
+        _lib.orc_cheblantr_gen.restype = i32
+        _lib.orc_cheblantr_gen.argtypes = [i64, P, P, P, P, P, P, d, d, i32, P, d, d, i32, d, d, i32, P, d,
+                                           i32, i32, i32, d, d, u64, i32, P, P, P, P, P]
         _lib.orc_kpm_moments_gen.restype = i32
         _lib.orc_kpm_moments_gen.argtypes = [i64, P, P, P, P, P, P, d, d, i32, P, i32, P, i32, i32, u64, d, d, P]
         _lib.orc_polyB_apply.restype = None
@@ -300,6 +303,27 @@ def cheblannr_gen(A, B, lp, a, b, pol, m=200, ncycle=10, tol=1e-8, tau1=1e-10, s
     k = nev.value
     return dict(status=st, nev=k, lam=lam[:k].copy(), Y=X[:, :k].copy(), res=res[:k].copy(),
                 niter=int(stats[0]), nmv=int(stats[1]))
+
+
+def cheblantr_gen(A, B, lp, a, b, pol, m=100, maxit=0, ncycle=10, tol=1e-8, tau1=1e-10, seed=0, cap=None,
+                  right_closed=True):
+    """Filtered thick-restart Lanczos with locking for A x = lambda B x (B-orthonormal
+    eigenvectors); stats as cheblantr (npass = 0)."""
+    cap = cap or (m + 64)
+    maxit = maxit or 20 * m
+    lam = np.empty(cap)
+    res = np.empty(cap)
+    X = np.empty((A.n, cap), order="F")
+    nev = C.c_int()
+    stats = np.zeros(4, dtype=np.int64)
+    coef = np.ascontiguousarray(pol["coef"], dtype=np.float64)
+    st = _load().orc_cheblantr_gen(*_csr_args(A), *_csr_args(B)[1:], lp["bmin"], lp["bmax"], lp["deg"],
+                                   _p(lp["coef"]), a, b, int(right_closed), pol["lmin"], pol["lmax"],
+                                   len(coef) - 1, _p(coef), pol["bar"], m, maxit, ncycle, tol, tau1, seed, cap,
+                                   C.byref(nev), _p(lam), _p(X), _p(res), _p(stats))
+    k = nev.value
+    return dict(status=st, nev=k, lam=lam[:k].copy(), Y=X[:, :k].copy(), res=res[:k].copy(),
+                niter=int(stats[0]), nmv=int(stats[1]), nrestart=int(stats[2]))
 
 
 def chebsi(A, a, b, pol, nv, maxit=100, tol=1e-8, seed=0, cap=None, right_closed=True):

@@ -1661,3 +1661,279 @@ int orc_kpm_moments_gen(int64_t n, const int64_t *rp, const int32_t *ci, const d
     free(t); free(vl); free(u); free(y0); free(y1); free(y2); free(s); free(As);
     return 0;
 }
+
+/* ---- Thick-restart filtered Lanczos with locking for A x = lambda B x ------------------ */
+/* Vectors come in pairs (w, z = B w); the inner product of two z-vectors is (z, z')_{B^{-1}} =
+ * w^T z', so a pair basis (W, Z) has W^T Z = I.  Locked eigenvectors U are B-orthonormal and
+ * BU = B U is kept beside them: deflating z against them is z -= BU (U^T z), the (I - B U U^T)
+ * of the paper's generalized TR scheme (Sec. 2.5). */
+
+/* z = rho(Mhat) zi, Mhat = (A B^{-1} - cI)/d, the recurrence of orc_cheblannr_gen */
+static void orc_gen_filter(orc_pencil *P, double cc, double dd, int deg, const double *coef, const double *zi,
+                           double *z, double *f0, double *f1, double *f2, double *u, double *Au, long *nmv)
+{
+    const int64_t n = P->A->n;
+    double *p0 = f0, *p1 = f1, *p2 = f2;
+    memcpy(p0, zi, sizeof(double) * n);
+    for (int64_t r = 0; r < n; r++) z[r] = coef[0] * p0[r];
+    for (int j = 1; j <= deg; j++) {
+        const double *src = (j == 1) ? p0 : p1;
+        double *dst = (j == 1) ? p1 : p2;
+        orc_solveB(P, src, u);
+        orc_matvec(P->A, u, Au);
+        (*nmv)++;
+        for (int64_t r = 0; r < n; r++) {
+            const double mf = (Au[r] - cc * src[r]) / dd;
+            dst[r] = (j == 1) ? mf : 2.0 * mf - p0[r];
+        }
+        for (int64_t r = 0; r < n; r++) z[r] += coef[j] * dst[r];
+        if (j >= 2) { double *tmp = p0; p0 = p1; p1 = p2; p2 = tmp; }
+    }
+}
+
+/* two passes of z -= BU (U^T z) (locked, nlock columns) and z -= Z (W^T z) (basis, k columns) */
+static void orc_gen_reorth(int64_t n, double *z, const double *U, const double *BU, int nlock, const double *W,
+                           const double *Z, int k)
+{
+    for (int pass = 0; pass < 2; pass++) {
+        for (int j = 0; j < nlock; j++) {
+            const double h = orc_dot(n, z, U + (size_t)j * n);
+            for (int64_t r = 0; r < n; r++) z[r] -= h * BU[(size_t)j * n + r];
+        }
+        for (int j = 0; j < k; j++) {
+            const double h = orc_dot(n, z, W + (size_t)j * n);
+            for (int64_t r = 0; r < n; r++) z[r] -= h * Z[(size_t)j * n + r];
+        }
+    }
+}
+
+/* fresh pair: w uniform(-1, 1) (stream 3, k = index*n + i), made B-orthogonal to U and W by two
+ * passes of w -= U (BU^T w) and w -= W (Z^T w), z = B w, both scaled to w^T z = 1 */
+static void orc_gen_fresh(orc_pencil *P, uint64_t seed, uint64_t index, double *w, double *z, const double *U,
+                          const double *BU, int nlock, const double *W, const double *Z, int k)
+{
+    const int64_t n = P->A->n;
+    for (int64_t i = 0; i < n; i++)
+        w[i] = 2.0 * orc_unit(orc_draw(seed, ORC_STREAM_LANCZOS, index * (uint64_t)n + (uint64_t)i)) - 1.0;
+    /* the roles of the pairs swap: B-orthogonality of w to u_j is (BU_j)^T w */
+    orc_gen_reorth(n, w, BU, U, nlock, Z, W, k);
+    orc_matvec(P->B, w, z);
+    const double s = sqrt(orc_dot(n, w, z));
+    for (int64_t i = 0; i < n; i++) { w[i] /= s; z[i] /= s; }
+}
+
+/* w = p(B) z; beta = (w^T z)^{1/2}; breakdown (returns 0) if beta <= 1e-13 ||y|| / sqrt(bmax)
+ * (||y|| / sqrt(bmax) bounds the B^{-1}-norm of the filtered vector y from below) */
+static int orc_gen_close(orc_pencil *P, double bmax, const double *y, double *z, double *w, double *beta)
+{
+    const int64_t n = P->A->n;
+    orc_solveB(P, z, w);
+    const double b = sqrt(fmax(0.0, orc_dot(n, w, z)));
+    *beta = b;
+    return b > 1e-13 * orc_nrm2(n, y) / sqrt(bmax);
+}
+
+/* Filtered thick-restart Lanczos with locking (Algorithm 2) for the pencil, in the pair basis
+ * above: the operator rho(Mhat) (orc_cheblannr_gen) applied to z-vectors, Lanczos coefficients
+ * alpha = w_i^T y, beta = (w^T z)^{1/2}, two reorthogonalisation passes against locked and basis
+ * pairs.  READINGS: the control flow of orc_cheblantr (special TR step with the arrow matrix,
+ * early restart on the sum of Ritz values >= bar, candidates largest first, lock when
+ * ||A x - lambda B x|| <= tol bmax max(|lmin|, |lmax|) with x = W s B-normalised and
+ * lambda = x^T A x, at most m/2 TR pairs (W s, Z s), fresh pairs after breakdown or a cycle
+ * without candidates, stop after two such cycles); the refinement of stalled candidates of the
+ * standard solver is not used.  stats: its, nmv, nrestart, 0. */
+int orc_cheblantr_gen(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                      const int64_t *brp, const int32_t *bci, const double *bv, double bmin, double bmax,
+                      int bdeg, const double *bcoef, double a, double b, int right_closed, double lmin,
+                      double lmax, int deg, const double *coef, double bar, int m, int maxit, int ncycle,
+                      double tol, double tau1, uint64_t seed, int cap, int *nev, double *lam, double *X,
+                      double *res, long *stats)
+{
+    orc_csr A = {n, rp, ci, v}, B = {n, brp, bci, bv};
+    double *t = malloc(sizeof(double) * 3 * n);
+    orc_pencil P = {&A, &B, 0.5 * (bmax + bmin), 0.5 * (bmax - bmin), bdeg, bcoef, t, t + n, t + 2 * n};
+    const double cc = 0.5 * (lmax + lmin), dd = 0.5 * (lmax - lmin);
+    const double scale = bmax * fmax(fabs(lmin), fabs(lmax));
+    if (m > n) m = (int)n;
+    const int capc = cap > 0 ? cap : 1;
+    double *U = calloc((size_t)n * capc, sizeof(double)), *BU = calloc((size_t)n * capc, sizeof(double));
+    double *W = calloc((size_t)n * (m + 1), sizeof(double)), *Z = calloc((size_t)n * (m + 1), sizeof(double));
+    double *T = calloc((size_t)(m + 1) * (m + 1), sizeof(double)), *Tk = malloc(sizeof(double) * (size_t)(m + 1) * (m + 1));
+    double *S = malloc(sizeof(double) * (size_t)(m + 1) * (m + 1)), *theta = malloc(sizeof(double) * (m + 1));
+    double *y = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n), *wt = malloc(sizeof(double) * n);
+    double *f0 = malloc(sizeof(double) * n), *f1 = malloc(sizeof(double) * n), *f2 = malloc(sizeof(double) * n);
+    double *u = malloc(sizeof(double) * n), *Au = malloc(sizeof(double) * n);
+    double *x = malloc(sizeof(double) * n), *xz = malloc(sizeof(double) * n), *Bx = malloc(sizeof(double) * n);
+    double *trw = malloc(sizeof(double) * (size_t)n * (m / 2 + 1)), *trz = malloc(sizeof(double) * (size_t)n * (m / 2 + 1));
+    double *trtheta = malloc(sizeof(double) * (m + 1)), *trs = malloc(sizeof(double) * (m + 1));
+    long nmv = 0;
+    int nlock = 0, l = 0, its = 0, nrestart = 0, nocand = 0, status = 0;
+    uint64_t fresh_index = 0;
+
+    orc_gen_fresh(&P, seed, fresh_index++, W, Z, U, BU, 0, NULL, NULL, 0);
+    while (its <= maxit) {
+        int k;
+        memset(T, 0, sizeof(double) * (size_t)(m + 1) * (m + 1));
+        if (l > 0) {
+            for (int j = 0; j < l; j++) {
+                AT(T, j, j, m + 1) = trtheta[j];
+                AT(T, j, l, m + 1) = trs[j];
+                AT(T, l, j, m + 1) = trs[j];
+            }
+            const double *zl = Z + (size_t)l * n, *wl = W + (size_t)l * n;
+            orc_gen_filter(&P, cc, dd, deg, coef, zl, y, f0, f1, f2, u, Au, &nmv);
+            its++;
+            const double alpha = orc_dot(n, wl, y);
+            memcpy(z, y, sizeof(double) * n);
+            for (int j = 0; j < l; j++)
+                for (int64_t r = 0; r < n; r++) z[r] -= trs[j] * Z[(size_t)j * n + r];
+            for (int64_t r = 0; r < n; r++) z[r] -= alpha * zl[r];
+            orc_gen_reorth(n, z, U, BU, nlock, W, Z, l + 1);
+            AT(T, l, l, m + 1) = alpha;
+            double beta = 0.0;
+            double *wn = W + (size_t)(l + 1) * n, *zn = Z + (size_t)(l + 1) * n;
+            if (orc_gen_close(&P, bmax, y, z, wt, &beta)) {
+                for (int64_t r = 0; r < n; r++) { wn[r] = wt[r] / beta; zn[r] = z[r] / beta; }
+            } else {
+                orc_gen_fresh(&P, seed, fresh_index++, wn, zn, U, BU, nlock, W, Z, l + 1);
+                beta = 0.0;
+            }
+            AT(T, l, l + 1, m + 1) = beta;
+            AT(T, l + 1, l, m + 1) = beta;
+            k = l + 1;
+        } else {
+            k = 0;
+        }
+        const int lstart = k;
+        double t_old = 0.0;
+        int have_old = 0, prev_nabove = 0;
+        for (int i = k; i < m; i++) {
+            its++;
+            const double *zi = Z + (size_t)i * n, *wi = W + (size_t)i * n;
+            orc_gen_filter(&P, cc, dd, deg, coef, zi, y, f0, f1, f2, u, Au, &nmv);
+            memcpy(z, y, sizeof(double) * n);
+            if (i > 0) {
+                const double bi = AT(T, i - 1, i, m + 1);
+                for (int64_t r = 0; r < n; r++) z[r] -= bi * Z[(size_t)(i - 1) * n + r];
+            }
+            const double alpha = orc_dot(n, wi, z);
+            for (int64_t r = 0; r < n; r++) z[r] -= alpha * zi[r];
+            orc_gen_reorth(n, z, U, BU, nlock, W, Z, i + 1);
+            AT(T, i, i, m + 1) = alpha;
+            double beta = 0.0;
+            double *wn = W + (size_t)(i + 1) * n, *zn = Z + (size_t)(i + 1) * n;
+            if (orc_gen_close(&P, bmax, y, z, wt, &beta)) {
+                for (int64_t r = 0; r < n; r++) { wn[r] = wt[r] / beta; zn[r] = z[r] / beta; }
+            } else {
+                orc_gen_fresh(&P, seed, fresh_index++, wn, zn, U, BU, nlock, W, Z, i + 1);
+                beta = 0.0;
+            }
+            AT(T, i, i + 1, m + 1) = beta;
+            AT(T, i + 1, i, m + 1) = beta;
+            k = i + 1;
+            if ((k - lstart) % ncycle == 0) {
+                for (int jj = 0; jj < k; jj++)
+                    for (int ii = 0; ii < k; ii++) AT(Tk, ii, jj, k) = AT(T, ii, jj, m + 1);
+                orc_syev(k, Tk, theta, NULL);
+                double t_new = 0.0;
+                int nabove = 0;
+                for (int jj = 0; jj < k; jj++)
+                    if (theta[jj] >= bar) { t_new += theta[jj]; nabove++; }
+                if (have_old && nabove > 0 && fabs(t_new - t_old) < tau1 * fmax(1.0, fabs(t_new))) break;
+                const int min_empty = (2 * ncycle > m / 4) ? 2 * ncycle : m / 4;
+                if (have_old && nabove == 0 && prev_nabove == 0 && k - lstart >= min_empty) break;
+                t_old = t_new;
+                prev_nabove = nabove;
+                have_old = 1;
+            }
+            if (its > maxit) break;
+        }
+        nrestart++;
+        for (int jj = 0; jj < k; jj++)
+            for (int ii = 0; ii < k; ii++) AT(Tk, ii, jj, k) = AT(T, ii, jj, m + 1);
+        orc_syev(k, Tk, theta, S);
+        const double betak = AT(T, k - 1, k, m + 1);
+        int ncand = 0, ntr = 0;
+        for (int jj = k - 1; jj >= 0; jj--) {
+            if (theta[jj] < bar) break;
+            const double *s = S + (size_t)jj * k;
+            for (int64_t r = 0; r < n; r++) {
+                double aw = 0.0, az = 0.0;
+                for (int p = 0; p < k; p++) {
+                    aw += W[(size_t)p * n + r] * s[p];
+                    az += Z[(size_t)p * n + r] * s[p];
+                }
+                x[r] = aw;
+                xz[r] = az;
+            }
+            orc_matvec(&B, x, Bx);
+            const double nb = sqrt(orc_dot(n, x, Bx));
+            for (int64_t r = 0; r < n; r++) { u[r] = x[r] / nb; Bx[r] /= nb; }
+            orc_matvec(&A, u, Au);
+            const double lamj = orc_dot(n, u, Au);
+            const int inside = (lamj >= a) && (right_closed ? (lamj <= b) : (lamj < b));
+            if (!inside) continue;
+            ncand++;
+            for (int64_t r = 0; r < n; r++) Au[r] -= lamj * Bx[r];
+            const double rj = orc_nrm2(n, Au) / scale;
+            if (rj <= tol) {
+                if (nlock >= cap) { status = -5; goto done; }
+                memcpy(U + (size_t)nlock * n, u, sizeof(double) * n);
+                memcpy(BU + (size_t)nlock * n, Bx, sizeof(double) * n);
+                lam[nlock] = lamj;
+                res[nlock] = rj;
+                nlock++;
+            } else if (ntr < m / 2) {
+                memcpy(trw + (size_t)ntr * n, x, sizeof(double) * n);
+                memcpy(trz + (size_t)ntr * n, xz, sizeof(double) * n);
+                trtheta[ntr] = theta[jj];
+                trs[ntr] = betak * s[k - 1];
+                ntr++;
+            }
+        }
+        if (ncand == 0) nocand++; else nocand = 0;
+        if (nocand >= 2) break;
+        if (its > maxit) { status = -4; break; }
+        if (ncand == 0) {
+            l = 0;
+            orc_gen_fresh(&P, seed, fresh_index++, W, Z, U, BU, nlock, NULL, NULL, 0);
+        } else {
+            if (ntr != k) {
+                memcpy(W + (size_t)ntr * n, W + (size_t)k * n, sizeof(double) * n);
+                memcpy(Z + (size_t)ntr * n, Z + (size_t)k * n, sizeof(double) * n);
+            }
+            memcpy(W, trw, sizeof(double) * (size_t)n * ntr);
+            memcpy(Z, trz, sizeof(double) * (size_t)n * ntr);
+            l = ntr;
+            if (l == 0) {
+                /* continue from z_{k+1}, deflated against the new locked pairs */
+                orc_gen_reorth(n, Z, U, BU, nlock, NULL, NULL, 0);
+                orc_solveB(&P, Z, W);
+                const double s = sqrt(orc_dot(n, W, Z));
+                for (int64_t r = 0; r < n; r++) { W[r] /= s; Z[r] /= s; }
+            }
+        }
+    }
+done:
+    for (int i = 0; i < nlock; i++) {
+        int best = i;
+        for (int j = i + 1; j < nlock; j++)
+            if (lam[j] < lam[best]) best = j;
+        if (best != i) {
+            double tt = lam[i]; lam[i] = lam[best]; lam[best] = tt;
+            tt = res[i]; res[i] = res[best]; res[best] = tt;
+            for (int64_t r = 0; r < n; r++) {
+                tt = U[(size_t)i * n + r];
+                U[(size_t)i * n + r] = U[(size_t)best * n + r];
+                U[(size_t)best * n + r] = tt;
+            }
+        }
+    }
+    if (X) memcpy(X, U, sizeof(double) * (size_t)n * nlock);
+    *nev = nlock;
+    if (stats) { stats[0] = its; stats[1] = nmv; stats[2] = nrestart; stats[3] = 0; }
+    free(t); free(U); free(BU); free(W); free(Z); free(T); free(Tk); free(S); free(theta); free(y); free(z);
+    free(wt); free(f0); free(f1); free(f2); free(u); free(Au); free(x); free(xz); free(Bx); free(trw); free(trz);
+    free(trtheta); free(trs);
+    return status;
+}

@@ -637,3 +637,49 @@ def test_kpm_gen_statistics_against_closed_form_trace(oracle_mod):
         tk = np.cos(k * np.arccos(lh))
         sig = np.sqrt(2.0 * np.sum(tk * tk) / nv)
         assert abs(mu[k] - tk.sum()) <= 6 * sig + 1e-9
+
+
+@pytest.mark.parametrize("a,b,m", [(2.0, 3.0, 40), (40.0, 42.0, 30)])
+def test_cheblantr_gen_restarts_against_closed_form(oracle_mod, a, b, m):
+    # thick restart with locking on the pencil, with a basis small enough to need several cycles:
+    # exact count and eigenvalues, residuals, B-orthonormal eigenvectors
+    nx = 20
+    A, B = I.laplacian_2d(nx), I.mass_matrix_2d(nx)
+    lam = pencil_eigs(nx)
+    lp, _ = _pencil_lsp(oracle_mod, A, B)
+    lo, hi = oracle_mod.bounds_gen(A, B, lp, 80, 0)
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    ex = lam[(lam >= a) & (lam <= b)]
+    r = oracle_mod.cheblantr_gen(A, B, lp, a, b, pol, m=m)
+    assert r["status"] == 0 and r["nev"] == len(ex) and r["nrestart"] >= 3
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.maximum(1.0, ex))
+    X, Ad, Bd = r["Y"], A.to_dense(), B.to_dense()
+    assert np.max(np.linalg.norm(Ad @ X - (Bd @ X) * r["lam"], axis=0)) <= 1e-8 * lp["bmax"] * hi
+    assert np.max(np.abs(X.T @ Bd @ X - np.eye(len(ex)))) <= 1e-10
+
+
+def test_cheblantr_gen_matches_dense_generalized_eigensolver(oracle_mod):
+    # a pencil whose matrices do not commute: Anderson A and B = 0.4 I + 0.05 L (3-D Laplacian),
+    # against scipy's dense generalized eigensolver
+    import scipy.linalg as sl
+    nx = 6
+    A = I.anderson_3d(nx, 3.0, 0)
+    L = I.laplacian_3d(nx)
+    n = A.n
+    Bd = 0.4 * np.eye(n) + 0.05 * L.to_dense()
+    rows, cols = np.nonzero(Bd)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    B = I.CSR(n, rp, cols.astype(np.int32), Bd[rows, cols])
+    w = sl.eigh(A.to_dense(), Bd, eigvals_only=True)
+    lp = oracle_mod.lspol(0.39, 1.01, 1e-13)
+    lo, hi = oracle_mod.bounds_gen(A, B, lp, 80, 0)
+    assert lo <= w[0] and hi >= w[-1] - 1e-9 * abs(w[-1])
+    for a, b in [(2.0, 4.0), (8.0, 9.0)]:
+        ex = w[(w >= a) & (w <= b)]
+        pol = oracle_mod.filter_build(a, b, lo, hi)
+        r = oracle_mod.cheblantr_gen(A, B, lp, a, b, pol, m=max(2 * len(ex), 40))
+        assert r["status"] == 0 and r["nev"] == len(ex)
+        assert np.max(np.abs(r["lam"] - ex)) <= 1e-9 * max(1.0, np.abs(ex).max())
+        rn = oracle_mod.cheblannr_gen(A, B, lp, a, b, pol, m=max(6 * len(ex), 200))
+        assert rn["nev"] == len(ex) and np.max(np.abs(rn["lam"] - ex)) <= 1e-9 * max(1.0, np.abs(ex).max())
