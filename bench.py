@@ -677,7 +677,7 @@ def gen_step_bytes(n: int, nnz: int, mode: int, separate_u: bool) -> float:
 
 def run_gen_2d(args):
     """Generalized problem A x = lambda B x with B^{-1} by the lsPol polynomial, on the pencil
-    (2-D 5-point Laplacian, 2-D linear-element mass matrix M (x) M).  Two legs:
+    (2-D 5-point Laplacian, 2-D linear-element mass matrix M (x) M).  Four legs:
     (1) the solve y = p(B) x on the 1000^2 mass matrix (n = 1e6, 9e6 nonzeros; matrix and
         vectors above L2 size): per-launch time of k_gen_step from CUDA events, its roofline;
     (2) the pencil's KPM density (degree 120, 20 probes, starting vectors by q(B) ~ B^{-1/2}) on
@@ -685,7 +685,9 @@ def run_gen_2d(args):
     (3) filtered non-restart Lanczos (ChebLanNr with B-inner products) on the 200^2 pencil over
         a slice cut between distinct closed-form eigenvalues: eigenpairs/s with the filter's
         CUDA graph and with direct launches (bitwise-equal results), counts checked against the
-        closed form.  B's bounds come from the library's Lanczos bounds on B."""
+        closed form;
+    (4) thick-restart Lanczos with locking for the pencil on the same slice (basis of 100 pairs).
+    B's bounds come from the library's Lanczos bounds on B."""
     import torch
 
     from paper_1802_05215_gb300 import native
@@ -775,6 +777,18 @@ def run_gen_2d(args):
                 "gen_step_ms": ms2, "max_res": float(r["res"].max()) if r["nev"] else 0.0,
                 "lam": r["lam"]}
         ctx.set_graphs(True)
+        # thick restart with locking on the same slice, a basis of 100 pairs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rt = ctx.chebLanTr_gen(a, b, f, m=100, cap=cap, Y=Y, tol=TOL, seed=SEED)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = rt["stats"]
+        out["thick_restart"] = {"m": 100, "eigenpairs": rt["nev"], "seconds": dt, "eigenpairs_per_s": rt["nev"] / dt,
+                                "niter": st["niter"], "nmv": st["nmv"], "restarts": st["nrestart"],
+                                "max_res": float(rt["res"].max()) if rt["nev"] else 0.0,
+                                "max_diff_vs_nonrestart": float(np.max(np.abs(rt["lam"] - runs["graphs"]["lam"])))
+                                if rt["nev"] == runs["graphs"]["eigenpairs"] else None}
     same = bool(np.array_equal(runs["graphs"]["lam"], runs["direct"]["lam"]))
     for v in runs.values():
         v.pop("lam")

@@ -379,6 +379,20 @@ int evsl_chebLanNr_gen(evsl_ctx *ctx, double a, double b, const evsl_polfilt *po
                        const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
                        double *res, evsl_stats *stats);
 
+/* Filtered thick-restart Lanczos with locking for the pencil on [a, b] (Algorithm 2 in the
+ * B-inner product; Sec. 2.5 describes the generalized TR and locking scheme, with deflation
+ * (I - B U U^T) A x = lambda B x for the B-orthonormal locked vectors U).  Vectors are kept in
+ * pairs (w, z = B w); the operator is evsl_chebLanNr_gen's; two reorthogonalisation passes against
+ * the locked pairs and the basis.  Restarts keep at most opts->m / 2 unconverged Ritz pairs
+ * (thick restart with the arrow matrix); early restart, candidates and locking as evsl_chebLanTr
+ * with the residual of evsl_chebLanNr_gen; fresh start vectors after a breakdown or a cycle
+ * without candidates, stop after two such cycles; opts->maxit bounds the Lanczos steps (0 = 20 m).
+ * No refinement of stalled candidates.  Outputs, stats (niter, nmv, nrestart, t_total) and errors as
+ * evsl_chebLanNr_gen. */
+int evsl_chebLanTr_gen(evsl_ctx *ctx, double a, double b, const evsl_polfilt *pol,
+                       const evsl_lan_opts *opts, int cap, int *nev, double *lam, double *Y,
+                       double *res, evsl_stats *stats);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Instrumentation (no counterpart in the paper).
  * evsl_launch_count: kernels launched by this context since its creation.

@@ -504,6 +504,19 @@ int evsl_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
     return drv_chebLanNr_gen(c, a, b, pol, opts, cap, nev, lam, Y, res, stats);
 }
 
+int evsl_chebLanTr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *opts,
+                       int cap, int *nev, double *lam, double *Y, double *res, evsl_stats *stats)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!pol || !pol->coef || pol->deg < 0 || !opts || !nev || !lam || !res || cap < 1 || !(b > a) || opts->m < 2 ||
+        !(pol->lmax > pol->lmin))
+        return ctx_fail(c, EVSL_ERR_ARG, "chebLanTr_gen: bad arguments");
+    if (opts->prec != EVSL_FP64) return ctx_fail(c, EVSL_ERR_ARG, "chebLanTr_gen: only the FP64 filter is supported");
+    cudaSetDevice(c->device);
+    return drv_chebLanTr_gen(c, a, b, pol, opts, cap, nev, lam, Y, res, stats);
+}
+
 int evsl_set_graphs(evsl_ctx *c, int enable)
 {
     if (!c) return EVSL_ERR_ARG;

@@ -106,7 +106,7 @@ int d2h(evsl_ctx *c, void *dst, const void *src, size_t bytes)
 }
 
 // device scalars: alpha, a scratch norm, beta^2, (x, Bx), lambda, then the projections h
-enum { S_ALPHA = 0, S_TMP = 1, S_BETA2 = 2, S_NB2 = 3, S_LAM = 4, S_RES2 = 5, S_H = 8 };
+enum { S_ALPHA = 0, S_TMP = 1, S_BETA2 = 2, S_NB2 = 3, S_LAM = 4, S_RES2 = 5, S_YN2 = 6, S_H = 8 };
 
 // n-vectors of the generalized drivers (one workspace, carved); zs: fixed input of the
 // filter graphs
@@ -272,8 +272,9 @@ int lanab_step(evsl_ctx *c, int i, double *W, double *Z, double *z, double beta_
     return EVSL_OK;
 }
 
-// bases W, Z (n x (k+1) each) and the device scalars
-int get_basis(evsl_ctx *c, int k, int extra_cols, double **W, double **Z, double **X, double **sc)
+// bases W, Z (n x (k+1) each), extra_cols more columns at *X, and the device scalars with room
+// for hcap projection coefficients
+int get_basis(evsl_ctx *c, int k, int extra_cols, double **W, double **Z, double **X, double **sc, int hcap)
 {
     const int64_t n = c->A.n;
     int st = EVSL_OK;
@@ -282,7 +283,7 @@ int get_basis(evsl_ctx *c, int k, int extra_cols, double **W, double **Z, double
     *W = p;
     *Z = p + (int64_t)(k + 1) * n;
     if (X) *X = p + 2 * (int64_t)(k + 1) * n;
-    *sc = (double *)ctx_ws(c, WS_GEN_SCAL, sizeof(double) * (S_H + (size_t)k + 8), &st);
+    *sc = (double *)ctx_ws(c, WS_GEN_SCAL, sizeof(double) * (S_H + (size_t)hcap + 8), &st);
     return st;
 }
 
@@ -400,7 +401,7 @@ int drv_bounds_gen(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *
     const int64_t n = c->A.n;
     if (steps > n) steps = (int)n;
     double *W, *Z, *sc;
-    EVSL_TRY(get_basis(c, steps, 0, &W, &Z, nullptr, &sc));
+    EVSL_TRY(get_basis(c, steps, 0, &W, &Z, nullptr, &sc, steps + 1));
     Vecs v;
     EVSL_TRY(get_vecs(c, v));
     EVSL_TRY(lanab_start(c, seed, W, Z, sc));
@@ -454,7 +455,7 @@ int drv_chebLanNr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, 
     const double bar = pol->bar;
     const double scale = c->b_max * std::max(std::fabs(pol->lmin), std::fabs(pol->lmax));
     double *W, *Z, *Xc, *sc;
-    EVSL_TRY(get_basis(c, m, cap, &W, &Z, &Xc, &sc));
+    EVSL_TRY(get_basis(c, m, cap, &W, &Z, &Xc, &sc, m + 1));
     Vecs v;
     EVSL_TRY(get_vecs(c, v));
     EVSL_TRY(lanab_start(c, o->seed, W, Z, sc));
@@ -623,4 +624,307 @@ int drv_kpm_gen(evsl_ctx *c, int M, int nvec, uint64_t seed, double lmin, double
         mu[k] = sum / nvec;
     }
     return EVSL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Thick-restart filtered Lanczos with locking for the pencil (Algorithm 2 in the B-inner
+// product).  Vectors come in pairs (w, z = B w) with W^T Z = I; locked eigenvectors U are
+// B-orthonormal and BU = B U is kept beside them, so deflating a z-vector is z -= BU (U^T z)
+// (the paper's (I - B U U^T) scheme, Sec. 2.5).
+namespace {
+
+struct TrGen {
+    evsl_ctx *c;
+    int64_t n;
+    double *W, *Z, *U, *BU, *trw, *trz, *sc;
+    Vecs v;
+    uint64_t seed, fresh_index = 0;
+    int nlock = 0;
+
+    // one classical Gram-Schmidt pass of x against [P1 (k1 columns), P2 (k2)] with update
+    // columns [Q1, Q2]: x -= [Q1 Q2] ([P1 P2]^T x)
+    int pass(double *x, const double *P1, const double *Q1, int k1, const double *P2, const double *Q2, int k2)
+    {
+        if (k1 + k2 == 0) return EVSL_OK;
+        EVSL_TRY(gemv_t2(c, n, k1 ? P1 : P2, k1 ? k1 : k2, k1 ? P2 : nullptr, k1 ? k2 : 0, x, sc + S_H));
+        return gemv_n2(c, n, k1 ? Q1 : Q2, k1 ? k1 : k2, k1 ? Q2 : nullptr, k1 ? k2 : 0, sc + S_H, x, sc + S_TMP);
+    }
+
+    // two passes of z -= BU (U^T z) and z -= Z (W^T z) over the first k basis pairs
+    int reorth(double *z, int k)
+    {
+        for (int p = 0; p < 2; p++) EVSL_TRY(pass(z, U, BU, nlock, W, Z, k));
+        return EVSL_OK;
+    }
+
+    // fresh pair into (w, z): w uniform(-1, 1) (Lanczos stream, next index), made B-orthogonal to
+    // U and the first k basis vectors (w -= U (BU^T w), w -= W (Z^T w), twice), z = B w, w^T z = 1
+    int fresh(double *w, double *z, int k)
+    {
+        EVSL_TRY(fill_uniform_f64(c, n, seed, SM_STREAM_LANCZOS, fresh_index++, w));
+        for (int p = 0; p < 2; p++) EVSL_TRY(pass(w, BU, U, nlock, Z, W, k));
+        EVSL_TRY(gen_step<2>(c, c->B, w, nullptr, nullptr, z, nullptr, 0.0, 0.0, 0.0, 0.0));
+        EVSL_TRY(coldot(c, n, 1, w, n, z, n, sc + S_NB2));
+        double s2 = 0.0;
+        EVSL_TRY(d2h(c, &s2, sc + S_NB2, sizeof(double)));
+        if (!(s2 > 0.0)) return ctx_fail(c, EVSL_ERR_ARG, "chebLanTr_gen: (w, B w) = %g; B is not positive definite", s2);
+        const double inv = 1.0 / std::sqrt(s2);
+        EVSL_TRY(scale_vec(c, n, w, inv, nullptr));
+        return scale_vec(c, n, z, inv, nullptr);
+    }
+
+    // close a step on z (= v.z, reorthogonalised): w = p(B) z, beta = (w^T z)^{1/2}; the next pair
+    // is (w, z) / beta, or a fresh pair after a breakdown (beta <= 1e-13 ||y|| / sqrt(bmax), ||y||^2
+    // in sc[S_YN2]); returns beta (0 after a breakdown) and alpha from sc[S_ALPHA]
+    int close(int next, double *alpha, double *beta)
+    {
+        EVSL_TRY(solve_b(c, v.z, v.wt, v.t1, v.t2));
+        EVSL_TRY(coldot(c, n, 1, v.wt, n, v.z, n, sc + S_BETA2));
+        double hs[S_YN2 + 1];
+        EVSL_TRY(d2h(c, hs, sc, sizeof(hs)));
+        *alpha = hs[S_ALPHA];
+        const double b = std::sqrt(std::max(0.0, hs[S_BETA2]));
+        double *wn = W + (int64_t)next * n, *zn = Z + (int64_t)next * n;
+        if (b > 1e-13 * std::sqrt(std::max(0.0, hs[S_YN2])) / std::sqrt(c->b_max)) {
+            EVSL_TRY(scale_vec(c, n, v.wt, 1.0 / b, wn));
+            EVSL_TRY(scale_vec(c, n, v.z, 1.0 / b, zn));
+            *beta = b;
+        } else {
+            EVSL_TRY(fresh(wn, zn, next));
+            *beta = 0.0;
+        }
+        return EVSL_OK;
+    }
+};
+
+}  // namespace
+
+// Filtered thick-restart Lanczos with locking for A x = lambda B x.  The control flow of the
+// standard solver's Algorithm 2 (special TR step with the arrow matrix, early restart on the sum
+// of Ritz values >= bar every ncycle steps, candidates largest first, at most m/2 TR pairs
+// (W s, Z s), fresh pairs after breakdown or a cycle without candidates, stop after two such
+// cycles); locking when ||A x - lambda B x|| <= tol bmax max(|lmin|, |lmax|) with x = W s
+// B-normalised and lambda = x^T A x.  No refinement of stalled candidates.  FP64.
+int drv_chebLanTr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *o, int cap,
+                      int *nev, double *lam, double *Y, double *res, evsl_stats *stats)
+{
+    EVSL_TRY(check_pencil(c, "chebLanTr_gen"));
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t n = c->A.n;
+    int m = o->m;
+    if (m > n) m = (int)n;
+    const int maxit = o->maxit > 0 ? o->maxit : 20 * m;
+    const int ncycle = o->ncycle > 0 ? o->ncycle : 10;
+    const int trcap = m / 2 + 1;
+    const double bar = pol->bar;
+    const double scale = c->b_max * std::max(std::fabs(pol->lmin), std::fabs(pol->lmax));
+    TrGen g;
+    g.c = c;
+    g.n = n;
+    g.seed = o->seed;
+    double *X = nullptr;
+    EVSL_TRY(get_basis(c, m, 2 * cap + 2 * trcap, &g.W, &g.Z, &X, &g.sc, cap + m + 2));
+    g.U = X;
+    g.BU = X + (int64_t)cap * n;
+    g.trw = X + 2 * (int64_t)cap * n;
+    g.trz = g.trw + (int64_t)trcap * n;
+    EVSL_TRY(get_vecs(c, g.v));
+    const Vecs &v = g.v;
+    double *W = g.W, *Z = g.Z, *sc = g.sc;
+    const int ldt = m + 1;
+    std::vector<double> T((size_t)ldt * ldt), w, trtheta(trcap), trs(trcap), lam_c(cap), res_c(cap);
+    int64_t nmv = 0, nrestart = 0;
+    int its = 0, l = 0, nocand = 0, status = EVSL_OK;
+
+    EVSL_TRY(g.fresh(W, Z, 0));
+    while (its <= maxit) {
+        int k;
+        std::fill(T.begin(), T.end(), 0.0);
+        if (l > 0) {
+            for (int j = 0; j < l; j++) {
+                T[(size_t)j * ldt + j] = trtheta[j];
+                T[(size_t)l * ldt + j] = trs[j];
+                T[(size_t)j * ldt + l] = trs[j];
+            }
+            const double *zl = Z + (int64_t)l * n, *wl = W + (int64_t)l * n;
+            EVSL_TRY(filter_gen_run(c, pol, zl, v, &nmv));
+            its++;
+            EVSL_TRY(coldot(c, n, 1, v.z, n, v.z, n, sc + S_YN2));
+            EVSL_TRY(coldot(c, n, 1, wl, n, v.z, n, sc + S_ALPHA));     // alpha = w_l^T y
+            cudaError_t e = cudaMemcpyAsync(sc + S_H, trs.data(), sizeof(double) * l, cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) return ctx_cuda(c, e, "chebLanTr_gen arrow upload");
+            EVSL_TRY(gemv_n2(c, n, Z, l, nullptr, 0, sc + S_H, v.z, sc + S_TMP));   // z -= sum_j s_j z_j
+            EVSL_TRY(lan_sub_alpha(c, n, v.z, zl, sc + S_ALPHA, sc + S_TMP));
+            EVSL_TRY(g.reorth(v.z, l + 1));
+            double alpha = 0.0, beta = 0.0;
+            EVSL_TRY(g.close(l + 1, &alpha, &beta));
+            T[(size_t)l * ldt + l] = alpha;
+            T[(size_t)(l + 1) * ldt + l] = beta;
+            T[(size_t)l * ldt + l + 1] = beta;
+            k = l + 1;
+        } else {
+            k = 0;
+        }
+        const int lstart = k;
+        double t_old = 0.0;
+        bool have_old = false;
+        int prev_nabove = 0;
+        for (int i = k; i < m; i++) {
+            its++;
+            const double *zi = Z + (int64_t)i * n, *wi = W + (int64_t)i * n;
+            EVSL_TRY(filter_gen_run(c, pol, zi, v, &nmv));
+            EVSL_TRY(coldot(c, n, 1, v.z, n, v.z, n, sc + S_YN2));
+            const double bi = i > 0 ? T[(size_t)i * ldt + i - 1] : 0.0;
+            EVSL_TRY(lan_three_term(c, n, v.z, i > 0 ? Z + (int64_t)(i - 1) * n : nullptr, bi, wi, v.z, sc + S_ALPHA));
+            EVSL_TRY(lan_sub_alpha(c, n, v.z, zi, sc + S_ALPHA, sc + S_TMP));
+            EVSL_TRY(g.reorth(v.z, i + 1));
+            double alpha = 0.0, beta = 0.0;
+            EVSL_TRY(g.close(i + 1, &alpha, &beta));
+            T[(size_t)i * ldt + i] = alpha;
+            T[(size_t)(i + 1) * ldt + i] = beta;
+            T[(size_t)i * ldt + i + 1] = beta;
+            k = i + 1;
+            if ((k - lstart) % ncycle == 0) {
+                double *V = nullptr;
+                int ldv = 0;
+                EVSL_TRY(tri_eig(c, k, T, ldt, w, &V, &ldv));
+                double t_new = 0.0;
+                int nabove = 0;
+                for (double th : w)
+                    if (th >= bar) {
+                        t_new += th;
+                        nabove++;
+                    }
+                if (have_old && nabove > 0 && std::fabs(t_new - t_old) < o->tau1 * std::max(1.0, std::fabs(t_new))) break;
+                const int min_empty = std::max(2 * ncycle, m / 4);
+                if (have_old && nabove == 0 && prev_nabove == 0 && k - lstart >= min_empty) break;
+                t_old = t_new;
+                prev_nabove = nabove;
+                have_old = true;
+            }
+            if (its > maxit) break;
+        }
+        // restart: Ritz pairs of T_k
+        nrestart++;
+        double *V = nullptr;
+        int ldv = 0;
+        EVSL_TRY(tri_eig(c, k, T, ldt, w, &V, &ldv));
+        const double betak = T[(size_t)(k - 1) * ldt + k];
+        std::vector<int> order(k);
+        for (int j = 0; j < k; j++) order[j] = j;
+        std::sort(order.begin(), order.end(), [&](int p, int q) { return w[p] > w[q]; });
+        int ncand = 0, ntr = 0;
+        for (int jj : order) {
+            if (w[jj] < bar) break;
+            const double *s = V + (int64_t)jj * ldv;
+            EVSL_TRY(gemm_nn(c, n, 1, k, W, n, s, ldv, v.x, n));     // x = W s
+            EVSL_TRY(gemm_nn(c, n, 1, k, Z, n, s, ldv, v.f1, n));    // B x = Z s (the z-side of the pair)
+            EVSL_TRY(gen_step<2>(c, c->B, v.x, nullptr, nullptr, v.bx, nullptr, 0.0, 0.0, 0.0, 0.0));
+            EVSL_TRY(coldot(c, n, 1, v.x, n, v.bx, n, sc + S_NB2));
+            double sh[2];  // (x, B x), s_k (last component of the Ritz vector)
+            EVSL_TRY(d2h(c, sh, sc + S_NB2, sizeof(double)));
+            EVSL_TRY(d2h(c, sh + 1, s + (k - 1), sizeof(double)));
+            if (!(sh[0] > 0.0)) return ctx_fail(c, EVSL_ERR_ARG, "chebLanTr_gen: (x, B x) = %g; B is not positive definite", sh[0]);
+            const double inv = 1.0 / std::sqrt(sh[0]);
+            EVSL_TRY(scale_vec(c, n, v.x, inv, v.f2));               // u = x / ||x||_B
+            EVSL_TRY(scale_vec(c, n, v.bx, inv, nullptr));
+            EVSL_TRY(gen_step<2>(c, c->A, v.f2, nullptr, nullptr, v.ax, nullptr, 0.0, 0.0, 0.0, 0.0));
+            EVSL_TRY(coldot(c, n, 1, v.f2, n, v.ax, n, sc + S_LAM));
+            EVSL_TRY(colres2(c, n, 1, v.ax, v.bx, n, sc + S_LAM, sc + S_RES2));
+            double lr[2];
+            EVSL_TRY(d2h(c, lr, sc + S_LAM, sizeof(lr)));
+            const double lamj = lr[0];
+            const bool inside = lamj >= a && (o->right_closed ? lamj <= b : lamj < b);
+            if (!inside) continue;
+            ncand++;
+            const double rj = std::sqrt(std::max(0.0, lr[1])) / scale;
+            if (rj <= o->tol) {
+                if (g.nlock >= cap) {
+                    status = EVSL_ERR_CAPACITY;
+                    break;
+                }
+                cudaError_t e = cudaMemcpyAsync(g.U + (int64_t)g.nlock * n, v.f2, sizeof(double) * n,
+                                                cudaMemcpyDeviceToDevice, c->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(g.BU + (int64_t)g.nlock * n, v.bx, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                        c->stream);
+                if (e != cudaSuccess) return ctx_cuda(c, e, "chebLanTr_gen lock");
+                lam_c[g.nlock] = lamj;
+                res_c[g.nlock] = rj;
+                g.nlock++;
+            } else if (ntr < m / 2) {
+                cudaError_t e = cudaMemcpyAsync(g.trw + (int64_t)ntr * n, v.x, sizeof(double) * n,
+                                                cudaMemcpyDeviceToDevice, c->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(g.trz + (int64_t)ntr * n, v.f1, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                        c->stream);
+                if (e != cudaSuccess) return ctx_cuda(c, e, "chebLanTr_gen TR copy");
+                trtheta[ntr] = w[jj];
+                trs[ntr] = betak * sh[1];
+                ntr++;
+            }
+        }
+        if (status == EVSL_ERR_CAPACITY) break;
+        nocand = (ncand == 0) ? nocand + 1 : 0;
+        if (nocand >= 2) break;
+        if (its > maxit) {
+            status = EVSL_ERR_NOCONV;
+            break;
+        }
+        if (ncand == 0) {
+            l = 0;
+            EVSL_TRY(g.fresh(W, Z, 0));
+        } else {
+            cudaError_t e = cudaSuccess;
+            if (ntr != k) {
+                e = cudaMemcpyAsync(W + (int64_t)ntr * n, W + (int64_t)k * n, sizeof(double) * n,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(Z + (int64_t)ntr * n, Z + (int64_t)k * n, sizeof(double) * n,
+                                        cudaMemcpyDeviceToDevice, c->stream);
+            }
+            if (e == cudaSuccess && ntr > 0)
+                e = cudaMemcpyAsync(W, g.trw, sizeof(double) * n * ntr, cudaMemcpyDeviceToDevice, c->stream);
+            if (e == cudaSuccess && ntr > 0)
+                e = cudaMemcpyAsync(Z, g.trz, sizeof(double) * n * ntr, cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) return ctx_cuda(c, e, "chebLanTr_gen restart copy");
+            l = ntr;
+            if (l == 0) {
+                // continue from z_{k+1}, deflated against the new locked pairs
+                for (int p = 0; p < 2; p++) EVSL_TRY(g.pass(Z, g.U, g.BU, g.nlock, nullptr, nullptr, 0));
+                EVSL_TRY(solve_b(c, Z, W, v.t1, v.t2));
+                EVSL_TRY(coldot(c, n, 1, W, n, Z, n, sc + S_NB2));
+                double s2 = 0.0;
+                EVSL_TRY(d2h(c, &s2, sc + S_NB2, sizeof(double)));
+                if (!(s2 > 0.0)) return ctx_fail(c, EVSL_ERR_ARG, "chebLanTr_gen: (w, z) = %g after deflation", s2);
+                const double inv = 1.0 / std::sqrt(s2);
+                EVSL_TRY(scale_vec(c, n, W, inv, nullptr));
+                EVSL_TRY(scale_vec(c, n, Z, inv, nullptr));
+            }
+        }
+    }
+    const int found = g.nlock;
+    std::vector<int> perm(found);
+    for (int i = 0; i < found; i++) perm[i] = i;
+    std::sort(perm.begin(), perm.end(), [&](int p, int q) { return lam_c[p] < lam_c[q]; });
+    for (int i = 0; i < found; i++) {
+        lam[i] = lam_c[perm[i]];
+        res[i] = res_c[perm[i]];
+        if (Y) {
+            cudaError_t e = cudaMemcpyAsync(Y + (int64_t)i * n, g.U + (int64_t)perm[i] * n, sizeof(double) * n,
+                                            cudaMemcpyDefault, c->stream);
+            if (e != cudaSuccess) return ctx_cuda(c, e, "chebLanTr_gen eigenvector readback");
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "chebLanTr_gen outputs");
+    *nev = found;
+    if (stats) {
+        *stats = evsl_stats();
+        stats->niter = its;
+        stats->nmv = nmv;
+        stats->nrestart = nrestart;
+        stats->t_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
 }

@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
         "evsl_polyB_apply": (i32, [P, P, P]),
         "evsl_bounds_gen": (i32, [P, i32, u64, P, P]),
         "evsl_chebLanNr_gen": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
+        "evsl_chebLanTr_gen": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_launch_count": (i64, [P]),
         "evsl_set_graphs": (i32, [P, i32]),
         "evsl_profile": (i32, [P, i32]),
@@ -295,6 +296,26 @@ class Context:
                                          C.byref(nev), _addr(lam), _addr(Y), _addr(res), C.byref(stats))
         if st != EVSL_OK and not (allow_partial and st in (-4, -5)):
             self._check(st, "chebLanNr_gen")
+        k = nev.value
+        return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
+                    stats=stats.as_dict())
+
+    def chebLanTr_gen(self, a, b, filt: Filter, m=100, maxit=0, ncycle=10, tol=1e-8, tau1=1e-10, seed=0,
+                      right_closed=True, cap=None, Y=None, allow_partial=False):
+        """Filtered thick-restart Lanczos with locking for A x = lambda B x on [a, b]; outputs as
+        chebLanTr (B-orthonormal eigenvectors)."""
+        cap = cap or (m + 64)
+        opts = LanOpts(m, maxit, ncycle, tol, tau1, seed, FP64, int(right_closed))
+        lam = np.zeros(cap)
+        res = np.zeros(cap)
+        if Y is None:
+            Y = np.zeros((cap, self.n))
+        nev = C.c_int()
+        stats = Stats()
+        st = self.lib.evsl_chebLanTr_gen(self.h, a, b, C.byref(filt.pol), C.byref(opts), cap,
+                                         C.byref(nev), _addr(lam), _addr(Y), _addr(res), C.byref(stats))
+        if st != EVSL_OK and not (allow_partial and st in (-4, -5)):
+            self._check(st, "chebLanTr_gen")
         k = nev.value
         return dict(status=st, nev=k, lam=lam[:k].copy(), res=res[:k].copy(), Y=Y,
                     stats=stats.as_dict())

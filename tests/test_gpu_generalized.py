@@ -170,3 +170,54 @@ def test_kpm_gen_scaled_identity_equals_standard_kpm(ctx, nat, oracle_mod):
     mg = ctx.kpm_dos_gen(40, 3, 7, lo / 2, hi / 2)
     ms = ctx.kpm_dos(40, 3, 7, lo, hi)
     assert np.max(np.abs(mg - ms)) <= 1e-12 * n
+
+
+@pytest.mark.parametrize("a,b,m", [(2.0, 3.0, 40), (10.0, 11.0, 40), (40.0, 42.0, 30)])
+def test_cheblantr_gen_restarts_match_closed_form_and_oracle(ctx, nat, oracle_mod, a, b, m):
+    # thick restart with locking for the pencil, with bases small enough to need several
+    # cycles: exact count and eigenvalues, residuals, B-orthonormality; the oracle's run finds the
+    # same eigenvalues
+    nx = 20
+    A, B, lp = _pencil(ctx, oracle_mod, nx)
+    lam = pencil_eigs(nx)
+    lo, hi = oracle_mod.bounds_gen(A, B, lp, 80, 0)
+    f = nat.cheb_filter_build(a, b, lo, hi)
+    ex = lam[(lam >= a) & (lam <= b)]
+    r = ctx.chebLanTr_gen(a, b, f, m=m)
+    assert r["status"] == 0 and r["nev"] == len(ex) and r["stats"]["nrestart"] >= 3
+    assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.maximum(1.0, ex))
+    X, Ad, Bd = r["Y"][:r["nev"]].T, A.to_dense(), B.to_dense()
+    assert np.max(np.linalg.norm(Ad @ X - (Bd @ X) * r["lam"], axis=0)) <= 1e-8 * lp["bmax"] * hi
+    assert np.max(np.abs(X.T @ Bd @ X - np.eye(r["nev"]))) <= 1e-10
+    assert r["stats"]["nmv"] == f.deg * r["stats"]["niter"]
+    ro = oracle_mod.cheblantr_gen(A, B, lp, a, b, oracle_mod.filter_build(a, b, lo, hi), m=m)
+    assert ro["status"] == 0 and ro["nev"] == r["nev"]
+    assert np.all(np.abs(ro["lam"] - r["lam"]) <= 1e-9 * np.maximum(1.0, ex))
+
+
+def test_cheblantr_gen_noncommuting_pencil_matches_dense_eigensolver(ctx, nat, oracle_mod):
+    # Anderson A with B = 0.4 I + 0.05 L (3-D Laplacian): B's eigenvectors are not A's; the
+    # eigenvalues in two slices against scipy's dense generalized eigensolver
+    import scipy.linalg as sl
+    nx = 7
+    A = I.anderson_3d(nx, 3.0, 0)
+    n = A.n
+    Bd = 0.4 * np.eye(n) + 0.05 * I.laplacian_3d(nx).to_dense()
+    rows, cols = np.nonzero(Bd)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    B = I.CSR(n, rp, cols.astype(np.int32), Bd[rows, cols])
+    w = sl.eigh(A.to_dense(), Bd, eigvals_only=True)
+    ctx.set_csr(A)
+    ctx.set_csr_b(B, 0.39, 1.01, 1e-13)
+    lo, hi = ctx.bounds_gen(80, 0)
+    # converged bounds match the extreme eigenvalues up to p(B)'s 1e-13 accuracy
+    assert lo <= w[0] + 1e-12 * abs(w[-1]) and hi >= w[-1] - 1e-9 * abs(w[-1])
+    for a, b in [(2.0, 4.0), (8.0, 9.0)]:
+        ex = w[(w >= a) & (w <= b)]
+        f = nat.cheb_filter_build(a, b, lo, hi)
+        r = ctx.chebLanTr_gen(a, b, f, m=max(2 * len(ex), 40))
+        assert r["status"] == 0 and r["nev"] == len(ex)
+        assert np.max(np.abs(r["lam"] - ex)) <= 1e-9 * max(1.0, np.abs(ex).max())
+        X = r["Y"][:r["nev"]].T
+        assert np.max(np.abs(X.T @ Bd @ X - np.eye(r["nev"]))) <= 1e-10
