@@ -3,15 +3,19 @@
 // [bmin, bmax], applied to a vector with the Chebyshev three-term recurrence on
 // Bhat = (B - bc I) / bh.  The filter is rho((A B^{-1} - c I) / d): every degree of its
 // recurrence is one polynomial solve with B followed by one product with A, fused with the
-// recurrence update and the coefficient accumulation.  Lanczos runs in the B-inner product
-// (Algorithm 3) with two full reorthogonalisation passes; the eigenvectors come out
-// B-orthonormal.
+// recurrence update and the coefficient accumulation.  On top of it:
+//   - the pencil's spectral bounds by unfiltered Lanczos in the B-inner product (Algorithm 3);
+//   - the pencil's KPM density (Sec. 2.1), with starting vectors q(B) v, q(t) ~ t^{-1/2};
+//   - filtered non-restart Lanczos in the B-inner product with two full reorthogonalisation
+//     passes (ChebLanNr);
+//   - filtered thick-restart Lanczos with locking in the B-inner product (Algorithm 2).
+// The eigenvectors come out B-orthonormal.
 //
 // Kernels: one sliced-ELLPACK step (k_gen_step, a warp per 32-row slice, lane = row) whose
 // sparse operand u is separate from the shifted vector x, so that the same kernel serves the
-// solve with B (u = x) and the filter degree with A (u = p(B) x).  The Lanczos vector updates,
-// reorthogonalisation GEMVs, dot products and the small eigensolves are the dense helpers of
-// the standard path.
+// solve with B (u = x, on B's mapped values) and the filter degree with A (u = p(B) x).  The
+// Lanczos vector updates, reorthogonalisation GEMVs, dot products and the small eigensolves are
+// the dense helpers of the standard path.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -105,7 +109,8 @@ int d2h(evsl_ctx *c, void *dst, const void *src, size_t bytes)
     return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, "device-to-host copy");
 }
 
-// device scalars: alpha, a scratch norm, beta^2, (x, Bx), lambda, then the projections h
+// device scalars: alpha, a scratch norm, beta^2, (x, Bx), lambda, ||A x - lambda B x||^2,
+// ||y||^2 of the filtered vector, then the projection coefficients h
 enum { S_ALPHA = 0, S_TMP = 1, S_BETA2 = 2, S_NB2 = 3, S_LAM = 4, S_RES2 = 5, S_YN2 = 6, S_H = 8 };
 
 // n-vectors of the generalized drivers (one workspace, carved); zs: fixed input of the
