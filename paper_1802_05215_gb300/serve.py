@@ -144,8 +144,12 @@ class Server:
 def make_requests(server_mats: dict, spectra: dict, nreq: int, rate: float, seed: int = 0,
                   count_range=(20, 120)) -> list[Request]:
     """Poisson arrivals (rate per second); each request picks a matrix and an interval holding
-    a uniformly drawn number of eigenvalues, with ends placed midway between eigenvalues of the
-    known spectrum (closed form for the Laplacians, or a reference list)."""
+    about a uniformly drawn number of eigenvalues of the known spectrum (closed form for the
+    Laplacians, or a reference list).  The ends are placed midway between two distinct
+    eigenvalues (a drawn end inside a cluster of equal eigenvalues -- equal to 1e-10 of the
+    spectral radius, as closed-form multiple eigenvalues differ in their last bits -- moves
+    outwards to the cluster's edge), so the exact count, stored as the request's estimate, does
+    not depend on rounding."""
     rng = np.random.default_rng(seed)
     keys = sorted(server_mats)
     t = 0.0
@@ -153,11 +157,19 @@ def make_requests(server_mats: dict, spectra: dict, nreq: int, rate: float, seed
     for rid in range(nreq):
         t += rng.exponential(1.0 / rate)
         key = keys[rng.integers(len(keys))]
-        ev = spectra[key]
+        ev = np.sort(np.asarray(spectra[key], dtype=float))
+        tie = 1e-10 * np.abs(ev).max()
         c = int(rng.integers(count_range[0], count_range[1] + 1))
         i0 = int(rng.integers(1, len(ev) - c - 1))
+        e = i0 + c
+        while i0 > 1 and ev[i0] - ev[i0 - 1] <= tie:
+            i0 -= 1
+        while e < len(ev) - 1 and ev[e] - ev[e - 1] <= tie:
+            e += 1
+        if ev[i0] - ev[i0 - 1] <= tie or ev[e] - ev[e - 1] <= tie:
+            raise ValueError(f"no distinct eigenvalues to cut between for matrix {key}")
         a = 0.5 * (ev[i0 - 1] + ev[i0])
-        b = 0.5 * (ev[i0 + c - 1] + ev[i0 + c])
+        b = 0.5 * (ev[e - 1] + ev[e])
         exact = int(np.count_nonzero((ev >= a) & (ev <= b)))
         reqs.append(Request(rid, t, key, float(a), float(b), float(exact)))
     return reqs
