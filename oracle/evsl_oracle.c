@@ -18,6 +18,13 @@
  *   Chebyshev filter build           [Sec. 2.2.1, Eqs. (2.3)-(2.6)]
  *   filter application               [Eq. (2.4) with the mapping of Eq. (2.3)]
  *   filtered thick-restart Lanczos with locking  [Sec. 2.3, Eqs. (2.10)-(2.11); Algorithm 2]
+ *   non-restart filtered Lanczos (ChebLanNr)     [Sec. 2.3; Algorithm 2 without restarts]
+ *   polynomial filtered subspace iteration        [Sec. 2.6]
+ *   Lanczos quadrature density and its slicer     [Sec. 2.1]
+ *   KPM moment doubling                           [Sec. 2.1; T_2k = 2 T_k^2 - T_0]
+ *   generalized problems A x = lambda B x         [Sec. 2.4-2.5, Algorithm 3; lsPol of Sec. 4.3]:
+ *     polynomial B^{-1} and B^{-1/2}, the pencil's bounds, KPM density, non-restart and
+ *     thick-restart filtered Lanczos in the B-inner product
  *
  * Readings of passages that the paper leaves open are marked READING in the comments.
  */
