@@ -152,6 +152,27 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
+def reduce_over_ranks(x: float, op: str, device: str) -> float:
+    """x reduced over the ranks of the default process group ("max" or "sum"); x itself
+    without one (or with one rank).  device: where the reduction tensor lives (CUDA for NCCL,
+    CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[op])
+    return float(t.item())
+
+
+def whole_job_rate(local_units: float, local_seconds: float, device: str) -> tuple[float, float, float]:
+    """(units of all ranks, the slowest rank's seconds, units / seconds): the whole-job
+    throughput of a weak-scaling run, timed by the rank that finished last."""
+    total = reduce_over_ranks(local_units, "sum", device)
+    secs = reduce_over_ranks(local_seconds, "max", device)
+    return total, secs, total / secs
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -204,20 +225,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
     step = 0
     for _ in range(args.warmup):
         one_step(step, False)
@@ -242,7 +249,6 @@ def run_ours(args):
         ev1.record()
         barrier()
         wall = time.perf_counter() - t0
-    dev_s = max_over_ranks(max(ev0.elapsed_time(ev1) * 1e-3, 0.0) or wall)
     launches = ctx.launch_count() - launches0
     k_launch, k_ms = ctx.profile_get(native.K_CHEB_STEP)
     prof = {name: ctx.profile_get(k) for name, k in
@@ -250,8 +256,8 @@ def run_ours(args):
              ("reorth", native.K_REORTH), ("ritz_gemm", native.K_RITZ_GEMM),
              ("small_eig", native.K_SMALL_EIG)]}
     ctx.profile(False)
-    eig_total = sum_over_ranks(float(sum(r["nev"] for r in recs)))
-    value = eig_total / dev_s
+    eig_total, dev_s, value = whole_job_rate(float(sum(r["nev"] for r in recs)),
+                                             max(ev0.elapsed_time(ev1) * 1e-3, 0.0) or wall, "cuda")
 
     # ---- end-to-end leg through the C ABI with pinned host buffers
     barrier()
@@ -261,8 +267,7 @@ def run_ours(args):
         e2e_recs.append(one_step(step, True))
         step += 1
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_total = sum_over_ranks(float(sum(r["nev"] for r in e2e_recs)))
+    e2e_total, e2e_s, _ = whole_job_rate(float(sum(r["nev"] for r in e2e_recs)), time.perf_counter() - t0, "cuda")
     h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.val.nbytes
     d2h = float(np.mean([r["nev"] * n * 8 for r in e2e_recs]))
 

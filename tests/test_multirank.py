@@ -81,3 +81,39 @@ def test_two_rank_slice_sharding_matches_closed_form():
     ex = e[(e >= 0.5) & (e <= 1.5)]
     assert len(lam) == len(ex)
     assert np.max(np.abs(lam - ex)) < 1e-9
+
+
+def _rate_main(rank, world, port, out):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import torch.distributed as dist
+
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r found 10 (r + 1) eigenpairs in 1 + r seconds
+    out.put((rank, bench.whole_job_rate(10.0 * (rank + 1), 1.0 + rank, "cpu")))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_whole_job_rate_over_two_gloo_ranks():
+    # the bench's N-rank value: all ranks' eigenpairs over the slowest rank's time, the same on
+    # every rank; without a process group the rank's own numbers
+    import torch.multiprocessing as mp
+
+    import bench
+    assert bench.whole_job_rate(5.0, 2.0, "cpu") == (5.0, 2.0, 2.5)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rate_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got[0] == got[1] == (30.0, 2.0, 15.0)
