@@ -469,6 +469,27 @@ def test_landos_count_tracks_closed_form(oracle_mod):
         assert abs(oracle_mod.landos_count(d, A.n, t) - exact) <= 0.03 * A.n
 
 
+def test_slicer_ends_hit_the_quantiles_of_the_interpolated_count(oracle_mod):
+    # on a coarse grid x_0..x_{N-1} of [xi, eta], the slice ends are where the piecewise-linear
+    # interpolant of the cumulative count N(x_j) reaches the equal shares C_0 + (i/ns)(C_{N-1} - C_0)
+    # (first crossing, then linear interpolation between the grid points around it); the
+    # counts N(x_j) come from the separately pinned dos_count
+    A = I.laplacian_2d(40)
+    lo, hi = oracle_mod.bounds(A, 60, 0)
+    mu = oracle_mod.kpm_moments(A, 80, 10, 1, lo, hi)
+    xi, eta = 0.5, 6.5
+    for ns, npts in [(4, 9), (3, 7), (5, 16)]:
+        sli, est = oracle_mod.slicer(mu, lo, hi, xi, eta, ns, npts)
+        x = np.linspace(xi, eta, npts)
+        C = np.array([oracle_mod.dos_count(mu, lo, hi, t) for t in x])
+        assert np.all(np.diff(C) > 0)
+        for i in range(1, ns):
+            target = C[0] + (C[-1] - C[0]) * i / ns
+            assert abs(np.interp(sli[i], x, C) - target) <= 1e-9 * A.n
+        for i in range(ns):
+            assert abs(est[i] - (oracle_mod.dos_count(mu, lo, hi, sli[i + 1]) - oracle_mod.dos_count(mu, lo, hi, sli[i]))) <= 1e-9 * A.n
+
+
 def test_slicer_landos_balances_within_one_node(oracle_mod):
     # the slices partition [xi, eta]; their counts add up to the total, and each differs from
     # the equal share by at most the largest single node weight (first-crossing rule); on an
