@@ -162,3 +162,19 @@ def test_lspol_isqrt_matches_oracle(native, oracle_mod):
         assert lq["err"] <= eps
     with pytest.raises(native.EvslError):
         native.lspol(-1.0, 1.0, 1e-13, isqrt=True)
+
+
+def test_slice_by_landos_hand_computed_cuts(native):
+    # the same hand-computed quadratures as the oracle's pin: cuts midway between the first
+    # node reaching each equal share and the node before it
+    one = lambda nodes, weights: dict(nodes=np.array([nodes]), weights=np.array([weights]),
+                                      mused=np.array([len(nodes)], dtype=np.int32))
+    sli, est = native.slice_by_landos(one([0.1, 0.3, 0.5, 0.7, 0.9], [0.2] * 5), 100, 0.0, 1.0, 2)
+    assert np.allclose(sli, [0.0, 0.4, 1.0], atol=1e-15) and np.allclose(est, [40, 60], atol=1e-12)
+    sli, est = native.slice_by_landos(one([0.1, 0.3, 0.5, 0.7, 0.9], [0.1, 0.2, 0.3, 0.2, 0.2]), 100, 0.0, 1.0, 4)
+    assert np.allclose(sli, [0.0, 0.2, 0.4, 0.6, 1.0], atol=1e-15)
+    assert np.allclose(est, [10, 20, 30, 40], atol=1e-12)
+    d = dict(nodes=np.array([[0.1, 0.5], [0.3, 0.7]]), weights=np.full((2, 2), 0.5),
+             mused=np.array([2, 2], dtype=np.int32))
+    sli, est = native.slice_by_landos(d, 100, 0.0, 1.0, 2)
+    assert np.allclose(sli, [0.0, 0.2, 1.0], atol=1e-15) and np.allclose(est, [25, 75], atol=1e-12)

@@ -490,6 +490,27 @@ def test_slicer_ends_hit_the_quantiles_of_the_interpolated_count(oracle_mod):
             assert abs(est[i] - (oracle_mod.dos_count(mu, lo, hi, sli[i + 1]) - oracle_mod.dos_count(mu, lo, hi, sli[i]))) <= 1e-9 * A.n
 
 
+def test_slicer_landos_hand_computed_cuts(oracle_mod):
+    # small quadratures whose cuts follow by hand from the reading: a cut goes midway between the
+    # first node at which the cumulative count reaches the equal share and the node before it;
+    # est counts nodes in [t_i, t_{i+1}) ([t_i, t_{i+1}] for the last slice)
+    one = lambda nodes, weights: dict(nodes=np.array([nodes]), weights=np.array([weights]),
+                                      mused=np.array([len(nodes)], dtype=np.int32))
+    d = one([0.1, 0.3, 0.5, 0.7, 0.9], [0.2] * 5)            # counts 20 per node (n = 100)
+    sli, est = oracle_mod.slicer_landos(d, 100, 0.0, 1.0, 2)  # share 50: reached at 0.5
+    assert np.allclose(sli, [0.0, 0.4, 1.0], atol=1e-15) and np.allclose(est, [40, 60], atol=1e-12)
+    d = one([0.1, 0.3, 0.5, 0.7, 0.9], [0.1, 0.2, 0.3, 0.2, 0.2])   # counts 10, 20, 30, 20, 20
+    sli, est = oracle_mod.slicer_landos(d, 100, 0.0, 1.0, 4)  # shares 25, 50, 75
+    assert np.allclose(sli, [0.0, 0.2, 0.4, 0.6, 1.0], atol=1e-15)
+    assert np.allclose(est, [10, 20, 30, 40], atol=1e-12)
+    # two probes merge into one sorted quadrature (each node counts 25); the share 50 is reached
+    # exactly at the second node, which is where the cut goes
+    d = dict(nodes=np.array([[0.1, 0.5], [0.3, 0.7]]), weights=np.full((2, 2), 0.5),
+             mused=np.array([2, 2], dtype=np.int32))
+    sli, est = oracle_mod.slicer_landos(d, 100, 0.0, 1.0, 2)
+    assert np.allclose(sli, [0.0, 0.2, 1.0], atol=1e-15) and np.allclose(est, [25, 75], atol=1e-12)
+
+
 def test_slicer_landos_balances_within_one_node(oracle_mod):
     # the slices partition [xi, eta]; their counts add up to the total, and each differs from
     # the equal share by at most the largest single node weight (first-crossing rule); on an
