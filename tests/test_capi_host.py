@@ -178,3 +178,46 @@ def test_slice_by_landos_hand_computed_cuts(native):
              mused=np.array([2, 2], dtype=np.int32))
     sli, est = native.slice_by_landos(d, 100, 0.0, 1.0, 2)
     assert np.allclose(sli, [0.0, 0.2, 1.0], atol=1e-15) and np.allclose(est, [25, 75], atol=1e-12)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "evsl_gb300.h"
+
+int main(void)
+{
+    double coef[401];
+    evsl_filter_opts o = {0.8, 0.4, EVSL_DAMP_JACKSON, 400};
+    evsl_polfilt pol;
+    int st = evsl_cheb_filter_build(0.40, 0.48, 0.0, 8.0, &o, &pol, coef, 401);
+    printf("%d %d %.17g %.17g %.17g\n", st, pol.deg, pol.bar, pol.gamma, coef[pol.deg]);
+    double lc[201], err = 0.0;
+    int deg = 0;
+    st = evsl_lspol(0.11, 0.99, 1e-13, 200, &deg, lc, 201, &err);
+    printf("%d %d %.17g %.17g\n", st, deg, lc[0], err);
+    evsl_ctx *ctx = 0;
+    printf("%d\n", evsl_set_csr(ctx, 1, 0, 0, 0));
+    return 0;
+}
+"""
+
+
+def test_header_and_library_are_usable_from_c(native, tmp_path):
+    # a C99 program includes the header, links the library and calls host-only entry points;
+    # the values equal the Python binding's, and a NULL context is refused
+    import subprocess
+    src = tmp_path / "prog.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "prog"
+    libdir = os.path.dirname(native.library_path())
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-levsl_gb300", f"-Wl,-rpath,{libdir}"], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    st, deg, bar, gamma, clast = out[0].split()
+    f = native.cheb_filter_build(0.40, 0.48, 0.0, 8.0)
+    assert int(st) == 0 and int(deg) == f.deg
+    assert float(bar) == f.bar and float(gamma) == f.gamma and float(clast) == f.coef[-1]
+    st, deg, c0, err = out[1].split()
+    lp = native.lspol(0.11, 0.99, 1e-13)
+    assert int(st) == 0 and int(deg) == lp["deg"] and float(c0) == lp["coef"][0] and float(err) == lp["err"]
+    assert int(out[2]) == -1                    # EVSL_ERR_ARG
