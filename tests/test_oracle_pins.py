@@ -725,3 +725,19 @@ def test_cheblantr_gen_matches_dense_generalized_eigensolver(oracle_mod):
         assert np.max(np.abs(r["lam"] - ex)) <= 1e-9 * max(1.0, np.abs(ex).max())
         rn = oracle_mod.cheblannr_gen(A, B, lp, a, b, pol, m=max(6 * len(ex), 200))
         assert rn["nev"] == len(ex) and np.max(np.abs(rn["lam"] - ex)) <= 1e-9 * max(1.0, np.abs(ex).max())
+
+
+def test_cheblantr_unreachable_tolerance_locks_nothing_unconverged(oracle_mod):
+    # a tolerance at the residual floor is met by every pair (1e-15 relative), one below it
+    # (1e-16) by none: restarts then keep finding candidates that do not lock, which takes the
+    # stagnation refinement; a refined pair is kept only if it meets tol, so the run ends with
+    # EVSL_ERR_NOCONV and returns nothing it has not converged
+    A = I.laplacian_2d(20)
+    e = lap_eigs(2, 20)
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(1.0, 1.4, lo, hi)
+    r = oracle_mod.cheblantr(A, 1.0, 1.4, pol, m=40, maxit=600, tol=1e-15)
+    assert r["status"] == 0 and r["nev"] == count_in(e, 1.0, 1.4) and np.all(r["res"] <= 1e-15)
+    r = oracle_mod.cheblantr(A, 1.0, 1.4, pol, m=40, maxit=600, tol=1e-16)
+    assert r["status"] == -4 and r["nrestart"] >= 3
+    assert np.all(r["res"] <= 1e-16)
