@@ -741,3 +741,35 @@ def test_cheblantr_unreachable_tolerance_locks_nothing_unconverged(oracle_mod):
     r = oracle_mod.cheblantr(A, 1.0, 1.4, pol, m=40, maxit=600, tol=1e-16)
     assert r["status"] == -4 and r["nrestart"] >= 3
     assert np.all(r["res"] <= 1e-16)
+
+
+def test_empty_slices_run_the_minimum_empty_length(oracle_mod):
+    # reading 14: a slice holding no eigenvalue ends only after max(2 ncycle, m/4) = 50 steps
+    # (m = 200) in which no Ritz value reached bar: one such run for the non-restart solvers,
+    # two candidate-free cycles for thick restart; standard and generalized solvers alike
+    A, B = I.laplacian_2d(20), I.mass_matrix_2d(20)
+    e, lam = lap_eigs(2, 20), pencil_eigs(20)
+
+    def gap_slice(ev):
+        d = np.unique(np.round(ev, 10))
+        g = np.diff(d)
+        i = int(np.argmax(g[5:-5])) + 5
+        return d[i] + 0.25 * g[i], d[i + 1] - 0.25 * g[i]
+
+    a, b = gap_slice(e)
+    assert count_in(e, a, b) == 0
+    lo, hi = oracle_mod.bounds(A, 80, 0)
+    pol = oracle_mod.filter_build(a, b, lo, hi)
+    r = oracle_mod.cheblannr(A, a, b, pol, m=200)
+    assert r["status"] == 0 and r["nev"] == 0 and r["niter"] == 50
+    r = oracle_mod.cheblantr(A, a, b, pol, m=200)
+    assert r["status"] == 0 and r["nev"] == 0 and r["niter"] == 100 and r["nrestart"] == 2
+    lp, _ = _pencil_lsp(oracle_mod, A, B)
+    ga, gb = gap_slice(lam)
+    assert np.count_nonzero((lam >= ga) & (lam <= gb)) == 0
+    glo, ghi = oracle_mod.bounds_gen(A, B, lp, 80, 0)
+    gpol = oracle_mod.filter_build(ga, gb, glo, ghi)
+    r = oracle_mod.cheblannr_gen(A, B, lp, ga, gb, gpol, m=200)
+    assert r["status"] == 0 and r["nev"] == 0 and r["niter"] == 50
+    r = oracle_mod.cheblantr_gen(A, B, lp, ga, gb, gpol, m=200)
+    assert r["status"] == 0 and r["nev"] == 0 and r["niter"] == 100 and r["nrestart"] == 2
