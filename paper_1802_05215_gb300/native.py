@@ -2,7 +2,9 @@
 
 Every numerical step runs inside libevsl_gb300.so; this module converts numpy arrays and
 torch CUDA tensors to plain pointers.  Loading fails loudly if the library is missing: there
-is no CPU fallback.
+is no CPU fallback.  Each function mirrors the C call of the same name; the passage of
+arXiv:1802.05215 it implements is given in its docstring (and beside its declaration in the
+header).
 """
 from __future__ import annotations
 
@@ -156,7 +158,8 @@ class Filter:
 
 def lspol(bmin, bmax, eps=1e-13, maxdeg=200, isqrt=False):
     """Chebyshev coefficients of p(t) ~ 1/t (or ~ t^{-1/2} with isqrt) on [bmin, bmax] (the
-    polynomial B^{-1} or B^{-1/2}): dict(status, deg, coef, err)."""
+    polynomial B^{-1} of Sec. 4.3's lsPol, or B^{-1/2} for the starting vectors of a pencil's
+    density, Sec. 2.1): dict(status, deg, coef, err)."""
     lib = load()
     coef = np.zeros(maxdeg + 1)
     deg, err = C.c_int(), C.c_double()
@@ -169,6 +172,9 @@ def lspol(bmin, bmax, eps=1e-13, maxdeg=200, isqrt=False):
 
 def cheb_filter_build(a, b, lmin, lmax, tau=0.8, tau_ext=0.4, damping=DAMP_JACKSON,
                       max_deg=10000) -> Filter:
+    """Damped Chebyshev delta filter for [a, b] on [lmin, lmax] (Sec. 2.2.1, Eqs. (2.4)-(2.7);
+    boundary slices as in Sec. 4.2).  Returns a Filter; EVSL_ERR_NOCONV (max_deg reached) is
+    reported in its status, other errors raise."""
     lib = load()
     opts = FilterOpts(tau, tau_ext, damping, max_deg)
     pol = PolFilt()
@@ -182,7 +188,7 @@ def cheb_filter_build(a, b, lmin, lmax, tau=0.8, tau_ext=0.4, damping=DAMP_JACKS
 
 
 def slice_by_landos(d, n, xi, eta, nslices):
-    """Slices of [xi, eta] with equal counts under a Lanczos quadrature density d (from
+    """Slices of [xi, eta] with equal counts under a Lanczos quadrature density d (Sec. 2.1; from
     Context.landos); returns (sli, est)."""
     lib = load()
     nodes = np.ascontiguousarray(d["nodes"], dtype=np.float64)
@@ -198,6 +204,8 @@ def slice_by_landos(d, n, xi, eta, nslices):
 
 
 def slice_by_dos(mu, n, lmin, lmax, xi, eta, nslices, npts=0):
+    """DOS-balanced slice ends t_0..t_ns of [xi, eta] and per-slice count estimates from KPM
+    moments (Eq. (2.2), spslicer).  Host only."""
     lib = load()
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     sli = np.zeros(nslices + 1)
@@ -252,12 +260,13 @@ class Context:
         self._check(self.lib.evsl_set_stream(self.h, C.c_void_p(stream_handle or 0)), "set_stream")
 
     def set_csr(self, A):
+        """The matrix A (inputs.CSR, both triangles), copied to HBM in sliced ELLPACK (Sec. 3.1)."""
         self._check(self.lib.evsl_set_csr(self.h, A.n, _addr(A.row_ptr), _addr(A.col_idx),
                                           _addr(A.val)), "set_csr")
         self.n = A.n
 
     def set_csr_b(self, B, bmin, bmax, eps=1e-13, maxdeg=200):
-        """Mass matrix of a generalized problem with its spectrum in [bmin, bmax]; builds the
+        """Mass matrix of a generalized problem (Sec. 2.4) with its spectrum in [bmin, bmax]; builds the
         polynomial inverse.  Returns (degree, relative error) of p(t) ~ 1/t."""
         deg, err = C.c_int(), C.c_double()
         self._check(self.lib.evsl_set_csr_b(self.h, B.n, _addr(B.row_ptr), _addr(B.col_idx), _addr(B.val),
@@ -265,24 +274,24 @@ class Context:
         return deg.value, err.value
 
     def polyB_apply(self, x, y):
-        """y = p(B) x for device vectors of n doubles (synchronous)."""
+        """y = p(B) x, the polynomial solve with B (Sec. 4.3), for device vectors of n doubles."""
         self._check(self.lib.evsl_polyB_apply(self.h, _addr(x), _addr(y)), "polyB_apply")
 
     def kpm_dos_gen(self, degree, nvec, seed, lmin, lmax):
-        """KPM moments mu_0..degree of the pencil (the density of B^{-1/2} A B^{-1/2})."""
+        """KPM moments mu_0..degree of the pencil (the density of B^{-1/2} A B^{-1/2}; Sec. 2.1)."""
         mu = np.zeros(degree + 1)
         self._check(self.lib.evsl_kpm_dos_gen(self.h, degree, nvec, seed, lmin, lmax, _addr(mu)), "kpm_dos_gen")
         return mu
 
     def bounds_gen(self, steps=80, seed=0):
-        """Spectral bounds of the pencil (A, B) by B-Lanczos on B^{-1} A."""
+        """Spectral bounds of the pencil (A, B) by B-Lanczos on B^{-1} A (Algorithm 3)."""
         lo, hi = C.c_double(), C.c_double()
         self._check(self.lib.evsl_bounds_gen(self.h, steps, seed, C.byref(lo), C.byref(hi)), "bounds_gen")
         return lo.value, hi.value
 
     def chebLanNr_gen(self, a, b, filt: Filter, m=200, ncycle=10, tol=1e-8, tau1=1e-10, seed=0,
                       right_closed=True, cap=None, Y=None, allow_partial=False):
-        """Filtered non-restart Lanczos for A x = lambda B x on [a, b]; same outputs as chebLanNr
+        """Filtered non-restart Lanczos for A x = lambda B x on [a, b] (Sec. 2.5, Algorithm 3); as chebLanNr
         (the eigenvectors are B-orthonormal)."""
         cap = cap or m
         opts = LanOpts(m, 0, ncycle, tol, tau1, seed, FP64, int(right_closed))
@@ -302,7 +311,8 @@ class Context:
 
     def chebLanTr_gen(self, a, b, filt: Filter, m=100, maxit=0, ncycle=10, tol=1e-8, tau1=1e-10, seed=0,
                       right_closed=True, cap=None, Y=None, allow_partial=False):
-        """Filtered thick-restart Lanczos with locking for A x = lambda B x on [a, b]; outputs as
+        """Filtered thick-restart Lanczos with locking for A x = lambda B x on [a, b] (Algorithm 2 in
+        the B-inner product, Sec. 2.5); outputs as
         chebLanTr (B-orthonormal eigenvectors)."""
         cap = cap or (m + 64)
         opts = LanOpts(m, maxit, ncycle, tol, tau1, seed, FP64, int(right_closed))
@@ -321,26 +331,28 @@ class Context:
                     stats=stats.as_dict())
 
     def bounds(self, steps=80, seed=0):
+        """Spectral bounds (lmin, lmax) from `steps` Lanczos steps (Sec. 2.2.1, LanTrbounds)."""
         lo, hi = C.c_double(), C.c_double()
         self._check(self.lib.evsl_bounds(self.h, steps, seed, C.byref(lo), C.byref(hi)), "bounds")
         return lo.value, hi.value
 
     def kpm_dos(self, degree, nvec, seed, lmin, lmax, prec=FP64, doubling=False):
-        """KPM moments mu_0..degree (doubling: from ceil(degree/2) recurrence steps)."""
+        """KPM moments mu_0..degree (Sec. 2.1; doubling: from ceil(degree/2) recurrence steps)."""
         mu = np.zeros(degree + 1)
         fn = self.lib.evsl_kpm_dos_doubling if doubling else self.lib.evsl_kpm_dos
         self._check(fn(self.h, degree, nvec, seed, lmin, lmax, prec, _addr(mu)), "kpm_dos")
         return mu
 
     def filter_apply(self, filt: Filter, X, Y, prec=FP64):
-        """Y = rho(Ahat) X for device blocks X, Y (n x nvec column-major, e.g. torch tensors
+        """Y = rho(Ahat) X (Eq. (2.4)) for device blocks X, Y (n x nvec column-major, e.g. torch tensors
         of shape (nvec, n) on the GPU)."""
         nvec = X.numel() // self.n
         self._check(self.lib.evsl_filter_apply(self.h, C.byref(filt.pol), nvec, _addr(X),
                                                _addr(Y), prec), "filter_apply")
 
     def filter_apply_multi(self, filters, X, Y, prec=FP64):
-        """Column t of the device block X (n x len(filters)) is filtered by filters[t]."""
+        """Column t of the device block X (n x len(filters)) is filtered by filters[t] (Eq. (2.4) for
+        several slices at once)."""
         arr = (PolFilt * len(filters))(*[f.pol for f in filters])
         self._check(self.lib.evsl_filter_apply_multi(self.h, len(filters), arr, _addr(X), _addr(Y),
                                                      prec), "filter_apply_multi")
@@ -354,7 +366,7 @@ class Context:
 
     def chebLanTr(self, a, b, filt: Filter, m=100, maxit=0, ncycle=10, tol=1e-8, tau1=1e-10,
                   seed=0, prec=FP64, right_closed=True, cap=None, Y=None, allow_partial=False):
-        """Filtered thick-restart Lanczos on [a, b].  Y: None (host numpy result) or a
+        """Filtered thick-restart Lanczos with locking on [a, b] (Algorithm 2).  Y: None (host numpy result) or a
         caller-provided buffer (numpy host array or torch CUDA tensor of n*cap doubles)."""
         cap = cap or (m + 64)
         opts = LanOpts(m, maxit, ncycle, tol, tau1, seed, prec, int(right_closed))
@@ -374,7 +386,7 @@ class Context:
                     stats=stats.as_dict())
 
     def landos(self, m, nvec, seed=0):
-        """Lanczos quadrature density: dict of nodes, weights (nvec x m) and mused."""
+        """Lanczos quadrature density (Sec. 2.1): dict of nodes, weights (nvec x m) and mused."""
         nodes = np.zeros((nvec, m))
         weights = np.zeros((nvec, m))
         mused = np.zeros(nvec, dtype=np.int32)
@@ -384,7 +396,7 @@ class Context:
 
     def chebSI(self, a, b, filt: Filter, nv, maxit=100, tol=1e-8, seed=0, right_closed=True,
                cap=None, Y=None, allow_partial=False):
-        """Polynomial filtered subspace iteration with a block of nv vectors; same outputs as
+        """Polynomial filtered subspace iteration (Sec. 2.6) with a block of nv vectors; same outputs as
         chebLanTr (stats["niter"] counts passes)."""
         cap = cap or nv
         opts = LanOpts(nv, maxit, 10, tol, 1e-10, seed, FP64, int(right_closed))
@@ -404,7 +416,7 @@ class Context:
 
     def chebLanNr(self, a, b, filt: Filter, m=400, ncycle=10, tol=1e-8, tau1=1e-10, seed=0,
                   prec=FP64, right_closed=True, cap=None, Y=None, allow_partial=False):
-        """Filtered non-restart Lanczos on [a, b] with a basis of at most m vectors; same
+        """Filtered non-restart Lanczos (ChebLanNr, Sec. 2.3) on [a, b] with a basis of at most m vectors; same
         outputs as chebLanTr (stats["nrestart"] counts the extractions)."""
         cap = cap or m
         opts = LanOpts(m, 0, ncycle, tol, tau1, seed, prec, int(right_closed))
@@ -426,7 +438,7 @@ class Context:
     def chebLanTr_batch(self, slices, filters, ms, caps=None, maxit=0, ncycle=10, tol=1e-8,
                         tau1=1e-10, seed=0, prec=FP64, right_closed=None, Ys=None,
                         allow_partial=False):
-        """Several slices [a_j, b_j] of the current matrix solved in lockstep with batched
+        """Several slices [a_j, b_j] of the current matrix solved in lockstep (Algorithm 2 per slice) with batched
         filters.  Returns one result dict per slice (as chebLanTr)."""
         nj = len(slices)
         caps = caps or [m + 64 for m in ms]
