@@ -75,6 +75,8 @@ def _load():
         _lib.orc_cheblantr_gen.restype = i32
         _lib.orc_cheblantr_gen.argtypes = [i64, P, P, P, P, P, P, d, d, i32, P, d, d, i32, d, d, i32, P, d,
                                            i32, i32, i32, d, d, u64, i32, P, P, P, P, P]
+        _lib.orc_landos_gen.restype = i32
+        _lib.orc_landos_gen.argtypes = [i64, P, P, P, P, P, P, d, d, i32, P, i32, P, i32, i32, u64, P, P, P]
         _lib.orc_kpm_moments_gen.restype = i32
         _lib.orc_kpm_moments_gen.argtypes = [i64, P, P, P, P, P, P, d, d, i32, P, i32, P, i32, i32, u64, d, d, P]
         _lib.orc_polyB_apply.restype = None
@@ -268,6 +270,17 @@ def kpm_moments_gen(A, B, lp, lq, M, nvec, seed, lmin, lmax):
     _load().orc_kpm_moments_gen(*_csr_args(A), *_csr_args(B)[1:], lp["bmin"], lp["bmax"], lp["deg"], _p(lp["coef"]),
                                 lq["deg"], _p(lq["coef"]), M, nvec, seed, lmin, lmax, _p(mu))
     return mu
+
+
+def landos_gen(A, B, lp, lq, m, nvec, seed=0):
+    """Lanczos quadrature density of the pencil (A, B) (the density of B^{-1/2} A B^{-1/2}): dict of
+    nodes, weights (nvec x m) and mused, as landos."""
+    nodes = np.zeros((nvec, m))
+    weights = np.zeros((nvec, m))
+    mused = np.zeros(nvec, dtype=np.int32)
+    _load().orc_landos_gen(*_csr_args(A), *_csr_args(B)[1:], lp["bmin"], lp["bmax"], lp["deg"], _p(lp["coef"]),
+                           lq["deg"], _p(lq["coef"]), m, nvec, seed, _p(nodes), _p(weights), _p(mused))
+    return dict(nodes=nodes, weights=weights, mused=mused)
 
 
 def poly_solve(B, lp, x):

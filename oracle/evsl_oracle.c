@@ -1944,3 +1944,66 @@ done:
     free(trtheta); free(trs);
     return status;
 }
+
+/* Lanczos density of a pencil (Sec. 2.1: the DOS methods extend to A x = lambda B x with solves
+ * with B and starting vectors built with B^{1/2} or the Cholesky factor; Example 1 of Sec. 3 runs
+ * lanDos and spslicer2 on a pencil).  READING: the density of S = B^{-1/2} A B^{-1/2}, whose
+ * eigenvalues are the pencil's.  For each of nvec unit vectors v_l (as orc_landos: uniform(-1, 1)
+ * entries from stream 5, index l n + i, normalised), the pair w_1 = q(B) v_l (~ B^{-1/2} v_l,
+ * q from orc_lspol_isqrt), z_1 = B w_1, scaled to w_1^T z_1 = 1, starts m steps of the
+ * B-inner-product Lanczos on B^{-1} A (Algorithm 3 as in orc_bounds_gen, B^{-1} by p(B)).
+ * Since B^{1/2} f(B^{-1} A) B^{-1/2} = f(S), T_m = S diag(theta) S^T gives the Gaussian
+ * quadrature of v_l^T f(S) v_l: nodes theta_j, weights S_{1j}^2.  A breakdown
+ * (beta <= 1e-13 ||A w_i|| / sqrt(bmax), that norm a lower bound of ||A w_i||_{B^{-1}}) ends the
+ * run of that vector.  Outputs as orc_landos (nvec x m rows: nodes, weights; mused). */
+int orc_landos_gen(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                   const int64_t *brp, const int32_t *bci, const double *bv, double bmin, double bmax,
+                   int bdeg, const double *bcoef, int sdeg, const double *scoef, int m, int nvec,
+                   uint64_t seed, double *nodes, double *weights, int *mused)
+{
+    orc_csr A = {n, rp, ci, v}, B = {n, brp, bci, bv};
+    double *t = malloc(sizeof(double) * 3 * n);
+    orc_pencil P = {&A, &B, 0.5 * (bmax + bmin), 0.5 * (bmax - bmin), bdeg, bcoef, t, t + n, t + 2 * n};
+    if (m > n) m = (int)n;
+    double *W = calloc((size_t)n * (m + 1), sizeof(double)), *Z = calloc((size_t)n * (m + 1), sizeof(double));
+    double *T = calloc((size_t)m * m, sizeof(double)), *th = malloc(sizeof(double) * m);
+    double *z = malloc(sizeof(double) * n), *wt = malloc(sizeof(double) * n), *vl = malloc(sizeof(double) * n);
+    for (int l = 0; l < nvec; l++) {
+        for (int64_t i = 0; i < n; i++)
+            vl[i] = 2.0 * orc_unit(orc_draw(seed, ORC_STREAM_LANDOS, (uint64_t)l * (uint64_t)n + (uint64_t)i)) - 1.0;
+        const double nv = orc_nrm2(n, vl);
+        for (int64_t i = 0; i < n; i++) vl[i] /= nv;
+        orc_polyB(&B, P.bc, P.bh, sdeg, scoef, vl, W, t, t + n, t + 2 * n);     /* w_1 = q(B) v */
+        orc_matvec(&B, W, Z);                                                   /* z_1 = B w_1 */
+        const double s = sqrt(orc_dot(n, W, Z));
+        for (int64_t i = 0; i < n; i++) { W[i] /= s; Z[i] /= s; }
+        memset(T, 0, sizeof(double) * (size_t)m * m);
+        int k = 0;
+        double beta = 0.0;
+        for (int j = 0; j < m; j++) {
+            orc_matvec(&A, W + (size_t)j * n, z);
+            const double nz = orc_nrm2(n, z);
+            double bn = 0.0;
+            const double alpha = orc_lanab_step(&P, j, W, Z, z, beta, wt, &bn);
+            AT(T, j, j, m) = alpha;
+            k = j + 1;
+            beta = bn;
+            if (j + 1 == m || beta <= 1e-13 * nz / sqrt(bmax)) break;
+            AT(T, j, j + 1, m) = beta;
+            AT(T, j + 1, j, m) = beta;
+        }
+        double *Tk = malloc(sizeof(double) * (size_t)k * k), *Sk = malloc(sizeof(double) * (size_t)k * k);
+        for (int c = 0; c < k; c++)
+            for (int r = 0; r < k; r++) AT(Tk, r, c, k) = AT(T, r, c, m);
+        orc_syev(k, Tk, th, Sk);
+        for (int j = 0; j < m; j++) {
+            nodes[(size_t)l * m + j] = j < k ? th[j] : 0.0;
+            weights[(size_t)l * m + j] = j < k ? AT(Sk, 0, j, k) * AT(Sk, 0, j, k) : 0.0;
+        }
+        mused[l] = k;
+        free(Tk);
+        free(Sk);
+    }
+    free(t); free(W); free(Z); free(T); free(th); free(z); free(wt); free(vl);
+    return 0;
+}

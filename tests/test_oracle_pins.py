@@ -773,3 +773,83 @@ def test_empty_slices_run_the_minimum_empty_length(oracle_mod):
     assert r["status"] == 0 and r["nev"] == 0 and r["niter"] == 50
     r = oracle_mod.cheblantr_gen(A, B, lp, ga, gb, gpol, m=200)
     assert r["status"] == 0 and r["nev"] == 0 and r["niter"] == 100 and r["nrestart"] == 2
+
+
+def _inv_sqrt(M):
+    w, Q = np.linalg.eigh(M)
+    return Q @ np.diag(w ** -0.5) @ Q.T
+
+
+def _anderson_pencil(nx):
+    # Anderson A (W = 3) with B = 0.4 I + 0.05 L (3-D Laplacian): matrices that do not commute
+    A = I.anderson_3d(nx, 3.0, 0)
+    n = A.n
+    Bd = 0.4 * np.eye(n) + 0.05 * I.laplacian_3d(nx).to_dense()
+    rows, cols = np.nonzero(Bd)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    return A, I.CSR(n, rp, cols.astype(np.int32), Bd[rows, cols]), Bd
+
+
+def test_landos_gen_quadrature_is_exact_to_degree_2m_minus_1(oracle_mod):
+    # m B-Lanczos steps give the m-point Gauss quadrature of v^T f(S) v, S = B^{-1/2} A B^{-1/2}:
+    # sum_j tau_j theta_j^p = v^T S^p v for p <= 2m - 1 (v the normalised seeded start vector)
+    A, B = I.laplacian_2d(6), I.mass_matrix_2d(6)
+    lp, lq = _pencil_lsp(oracle_mod, A, B)
+    Bm = _inv_sqrt(B.to_dense())
+    S = Bm @ A.to_dense() @ Bm
+    smax = np.linalg.eigvalsh(S).max()
+    m, nvec = 6, 3
+    d = oracle_mod.landos_gen(A, B, lp, lq, m, nvec, 7)
+    assert list(d["mused"]) == [m] * nvec
+    for l in range(nvec):
+        v = I.start_vector(A.n, 7, I.STREAM_LANDOS, l)
+        v /= np.linalg.norm(v)
+        th, tau = d["nodes"][l, :m], d["weights"][l, :m]
+        x = v.copy()
+        for p in range(2 * m):
+            assert abs(np.sum(tau * th ** p) - v @ x) <= 1e-10 * smax ** p
+            x = S @ x
+
+
+def test_landos_gen_full_run_is_the_exact_spectral_measure(oracle_mod):
+    # a full-length run on a pencil with distinct eigenvalues: the nodes are the pencil's
+    # eigenvalues and the weights (v . y_j)^2, y_j the eigenvectors of S
+    A, B, Bd = _anderson_pencil(6)
+    lp, lq = oracle_mod.lspol(0.39, 1.01, 1e-13), oracle_mod.lspol_isqrt(0.39, 1.01, 1e-13)
+    Bm = _inv_sqrt(Bd)
+    w, Y = np.linalg.eigh(Bm @ A.to_dense() @ Bm)
+    d = oracle_mod.landos_gen(A, B, lp, lq, A.n, 1, 3)
+    k = int(d["mused"][0])
+    assert k == A.n
+    assert np.max(np.abs(np.sort(d["nodes"][0, :k]) - w)) <= 1e-10 * np.abs(w).max()
+    v = I.start_vector(A.n, 3, I.STREAM_LANDOS, 0)
+    v /= np.linalg.norm(v)
+    order = np.argsort(d["nodes"][0, :k])
+    assert np.max(np.abs(d["weights"][0, :k][order] - (Y.T @ v) ** 2)) <= 1e-10
+
+
+def test_landos_gen_with_scaled_identity_is_the_standard_density(oracle_mod):
+    # B = 2I: the pencil's eigenvalues are lambda(A)/2 and the start vectors are the same, so the
+    # nodes are the standard run's halved and the weights are equal
+    A = I.anderson_3d(6, 3.0, 1)
+    n = A.n
+    B2 = I.CSR(n, np.arange(n + 1), np.arange(n, dtype=np.int32), np.full(n, 2.0))
+    lp, lq = oracle_mod.lspol(1.5, 2.5, 1e-13), oracle_mod.lspol_isqrt(1.5, 2.5, 1e-13)
+    dg = oracle_mod.landos_gen(A, B2, lp, lq, 30, 3, 5)
+    ds = oracle_mod.landos(A, 30, 3, 5)
+    assert np.array_equal(dg["mused"], ds["mused"])
+    assert np.max(np.abs(2.0 * dg["nodes"] - ds["nodes"])) <= 1e-12 * np.abs(ds["nodes"]).max()
+    assert np.max(np.abs(dg["weights"] - ds["weights"])) <= 1e-12
+
+
+def test_landos_gen_count_tracks_the_pencil_closed_form(oracle_mod):
+    # the cumulative quadrature count of the 20^2 pencil estimates its closed-form counts
+    # (statistical: 30 vectors of 40 steps); the count above the spectrum is n
+    A, B = I.laplacian_2d(20), I.mass_matrix_2d(20)
+    lp, lq = _pencil_lsp(oracle_mod, A, B)
+    lam = pencil_eigs(20)
+    d = oracle_mod.landos_gen(A, B, lp, lq, 40, 30, 1)
+    assert abs(oracle_mod.landos_count(d, A.n, 1.1 * lam[-1]) - A.n) <= 1e-9 * A.n
+    for t in (5.0, 15.0, 30.0, 50.0, 65.0):
+        assert abs(oracle_mod.landos_count(d, A.n, t) - np.count_nonzero(lam <= t)) <= 0.03 * A.n
