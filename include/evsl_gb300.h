@@ -357,6 +357,16 @@ int evsl_polyB_apply(evsl_ctx *ctx, const double *x, double *y);
 int evsl_kpm_dos_gen(evsl_ctx *ctx, int degree, int nvec, uint64_t seed, double lmin, double lmax,
                      double *mu);
 
+/* Lanczos quadrature density of the pencil (Sec. 2.1's Lanczos density extended to A x = lambda B x;
+ * the lanDos step of the paper's Example 1): for each of nvec unit start vectors v_l (those of
+ * evsl_landos), m steps of the B-inner-product Lanczos (Algorithm 3) on B^{-1} A from
+ * w_1 = q(B) v_l (q ~ t^{-1/2}, set by evsl_set_csr_b) give the Gauss quadrature of
+ * v_l^T f(B^{-1/2} A B^{-1/2}) v_l.  Outputs, layout and breakdown rule as evsl_landos (the
+ * breakdown norm is ||A w_i|| / sqrt(bmax)); the result feeds evsl_slice_by_landos unchanged.
+ * Errors: EVSL_ERR_ARG, EVSL_ERR_STATE (as evsl_bounds_gen). */
+int evsl_landos_gen(evsl_ctx *ctx, int m, int nvec, uint64_t seed, double *nodes, double *weights,
+                    int *mused);
+
 /* Spectral bounds of the pencil: `steps` unfiltered steps of the B-inner-product Lanczos
  * (Algorithm 3) on B^{-1} A from a seeded start (Lanczos stream, index 0), with p(B) for B^{-1};
  * lmin = theta_1 - |beta s_{m,1}|, lmax = theta_m + |beta s_{m,m}|.  Errors: EVSL_ERR_ARG,

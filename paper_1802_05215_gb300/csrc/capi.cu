@@ -517,6 +517,15 @@ int evsl_chebLanTr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol,
     return drv_chebLanTr_gen(c, a, b, pol, opts, cap, nev, lam, Y, res, stats);
 }
 
+int evsl_landos_gen(evsl_ctx *c, int m, int nvec, uint64_t seed, double *nodes, double *weights, int *mused)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (m < 1 || nvec < 1 || !nodes || !weights || !mused) return ctx_fail(c, EVSL_ERR_ARG, "landos_gen: bad arguments");
+    cudaSetDevice(c->device);
+    return drv_landos_gen(c, m, nvec, seed, nodes, weights, mused);
+}
+
 int evsl_set_graphs(evsl_ctx *c, int enable)
 {
     if (!c) return EVSL_ERR_ARG;

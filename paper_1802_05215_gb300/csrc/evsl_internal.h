@@ -254,6 +254,7 @@ int host_lspol(double bmin, double bmax, double eps, int maxdeg, int *deg, doubl
 int gen_map_b(evsl_ctx *c);
 int drv_polyB_apply(evsl_ctx *c, const double *x, double *y);
 int drv_kpm_gen(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax, double *mu);
+int drv_landos_gen(evsl_ctx *c, int m, int nvec, uint64_t seed, double *nodes, double *weights, int *mused);
 int drv_chebLanTr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, const evsl_lan_opts *o,
                       int cap, int *nev, double *lam, double *Y, double *res, evsl_stats *st);
 int drv_bounds_gen(evsl_ctx *c, int steps, uint64_t seed, double *lmin, double *lmax);

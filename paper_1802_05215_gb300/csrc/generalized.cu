@@ -933,3 +933,71 @@ int drv_chebLanTr_gen(evsl_ctx *c, double a, double b, const evsl_polfilt *pol, 
     }
     return status;
 }
+
+// Lanczos quadrature density of the pencil (the density of S = B^{-1/2} A B^{-1/2}): for each of
+// nvec unit vectors v_l (uniform(-1, 1), the standard density's stream and indexing, normalised),
+// the pair w_1 = q(B) v_l, z_1 = B w_1 scaled to w_1^T z_1 = 1 starts m steps of Algorithm 3 on
+// B^{-1} A (as drv_bounds_gen).  T_m = S diag(theta) S^T gives the Gauss quadrature of
+// v_l^T f(S) v_l: nodes theta_j (ascending), weights S_{1j}^2.  A breakdown
+// (beta <= 1e-13 ||A w_i|| / sqrt(bmax)) ends that vector's run.  Outputs as drv_landos.
+int drv_landos_gen(evsl_ctx *c, int m, int nvec, uint64_t seed, double *nodes, double *weights, int *mused)
+{
+    EVSL_TRY(check_pencil(c, "landos_gen"));
+    if (c->b_coef_isqrt.empty()) return ctx_fail(c, EVSL_ERR_STATE, "landos_gen: no B^{-1/2} polynomial");
+    const int64_t n = c->A.n;
+    const int mm = (int)std::min<int64_t>(m, n);
+    double *W, *Z, *sc;
+    EVSL_TRY(get_basis(c, mm, 0, &W, &Z, nullptr, &sc, mm + 1));
+    Vecs v;
+    EVSL_TRY(get_vecs(c, v));
+    const double sqrt_bmax = std::sqrt(c->b_max);
+    for (int l = 0; l < nvec; l++) {
+        EVSL_TRY(fill_uniform_f64(c, n, seed, SM_STREAM_LANDOS, (uint64_t)l, v.x));
+        EVSL_TRY(coldot(c, n, 1, v.x, n, v.x, n, sc + S_NB2));
+        double nv2 = 0.0;
+        EVSL_TRY(d2h(c, &nv2, sc + S_NB2, sizeof(double)));
+        EVSL_TRY(scale_vec(c, n, v.x, 1.0 / std::sqrt(nv2), nullptr));
+        EVSL_TRY(apply_poly_b(c, c->b_coef_isqrt, v.x, W, v.t1, v.t2));                       // w_1 = q(B) v
+        EVSL_TRY(gen_step<2>(c, c->B, W, nullptr, nullptr, Z, nullptr, 0.0, 0.0, 0.0, 0.0));  // z_1 = B w_1
+        EVSL_TRY(coldot(c, n, 1, W, n, Z, n, sc + S_NB2));
+        double s2 = 0.0;
+        EVSL_TRY(d2h(c, &s2, sc + S_NB2, sizeof(double)));
+        if (!(s2 > 0.0)) return ctx_fail(c, EVSL_ERR_ARG, "landos_gen: (w, B w) = %g; B is not positive definite", s2);
+        EVSL_TRY(scale_vec(c, n, W, 1.0 / std::sqrt(s2), nullptr));
+        EVSL_TRY(scale_vec(c, n, Z, 1.0 / std::sqrt(s2), nullptr));
+        std::vector<double> T((size_t)mm * mm, 0.0);
+        double beta = 0.0;
+        int k = 0;
+        for (int j = 0; j < mm; j++) {
+            EVSL_TRY(gen_step<2>(c, c->A, W + (int64_t)j * n, nullptr, nullptr, v.z, nullptr, 0.0, 0.0, 0.0, 0.0));
+            EVSL_TRY(coldot(c, n, 1, v.z, n, v.z, n, sc + S_YN2));
+            double alpha = 0.0, bn = 0.0, nz2 = 0.0;
+            EVSL_TRY(lanab_step(c, j, W, Z, v.z, beta, v, sc, &alpha, &bn));
+            EVSL_TRY(d2h(c, &nz2, sc + S_YN2, sizeof(double)));
+            T[(size_t)j * mm + j] = alpha;
+            k = j + 1;
+            beta = bn;
+            if (j + 1 == mm || beta <= 1e-13 * std::sqrt(std::max(0.0, nz2)) / sqrt_bmax) break;
+            T[(size_t)(j + 1) * mm + j] = beta;
+            T[(size_t)j * mm + j + 1] = beta;
+        }
+        std::vector<double> w;
+        double *V = nullptr;
+        int ldv = 0;
+        EVSL_TRY(tri_eig(c, k, T, mm, w, &V, &ldv));
+        std::vector<double> s0(k);
+        cudaError_t e = cudaMemcpy2DAsync(s0.data(), sizeof(double), V, sizeof(double) * ldv, sizeof(double), k,
+                                          cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return ctx_cuda(c, e, "landos_gen first row");
+        std::vector<int> order(k);
+        for (int j = 0; j < k; j++) order[j] = j;
+        std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] < w[y]; });
+        for (int j = 0; j < m; j++) {
+            nodes[(size_t)l * m + j] = j < k ? w[order[j]] : 0.0;
+            weights[(size_t)l * m + j] = j < k ? s0[order[j]] * s0[order[j]] : 0.0;
+        }
+        mused[l] = k;
+    }
+    return EVSL_OK;
+}

@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
         "evsl_set_csr_b": (i32, [P, i64, P, P, P, d, d, d, i32, P, P]),
         "evsl_lspol_isqrt": (i32, [d, d, d, i32, P, P, i32, P]),
         "evsl_kpm_dos_gen": (i32, [P, i32, i32, u64, d, d, P]),
+        "evsl_landos_gen": (i32, [P, i32, i32, u64, P, P, P]),
         "evsl_polyB_apply": (i32, [P, P, P]),
         "evsl_bounds_gen": (i32, [P, i32, u64, P, P]),
         "evsl_chebLanNr_gen": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
@@ -282,6 +283,16 @@ class Context:
         mu = np.zeros(degree + 1)
         self._check(self.lib.evsl_kpm_dos_gen(self.h, degree, nvec, seed, lmin, lmax, _addr(mu)), "kpm_dos_gen")
         return mu
+
+    def landos_gen(self, m, nvec, seed=0):
+        """Lanczos quadrature density of the pencil (Sec. 2.1; the density of B^{-1/2} A B^{-1/2}):
+        dict of nodes, weights (nvec x m) and mused, as landos."""
+        nodes = np.zeros((nvec, m))
+        weights = np.zeros((nvec, m))
+        mused = np.zeros(nvec, dtype=np.int32)
+        self._check(self.lib.evsl_landos_gen(self.h, m, nvec, seed, _addr(nodes), _addr(weights),
+                                             mused.ctypes.data), "landos_gen")
+        return dict(nodes=nodes, weights=weights, mused=mused)
 
     def bounds_gen(self, steps=80, seed=0):
         """Spectral bounds of the pencil (A, B) by B-Lanczos on B^{-1} A (Algorithm 3)."""

@@ -122,6 +122,7 @@ def test_entry_points_reject_null_context_and_bad_arguments(native):
     assert lib.evsl_polyB_apply(nul, nul, nul) == -1
     assert lib.evsl_bounds_gen(nul, 10, 0, buf, buf) == -1
     assert lib.evsl_kpm_dos_gen(nul, 10, 2, 0, 0.0, 1.0, buf) == -1
+    assert lib.evsl_landos_gen(nul, 10, 2, 0, buf, buf, ibuf) == -1
     assert lib.evsl_chebLanTr_gen(nul, 0.0, 1.0, nul, nul, 1, ctypes.byref(i32()), buf, nul, buf, nul) == -1
     assert lib.evsl_chebLanNr_gen(nul, 0.0, 1.0, nul, nul, 1, ctypes.byref(i32()), buf, nul, buf, nul) == -1
     nodes = np.array([[0.1, 0.5, 0.9]])
