@@ -221,3 +221,23 @@ def test_cheblantr_gen_noncommuting_pencil_matches_dense_eigensolver(ctx, nat, o
         assert np.max(np.abs(r["lam"] - ex)) <= 1e-9 * max(1.0, np.abs(ex).max())
         X = r["Y"][:r["nev"]].T
         assert np.max(np.abs(X.T @ Bd @ X - np.eye(r["nev"]))) <= 1e-10
+
+
+def test_landos_gen_matches_oracle_and_slices(nat, oracle_mod):
+    # the pencil's Lanczos quadrature density against the oracle's (same start vectors, p and q
+    # from the same interval), and the quadrature slicer on it gives the oracle's slices
+    A, B = I.laplacian_2d(20), I.mass_matrix_2d(20)
+    blo, bhi = oracle_mod.bounds(B, 80, 0)
+    lp, lq = oracle_mod.lspol(blo, bhi, 1e-13), oracle_mod.lspol_isqrt(blo, bhi, 1e-13)
+    with nat.Context(0) as ctx:
+        ctx.set_csr(A)
+        ctx.set_csr_b(B, blo, bhi, 1e-13)
+        d = ctx.landos_gen(30, 6, 2)
+    do = oracle_mod.landos_gen(A, B, lp, lq, 30, 6, 2)
+    assert np.array_equal(d["mused"], do["mused"])
+    lam = pencil_eigs(20)
+    assert np.max(np.abs(d["nodes"] - do["nodes"])) <= 1e-9 * lam[-1]
+    assert np.max(np.abs(d["weights"] - do["weights"])) <= 1e-9
+    s, e = nat.slice_by_landos(d, A.n, 10.0, 60.0, 4)
+    so, eo = oracle_mod.slicer_landos(do, A.n, 10.0, 60.0, 4)
+    assert np.allclose(s, so, atol=1e-9 * lam[-1])
