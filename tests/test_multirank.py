@@ -4,7 +4,6 @@ import os
 import socket
 
 import numpy as np
-import pytest
 
 from closed_form import lap_eigs
 

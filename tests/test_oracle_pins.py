@@ -267,7 +267,6 @@ def test_filter_shape_properties(oracle_mod, damping):
     if damping == 1:
         assert k == 97
     # minimality: the balanced filter of degree k-1 does not reach tau
-    from oracle import _load  # noqa: F401  (library already loaded)
     prev = oracle_mod.filter_build(a, b, lmin, lmax, damping=damping, maxdeg=k - 1)
     assert prev["reached_max"] and prev["bar"] > 0.8
 
