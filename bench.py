@@ -173,6 +173,28 @@ def whole_job_rate(local_units: float, local_seconds: float, device: str) -> tup
     return total, secs, total / secs
 
 
+def laplacian_count(dim: int, nx: int, a: float, b: float, right_closed: bool) -> int:
+    """Exact number of eigenvalues of the Dirichlet dim-D nx^dim grid Laplacian in [a, b) (or
+    [a, b]): the spectrum is the sum over the axes of 2 - 2 cos(i pi / (nx + 1))."""
+    f = 2.0 - 2.0 * np.cos(np.arange(1, nx + 1) * np.pi / (nx + 1))
+    e = f[:, None] + f[None, :] if dim == 2 else (f[:, None, None] + f[None, :, None] + f[None, None, :])
+    e = e.ravel()
+    return int(np.count_nonzero((e >= a) & ((e <= b) if right_closed else (e < b))))
+
+
+def check_counts(recs, dim: int, nx: int, nslices: int):
+    """Every timed slice must return exactly the closed-form count of its slice (half-open
+    except the last); a wrong count makes the benchmark fail instead of reporting a rate."""
+    bad = []
+    for r in recs:
+        want = laplacian_count(dim, nx, r["a"], r["b"], r["slice"] == nslices - 1)
+        r["exact"] = want
+        if r["nev"] != want:
+            bad.append((r["slice"], r["nev"], want))
+    if bad:
+        raise RuntimeError(f"eigenvalue counts differ from the closed form (slice, found, exact): {bad}")
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -268,6 +290,7 @@ def run_ours(args):
         step += 1
     barrier()
     e2e_total, e2e_s, _ = whole_job_rate(float(sum(r["nev"] for r in e2e_recs)), time.perf_counter() - t0, "cuda")
+    check_counts(recs + e2e_recs, 3, 100, NSLICES)
     h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.val.nbytes
     d2h = float(np.mean([r["nev"] * n * 8 for r in e2e_recs]))
 

@@ -158,22 +158,27 @@ int evsl_filter_apply_multi(evsl_ctx *ctx, int npol, const evsl_polfilt *pols, c
                             double *Y, evsl_precision prec);
 
 /* Allocation-free form of evsl_filter_apply (the paper has no counterpart).  For callers that
- * must not allocate device memory once set up: code recording into a CUDA stream capture
- * (cudaMalloc is not allowed while a capture is in progress), real-time or embedded loops
- * that forbid allocation after initialisation, and hosts whose device memory is owned by
- * another allocator.  Same operation, arguments and layout as evsl_filter_apply with
- * prec = EVSL_FP64: Y = rho(Ahat) X on nvec columns, X and Y device pointers (n x nvec,
- * column-major, non-overlapping), matrix from the context.  The two recurrence temporaries
- * live in one fixed device array of 2 * EVSL_NOALLOC_MAX_ELEMS doubles (32 MiB) that this
- * library reserves on every GPU where its kernels are loaded, until the process exits; this
- * call allocates nothing (no cudaMalloc/cudaFree, no workspace growth, no event creation).
- * Its first call on a device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Every call shares the array: calls that
- * can overlap on the GPU (several contexts or threads on one device) race and must be
- * serialised by the caller.  The array keeps the previous call's contents; nothing in it has
- * to start at zero, because each temporary entry is written before it is read.  The call is
- * synchronous.  Errors: EVSL_ERR_ARG if n * nvec > EVSL_NOALLOC_MAX_ELEMS (the message names
- * the limit), EVSL_ERR_STATE without a matrix, EVSL_ERR_CUDA if the address lookup fails. */
+ * must not allocate device memory once set up: hosts whose device memory belongs to another
+ * allocator (a framework's caching pool that owns the GPU, so a cudaMalloc by this library
+ * would fail or fragment that pool), and real-time or embedded loops that forbid allocation
+ * after initialisation because cudaMalloc/cudaFree can block and synchronise the device.
+ * Same operation, arguments and layout as evsl_filter_apply with prec = EVSL_FP64:
+ * Y = rho(Ahat) X on nvec columns, X and Y device pointers (n x nvec, column-major,
+ * non-overlapping), matrix from the context.  The two recurrence temporaries live in one fixed
+ * device array of 2 * EVSL_NOALLOC_MAX_ELEMS doubles (32 MiB) that this library reserves on
+ * every GPU where its kernels are loaded, until the process exits; this call allocates nothing
+ * (no cudaMalloc/cudaFree, no workspace growth, no event creation).  Its first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current and keeps
+ * it for the life of the process; the kept address is valid only until the device is reset
+ * (cudaDeviceReset), after which this entry point must not be used in the same process.  Every
+ * call shares the array: calls that can overlap on the GPU (several contexts or threads on one
+ * device) race and must be serialised by the caller.  The array keeps the previous call's
+ * contents; nothing in it has to start at zero, because each temporary entry is written before
+ * it is read.  The call is synchronous: it waits on the context's stream for its kernels to
+ * finish before it returns.  It makes the context's device current while it runs and restores
+ * the calling thread's previous current device before returning.  Errors: EVSL_ERR_ARG if
+ * n * nvec > EVSL_NOALLOC_MAX_ELEMS (the message names the limit), EVSL_ERR_STATE without a
+ * matrix, EVSL_ERR_CUDA if the address lookup fails. */
 #define EVSL_NOALLOC_MAX_ELEMS (1 << 21)
 int evsl_filter_apply_noalloc(evsl_ctx *ctx, const evsl_polfilt *pol, int nvec, const double *X,
                               double *Y);
@@ -420,6 +425,17 @@ typedef enum {
 } evsl_kernel_family;
 
 int64_t evsl_launch_count(const evsl_ctx *ctx);
+/* Device memory accounting (no counterpart in the paper; the paper notes that memory grows
+ * with the number of eigenvalues a slice holds, Sec. 4.2, which is what admission must bound).
+ * evsl_set_device_budget caps the device memory held by ALL of this library's contexts on CUDA
+ * device `device` together (0 = no cap, the default): an allocation by any of them that would
+ * pass it fails with EVSL_ERR_NOMEM, and evsl_batch_add refuses a job whose bases and step
+ * workspaces would not fit.  It is checked in addition to each context's own budget; lowering it
+ * frees nothing.  EVSL_ERR_ARG for a device ordinal outside [0, 64).  evsl_device_used: bytes
+ * held by the library's contexts on that device; evsl_mem_used: bytes held by one context. */
+int evsl_set_device_budget(int device, size_t bytes);
+size_t evsl_device_used(int device);
+size_t evsl_mem_used(const evsl_ctx *ctx);
 /* evsl_set_graphs: 1 (the default) lets single-vector filter applications replay cached CUDA
  * graphs; 0 drops the cached graphs and makes every application launch its kernels directly.
  * Both give bitwise the same results. */

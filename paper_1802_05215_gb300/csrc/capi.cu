@@ -1,5 +1,6 @@
 // C ABI entry points (include/evsl_gb300.h) and context services: error reporting, the
 // HBM budget, grow-only workspaces and event-based kernel timing.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -32,6 +33,18 @@ int check_launch(evsl_ctx *c, const char *what)
     return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, what);
 }
 
+// Device-wide accounting: the bytes held by all contexts on one device, and an optional cap on
+// them shared by those contexts (evsl_set_device_budget).
+namespace {
+constexpr int DEV_SLOTS = 64;
+std::atomic<size_t> g_dev_budget[DEV_SLOTS];
+std::atomic<size_t> g_dev_used[DEV_SLOTS];
+inline bool dev_slot_ok(int d) { return d >= 0 && d < DEV_SLOTS; }
+}  // namespace
+
+size_t dev_budget_bytes(int device) { return dev_slot_ok(device) ? g_dev_budget[device].load() : 0; }
+size_t dev_used_bytes(int device) { return dev_slot_ok(device) ? g_dev_used[device].load() : 0; }
+
 int ctx_alloc(evsl_ctx *c, void **p, size_t bytes)
 {
     *p = nullptr;
@@ -39,10 +52,22 @@ int ctx_alloc(evsl_ctx *c, void **p, size_t bytes)
     if (c->budget && c->used + bytes > c->budget)
         return ctx_fail(c, EVSL_ERR_NOMEM, "HBM budget exceeded (%zu + %zu > %zu bytes)", c->used,
                         bytes, c->budget);
+    const bool slot = dev_slot_ok(c->device);
+    if (slot) {
+        // reserve the bytes against the device-wide budget before allocating
+        const size_t cap = g_dev_budget[c->device].load();
+        size_t cur = g_dev_used[c->device].load();
+        do {
+            if (cap && cur + bytes > cap)
+                return ctx_fail(c, EVSL_ERR_NOMEM, "device HBM budget exceeded (%zu + %zu > %zu bytes)", cur,
+                                bytes, cap);
+        } while (!g_dev_used[c->device].compare_exchange_weak(cur, cur + bytes));
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
+        if (slot) g_dev_used[c->device] -= bytes;
         return ctx_fail(c, EVSL_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
     c->used += bytes;
@@ -54,6 +79,7 @@ void ctx_free(evsl_ctx *c, void *p, size_t bytes)
     if (!p) return;
     cudaFree(p);
     c->used -= std::min(c->used, bytes);
+    if (dev_slot_ok(c->device)) g_dev_used[c->device] -= bytes;
 }
 
 // Grow-only workspace: the returned buffer holds at least `bytes`; growing discards contents.
@@ -384,6 +410,17 @@ void evsl_batch_destroy(evsl_batch *batch)
 }
 
 int64_t evsl_launch_count(const evsl_ctx *c) { return c ? c->launches : 0; }
+
+int evsl_set_device_budget(int device, size_t bytes)
+{
+    if (!dev_slot_ok(device)) return EVSL_ERR_ARG;
+    g_dev_budget[device] = bytes;
+    return EVSL_OK;
+}
+
+size_t evsl_device_used(int device) { return dev_used_bytes(device); }
+
+size_t evsl_mem_used(const evsl_ctx *c) { return c ? c->used : 0; }
 
 int evsl_profile(evsl_ctx *c, int enable)
 {

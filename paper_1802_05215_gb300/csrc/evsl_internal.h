@@ -109,6 +109,9 @@ int ctx_cuda(evsl_ctx *c, cudaError_t e, const char *what);
 void *ctx_ws(evsl_ctx *c, int slot, size_t bytes, int *status);
 int ctx_alloc(evsl_ctx *c, void **p, size_t bytes);
 void ctx_free(evsl_ctx *c, void *p, size_t bytes);
+// device-wide budget (0 = none) and the bytes all contexts hold on a device
+size_t dev_budget_bytes(int device);
+size_t dev_used_bytes(int device);
 // profiling: begin/end a group of `launches` launches of one kernel family
 void prof_begin(evsl_ctx *c, int family, ProfGroup *g);
 void prof_end(evsl_ctx *c, ProfGroup *g, int launches);

@@ -112,8 +112,11 @@ __device__ __forceinline__ void cheb_epilogue(int64_t o, T acc, T xr, const T *x
 template <int MODE, bool HAT>
 constexpr bool needs_xr() { return MODE == 0 || (MODE == 1 && !HAT); }
 
-// Single vector: each nonzero is used once, so nothing is cached in registers; the loop is
-// unrolled so that several index loads and gathers are in flight per warp.
+// Single vector: each nonzero is used once.  For slices up to WREG entries wide every index
+// and value load of the row is issued first, then every gather, so one memory latency of each
+// kind is exposed per row instead of one per unrolled group; the row's own operands of the
+// recurrence (x, w_{j-1}, y) are loaded up front as well.  The FMAs run in the same order as in
+// the block kernel, so both give bitwise the same column.
 template <typename T, int MODE, bool HAT>
 __global__ void __launch_bounds__(TPB)
 k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
@@ -127,11 +130,47 @@ k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
     int w = (int)((sptr[s + 1] - b0) >> 5);
     const T *vp = val + b0 + lane;
     const int32_t *cp = col + b0 + lane;
+    const int64_t r = s * 32 + lane;
+    const bool live = r < n;
     T acc = T(0);
+    if (w <= WREG) {
+        int c[WREG];
+        T v[WREG], xv[WREG];
+#pragma unroll
+        for (int j = 0; j < WREG; j++)
+            if (j < w) {
+                c[j] = cp[32 * j];
+                v[j] = vp[32 * j];
+            }
+        const T xr = (live && needs_xr<MODE, HAT>()) ? x[r] : T(0);
+        const T xp = (live && MODE == 1) ? xprev[r] : T(0);
+        const T yo = (live && MODE == 1) ? y[r] : T(0);
+#pragma unroll
+        for (int j = 0; j < WREG; j++)
+            if (j < w) xv[j] = __ldg(x + c[j]);
+#pragma unroll
+        for (int j = 0; j < WREG; j++)
+            if (j < w) acc = fma_r(v[j], xv[j], acc);
+        if (live) {
+            T wv;
+            if (HAT)
+                wv = (MODE == 0) ? mul_r(T(0.5), acc) : sub_r(acc, xp);
+            else {
+                wv = mul_r(fma_r(-cc, xr, acc), sc);
+                if (MODE == 1) wv = sub_r(wv, xp);
+            }
+            if (MODE == 2) {
+                out[r] = acc;
+            } else {
+                out[r] = wv;
+                y[r] = (MODE == 0) ? fma_r(cj, wv, mul_r(c0, xr)) : fma_r(cj, wv, yo);
+            }
+        }
+        return;
+    }
 #pragma unroll 4
     for (int j = 0; j < w; j++) acc = fma_r(vp[32 * j], __ldg(x + cp[32 * j]), acc);
-    int64_t r = s * 32 + lane;
-    if (r < n)
+    if (live)
         cheb_epilogue<T, MODE, HAT>(r, acc, needs_xr<MODE, HAT>() ? x[r] : T(0), xprev, out, y, cc, sc, c0, cj);
 }
 
@@ -232,12 +271,56 @@ template <> struct VecN<float, 4> { using type = float4; };
 // PPL consecutive probes with one vector load (64 probes per pass), so a row takes 64 / PPL
 // lanes and a warp works on 32 PPL / 64 rows at a time (FP64: PPL = 2, one row; FP32:
 // PPL = 4, two rows), and every gathered neighbour row of the block is one coalesced load.
+// The slice's matrix entries are loaded once per slice, one row per lane (coalesced, all in
+// flight together), and handed to the lanes working on a row by warp shuffles, so the row loop
+// waits only on the neighbour gathers; two row groups are processed per iteration to keep twice
+// the gathers in flight.  Slices wider than WREG entries per row read their entries directly.
 // Grid-stride over slices with a fixed grid so that the partials of one step fill exactly
-// part[0..gridDim.x).  Each lane sums its share of one slice in the block's precision and adds
-// it to an FP64 partial, so the sums across slices are FP64 in both precisions (FP64 issue is
-// 1/64 of FP32 here).
+// part[0..gridDim.x).  Each lane sums its share of one slice in the block's precision, row by
+// row in ascending order, and adds it to an FP64 partial, so the sums across slices are FP64 in
+// both precisions (FP64 issue is 1/64 of FP32 here).
 // DBL (the moment-doubling form): instead of the probe-weighted sum the step accumulates
 // sum out.x_row (w_{k+1}^T w_k, into part) and sum out.out (||w_{k+1}||^2, into part2).
+template <typename T, bool HAT, int PPL, bool DBL>
+__device__ __forceinline__ void kpm_row_epilogue(int mode, int64_t r, int l, int nvec, int ld, int nw,
+                                                 const uint32_t *__restrict__ bits, const T *__restrict__ x,
+                                                 const T *xprev, T *out, T cc, T sc, const T (&a)[PPL],
+                                                 T &smom, T &smom2)
+{
+    using VL = typename VecN<T, PPL>::type;
+    const int64_t o = r * ld + l;
+    T w[PPL], pv[PPL];
+    if (mode == 1) *reinterpret_cast<VL *>(pv) = *reinterpret_cast<const VL *>(xprev + o);
+    if (HAT) {
+#pragma unroll
+        for (int q = 0; q < PPL; q++) w[q] = (mode == 1) ? a[q] - pv[q] : T(0.5) * a[q];
+    } else {
+        T xo[PPL];
+        *reinterpret_cast<VL *>(xo) = *reinterpret_cast<const VL *>(x + o);
+#pragma unroll
+        for (int q = 0; q < PPL; q++) {
+            w[q] = (a[q] - cc * xo[q]) * sc;
+            if (mode == 1) w[q] -= pv[q];
+        }
+    }
+    *reinterpret_cast<VL *>(out + o) = *reinterpret_cast<const VL *>(w);
+    if (DBL) {
+        T xr[PPL];
+        *reinterpret_cast<VL *>(xr) = *reinterpret_cast<const VL *>(x + o);
+#pragma unroll
+        for (int q = 0; q < PPL; q++) {
+            smom += w[q] * xr[q];     // padding probes are zero on both sides
+            smom2 += w[q] * w[q];
+        }
+    } else {
+        const uint32_t word = bits[r * nw + (l >> 5)];
+        const int b = l & 31;
+#pragma unroll
+        for (int q = 0; q < PPL; q++)
+            if (l + q < nvec) smom += ((word >> (b + q)) & 1u) ? -w[q] : w[q];
+    }
+}
+
 template <typename T, bool HAT, int PPL, bool DBL>
 __global__ void __launch_bounds__(TPB, 4)
 k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
@@ -257,32 +340,69 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
     double mom = 0.0, mom2 = 0.0;
     for (int64_t s = warp; s < nslices; s += nwarps) {
         const int64_t sbase = sptr[s];
+        const int w = (int)((sptr[s + 1] - sbase) >> 5);
         T smom = T(0), smom2 = T(0);  // this lane's share of the slice, in the block's precision
-        for (int rr0 = 0; rr0 < 32; rr0 += RPI) {
-            const int rr = rr0 + rsub;
-            const int64_t r = s * 32 + rr;
-            const int len = (r < n) ? rlen[r] : 0;
-            for (int l0 = 0; l0 < nvec; l0 += 64) {
-                const int l = l0 + PPL * sub;
-                const bool act = (r < n) && (l < nvec);
-                T a[PPL];
+        // FP32 with mapped values only: the FP64 step is bound by the FP64 pipe, and the staged
+        // entries would not fit the register budget of the other variants
+        if (sizeof(T) == 4 && HAT && w <= WREG) {
+            // lane t holds row 32 s + t of the slice: its entries, columns and length
+            const int64_t rl = s * 32 + lane;
+            const int mylen = (rl < n) ? rlen[rl] : 0;
+            T mv[WREG];
+            int mc[WREG];
 #pragma unroll
-                for (int q = 0; q < PPL; q++) a[q] = T(0);
-                if (len <= WREG) {
+            for (int j = 0; j < WREG; j++) {
+                mv[j] = (j < w) ? val[sbase + 32 * (int64_t)j + lane] : T(0);
+                mc[j] = (j < w) ? col[sbase + 32 * (int64_t)j + lane] : 0;
+            }
+            for (int rr0 = 0; rr0 < 32; rr0 += 2 * RPI) {
+                const int rA = rr0 + rsub, rB = rr0 + RPI + rsub;
+                const int64_t gA = s * 32 + rA, gB = s * 32 + rB;
+                const int lenA = __shfl_sync(0xffffffffu, mylen, rA);
+                const int lenB = __shfl_sync(0xffffffffu, mylen, rB);
+                for (int l0 = 0; l0 < nvec; l0 += 64) {
+                    const int l = l0 + PPL * sub;
+                    const bool actA = (gA < n) && (l < nvec), actB = (gB < n) && (l < nvec);
+                    T aA[PPL], aB[PPL];
+#pragma unroll
+                    for (int q = 0; q < PPL; q++) aA[q] = aB[q] = T(0);
 #pragma unroll
                     for (int j = 0; j < WREG; j++)
-                        if (j < len) {
-                            const int64_t e = sbase + 32 * (int64_t)j + rr;
-                            const T v = val[e];
-                            const int cj = col[e];
-                            if (act) {
-                                T xv[PPL];
-                                *reinterpret_cast<VL *>(xv) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cj * ld + l));
+                        if (j < w) {
+                            const T vA = __shfl_sync(0xffffffffu, mv[j], rA);
+                            const int cA = __shfl_sync(0xffffffffu, mc[j], rA);
+                            const T vB = __shfl_sync(0xffffffffu, mv[j], rB);
+                            const int cB = __shfl_sync(0xffffffffu, mc[j], rB);
+                            T xa[PPL], xb[PPL];
+                            const bool ua = actA && j < lenA, ub = actB && j < lenB;
+                            if (ua) *reinterpret_cast<VL *>(xa) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cA * ld + l));
+                            if (ub) *reinterpret_cast<VL *>(xb) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cB * ld + l));
+                            if (ua)
 #pragma unroll
-                                for (int q = 0; q < PPL; q++) a[q] += v * xv[q];
-                            }
+                                for (int q = 0; q < PPL; q++) aA[q] += vA * xa[q];
+                            if (ub)
+#pragma unroll
+                                for (int q = 0; q < PPL; q++) aB[q] += vB * xb[q];
                         }
-                } else {
+                    if (actA)
+                        kpm_row_epilogue<T, HAT, PPL, DBL>(mode, gA, l, nvec, ld, nw, bits, x, xprev, out, cc, sc, aA,
+                                                          smom, smom2);
+                    if (actB)
+                        kpm_row_epilogue<T, HAT, PPL, DBL>(mode, gB, l, nvec, ld, nw, bits, x, xprev, out, cc, sc, aB,
+                                                          smom, smom2);
+                }
+            }
+        } else {
+            for (int rr0 = 0; rr0 < 32; rr0 += RPI) {
+                const int rr = rr0 + rsub;
+                const int64_t r = s * 32 + rr;
+                const int len = (r < n) ? rlen[r] : 0;
+                for (int l0 = 0; l0 < nvec; l0 += 64) {
+                    const int l = l0 + PPL * sub;
+                    const bool act = (r < n) && (l < nvec);
+                    T a[PPL];
+#pragma unroll
+                    for (int q = 0; q < PPL; q++) a[q] = T(0);
                     for (int j = 0; j < len; j++) {
                         const int64_t e = sbase + 32 * (int64_t)j + rr;
                         const T v = val[e];
@@ -294,39 +414,9 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                             for (int q = 0; q < PPL; q++) a[q] += v * xv[q];
                         }
                     }
-                }
-                if (act) {
-                    const int64_t o = r * ld + l;
-                    T w[PPL], pv[PPL];
-                    if (mode == 1) *reinterpret_cast<VL *>(pv) = *reinterpret_cast<const VL *>(xprev + o);
-                    if (HAT) {
-#pragma unroll
-                        for (int q = 0; q < PPL; q++) w[q] = (mode == 1) ? a[q] - pv[q] : T(0.5) * a[q];
-                    } else {
-                        T xo[PPL];
-                        *reinterpret_cast<VL *>(xo) = *reinterpret_cast<const VL *>(x + o);
-#pragma unroll
-                        for (int q = 0; q < PPL; q++) {
-                            w[q] = (a[q] - cc * xo[q]) * sc;
-                            if (mode == 1) w[q] -= pv[q];
-                        }
-                    }
-                    *reinterpret_cast<VL *>(out + o) = *reinterpret_cast<const VL *>(w);
-                    if (DBL) {
-                        T xr[PPL];
-                        *reinterpret_cast<VL *>(xr) = *reinterpret_cast<const VL *>(x + o);
-#pragma unroll
-                        for (int q = 0; q < PPL; q++) {
-                            smom += w[q] * xr[q];     // padding probes are zero on both sides
-                            smom2 += w[q] * w[q];
-                        }
-                    } else {
-                        const uint32_t word = bits[r * nw + (l >> 5)];
-                        const int b = l & 31;
-#pragma unroll
-                        for (int q = 0; q < PPL; q++)
-                            if (l + q < nvec) smom += ((word >> (b + q)) & 1u) ? -w[q] : w[q];
-                    }
+                    if (act)
+                        kpm_row_epilogue<T, HAT, PPL, DBL>(mode, r, l, nvec, ld, nw, bits, x, xprev, out, cc, sc, a,
+                                                          smom, smom2);
                 }
             }
         }
@@ -948,7 +1038,15 @@ extern "C" int evsl_filter_apply_noalloc(evsl_ctx *c, const evsl_polfilt *pol, i
                         (long long)N, EVSL_NOALLOC_MAX_ELEMS);
     if (c->device < 0 || c->device >= NOALLOC_MAX_DEVICES)
         return ctx_fail(c, EVSL_ERR_ARG, "filter_apply_noalloc: device ordinal %d not supported", c->device);
-    cudaError_t e = cudaSetDevice(c->device);
+    // the caller's current device is put back on every return path
+    int prev_dev = -1;
+    cudaError_t e = cudaGetDevice(&prev_dev);
+    if (e != cudaSuccess) return ctx_cuda(c, e, "filter_apply_noalloc get device");
+    struct DeviceRestore {
+        int dev;
+        ~DeviceRestore() { cudaSetDevice(dev); }
+    } restore{prev_dev};
+    e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return ctx_cuda(c, e, "filter_apply_noalloc set device");
     double *scratch = nullptr;
     {

@@ -1232,6 +1232,11 @@ int batch_add(evsl_batch *bt, evsl_slice_job *job)
     if (c->budget && c->used + need + bases > c->budget)
         return ctx_fail(c, EVSL_ERR_NOMEM, "batch_add: HBM budget has no room for the job (%zu + %zu + %zu > %zu bytes)",
                         c->used, bases, need, c->budget);
+    const size_t dcap = dev_budget_bytes(c->device), dused = dev_used_bytes(c->device);
+    if (dcap && dused + need + bases > dcap)
+        return ctx_fail(c, EVSL_ERR_NOMEM,
+                        "batch_add: device HBM budget has no room for the job (%zu + %zu + %zu > %zu bytes)", dused,
+                        bases, need, dcap);
     std::unique_ptr<SliceSolver> s(new SliceSolver(c, job->a, job->b, job->pol, bt->o, job->m, job->cap,
                                                    job->right_closed != 0));
     int rc = s->init();

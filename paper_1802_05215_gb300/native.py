@@ -115,6 +115,9 @@ def load(build_if_missing: bool = True):
         "evsl_chebLanNr_gen": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_chebLanTr_gen": (i32, [P, d, d, P, P, i32, P, P, P, P, P]),
         "evsl_launch_count": (i64, [P]),
+        "evsl_set_device_budget": (i32, [i32, sz]),
+        "evsl_device_used": (sz, [i32]),
+        "evsl_mem_used": (sz, [P]),
         "evsl_set_graphs": (i32, [P, i32]),
         "evsl_profile": (i32, [P, i32]),
         "evsl_profile_get": (i32, [P, i32, P, P]),
@@ -216,6 +219,18 @@ def slice_by_dos(mu, n, lmin, lmax, xi, eta, nslices, npts=0):
     if st != EVSL_OK:
         raise EvslError(st, "slice_by_dos")
     return sli, est
+
+
+def set_device_budget(device: int, nbytes: int):
+    """Cap the device memory held by all contexts on `device` together (0 = no cap)."""
+    st = load().evsl_set_device_budget(device, nbytes)
+    if st != EVSL_OK:
+        raise EvslError(st, f"set_device_budget({device})")
+
+
+def device_used(device: int) -> int:
+    """Bytes held by the library's contexts on `device`."""
+    return int(load().evsl_device_used(device))
 
 
 class Context:
@@ -480,6 +495,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.lib.evsl_launch_count(self.h))
+
+    def mem_used(self) -> int:
+        """Device bytes this context holds."""
+        return int(self.lib.evsl_mem_used(self.h))
 
     def profile(self, enable: bool):
         self._check(self.lib.evsl_profile(self.h, int(enable)), "profile")

@@ -4,7 +4,6 @@
     python -m paper_1802_05215_gb300.profile_cases gemv      # Gram-Schmidt GEMV-T / GEMV-N
     python -m paper_1802_05215_gb300.profile_cases kpm       # KPM moment step, FP64 then FP32
     python -m paper_1802_05215_gb300.profile_cases multi     # 16-slice batched filter step, FP32
-    python -m paper_1802_05215_gb300.profile_cases fp64rate  # dense FP64 vs FP32 GEMM rate (cuBLAS)
     python -m paper_1802_05215_gb300.profile_cases gen       # generalized step: solves with p(B)
 
 Each case but `gen` runs on the 100^3 7-point Laplacian (n = 1e6, nnz = 6.94e6); `gen` uses the
@@ -69,28 +68,6 @@ def multi():
     return ctx
 
 
-def fp64rate():
-    """Dense GEMM rate of the part in FP64 and FP32 (library GEMMs, CUDA-event timed): the
-    ceiling that bounds every FP64 kernel of the solver.  Prints one line per precision."""
-    import torch
-    n = 8192
-    for dt in (torch.float64, torch.float32):
-        a = torch.randn(n, n, dtype=dt, device="cuda")
-        b = torch.randn(n, n, dtype=dt, device="cuda")
-        for _ in range(3):
-            torch.matmul(a, b)
-        reps = 10 if dt == torch.float64 else 50
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            torch.matmul(a, b)
-        e1.record()
-        torch.cuda.synchronize()
-        s = e0.elapsed_time(e1) * 1e-3 / reps
-        print(f"{str(dt).split('.')[-1]} GEMM {n}^3: {s * 1e3:.2f} ms = {2 * n ** 3 / s / 1e12:.2f} TFLOP/s")
-    return None
-
-
 def gen():
     """Two solves y = p(B) x with the lsPol polynomial on [0.11, 1] (which holds the spectrum of
     the 1000^2 mass matrix M (x) M, M = tridiag(1, 4, 1)/6): 2 x deg(p) launches of k_gen_step,
@@ -109,7 +86,7 @@ def gen():
     return ctx
 
 
-CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "fp64rate": fp64rate, "gen": gen}
+CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "gen": gen}
 
 if __name__ == "__main__":
     name = sys.argv[1] if len(sys.argv) > 1 else "cheb"

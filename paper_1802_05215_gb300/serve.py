@@ -1,18 +1,24 @@
 """Serving of slice solves with continuous batching (requests = (matrix, interval) pairs).
 
 A Server keeps every matrix it has seen resident on the GPU (one context per matrix, CSR
-uploaded once) and runs one continuous batch per matrix: a request is admitted into its
-matrix's batch as soon as the HBM budget has room for its Lanczos bases, all admitted jobs of a
-matrix advance together (one multi-slice filter pass per degree per step), and a job leaves the
-batch the step it finishes.  The plain mode runs the same requests one at a time in arrival
-order with the FP64 filter, for comparison.
+uploaded once, each context on its own CUDA stream) and runs one continuous batch per matrix in
+a worker thread of its own.  Admission is decided against ONE GPU-wide HBM budget shared by all
+the matrices' contexts (evsl_set_device_budget): a request joins its matrix's batch as soon as
+the device has room for its Lanczos bases and step workspaces.  All admitted jobs of a matrix
+advance together (one multi-slice filter pass per degree per step), a job leaves the batch the
+step it finishes, and the batches of different matrices run concurrently on their own streams
+(the library's calls release the interpreter lock, so the workers' kernels overlap on the
+device).  A request that cannot fit even when no job is running anywhere is refused with
+EVSL_ERR_NOMEM in its outcome instead of waiting forever.  The plain mode runs the same
+requests one at a time in arrival order with the FP64 filter, for comparison.
 
 Every request is one slice: its filter is built for [a, b] on the matrix's spectral bounds, and
-its Krylov dimension comes from the KPM estimate of the count in [a, b].
+its Krylov dimension comes from the estimated count in [a, b].
 """
 from __future__ import annotations
 
 import dataclasses
+import threading
 import time
 
 import numpy as np
@@ -28,6 +34,7 @@ class Request:
     a: float
     b: float
     est: float              # estimated eigenvalue count (DOS)
+    right_closed: bool = True
 
 
 @dataclasses.dataclass
@@ -39,6 +46,8 @@ class Outcome:
     nev: int
     res_max: float
     lam: np.ndarray
+    status: int = 0
+    Y: np.ndarray | None = None   # eigenvectors (rows), kept when the run asks for them
 
     @property
     def latency(self):
@@ -50,10 +59,10 @@ def krylov_dim(est: float) -> int:
 
 
 class ResidentMatrix:
-    def __init__(self, key: str, A: inputs.CSR, device: int, budget: int, bounds_steps=80):
+    def __init__(self, key: str, A: inputs.CSR, device: int, bounds_steps=80):
         self.key = key
         self.A = A
-        self.ctx = native.Context(device, budget)
+        self.ctx = native.Context(device)
         self.ctx.set_csr(A)
         self.lmin, self.lmax = self.ctx.bounds(bounds_steps, 0)
         self.batch = None
@@ -68,12 +77,13 @@ class ResidentMatrix:
 
 
 class Server:
-    """Continuous-batching server over resident matrices (one GPU)."""
+    """Continuous-batching server over resident matrices (one GPU, one HBM budget)."""
 
-    def __init__(self, matrices: dict, device: int = 0, hbm_budget_per_matrix: int = 0,
+    def __init__(self, matrices: dict, device: int = 0, hbm_budget: int = 0,
                  prec=native.FP32, tol=1e-8):
-        self.mats = {k: ResidentMatrix(k, A, device, hbm_budget_per_matrix)
-                     for k, A in matrices.items()}
+        self.device = device
+        self.mats = {k: ResidentMatrix(k, A, device) for k, A in matrices.items()}
+        self.hbm_budget = hbm_budget
         self.prec = prec
         self.tol = tol
 
@@ -81,17 +91,23 @@ class Server:
         for m in self.mats.values():
             m.close()
 
-    def run(self, requests: list[Request], batched: bool = True, prec=None) -> list[Outcome]:
-        """Serve the requests against the wall clock; returns one outcome per request.
-        prec: filter precision of the batched mode (default: the server's)."""
+    def run(self, requests: list[Request], batched: bool = True, prec=None,
+            keep_vectors: bool = False) -> list[Outcome]:
+        """Serve the requests against the wall clock; returns one outcome per request, in the
+        order given.  prec: filter precision of the batched mode (default: the server's).
+        keep_vectors: store each result's eigenvectors (host rows) in its outcome."""
         prec = self.prec if prec is None else prec
         pending = sorted(requests, key=lambda r: r.arrival)
-        queue: list[Request] = []
         out: dict[int, Outcome] = {}
-        started: dict[int, float] = {}
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
-        i = 0
+
+        def outcome(r, start, res):
+            nev = res["nev"]
+            return Outcome(r.rid, r.arrival, start, now(), nev,
+                           float(res["res"].max()) if nev else 0.0, res["lam"], res["status"],
+                           np.array(res["Y"][:nev]) if keep_vectors else None)
+
         if not batched:
             for r in pending:
                 while now() < r.arrival:
@@ -100,44 +116,100 @@ class Server:
                 f = M.filter(r.a, r.b)
                 st = now()
                 res = M.ctx.chebLanTr(r.a, r.b, f, m=krylov_dim(r.est), tol=self.tol,
-                                      prec=native.FP64, allow_partial=True)
-                out[r.rid] = Outcome(r.rid, r.arrival, st, now(), res["nev"],
-                                     float(res["res"].max()) if res["nev"] else 0.0, res["lam"])
+                                      prec=native.FP64, right_closed=r.right_closed,
+                                      allow_partial=True)
+                out[r.rid] = outcome(r, st, res)
             return [out[r.rid] for r in requests]
+
+        native.set_device_budget(self.device, self.hbm_budget)
+        lock = threading.Condition()
+        queues: dict[str, list[Request]] = {k: [] for k in self.mats}
+        active = {k: 0 for k in self.mats}        # admitted, unfinished jobs per matrix
+        remaining = [len(requests)]
+        errors: list[BaseException] = []
         for M in self.mats.values():
             M.batch = native.Batch(M.ctx, tol=self.tol, prec=prec)
-        while len(out) < len(requests):
-            t = now()
-            while i < len(pending) and pending[i].arrival <= t:
-                queue.append(pending[i])
-                i += 1
-            # admission in arrival order, as HBM allows (a refused job waits in the queue)
-            still = []
-            for r in queue:
-                M = self.mats[r.matrix]
-                try:
-                    M.batch.add(r.a, r.b, M.filter(r.a, r.b), krylov_dim(r.est), tag=r.rid)
-                    started[r.rid] = now()
-                except native.EvslError as e:
-                    if e.code != -2:
-                        raise
-                    still.append(r)
-            queue = still
-            busy = False
-            for M in self.mats.values():
-                if M.batch.active:
-                    busy = True
+
+        def worker(key: str):
+            M = self.mats[key]
+            started: dict[int, float] = {}
+            try:
+                while True:
+                    with lock:
+                        while not queues[key] and active[key] == 0 and remaining[0] > 0 and not errors:
+                            lock.wait(0.05)
+                        if remaining[0] == 0 or errors:
+                            return
+                        admit = list(queues[key])
+                    # admission in arrival order, as the device budget allows
+                    taken = []
+                    for r in admit:
+                        try:
+                            M.batch.add(r.a, r.b, M.filter(r.a, r.b), krylov_dim(r.est),
+                                        right_closed=r.right_closed, tag=r.rid)
+                            started[r.rid] = now()
+                            taken.append(r)
+                        except native.EvslError as e:
+                            if e.code != -2:
+                                raise
+                            with lock:
+                                idle = sum(active.values()) == 0 and not taken and not M.batch.active
+                            if idle:
+                                # nothing runs anywhere and it still does not fit: it never will
+                                with lock:
+                                    out[r.rid] = Outcome(r.rid, r.arrival, now(), now(), 0, 0.0,
+                                                         np.zeros(0), -2, None)
+                                    queues[key].remove(r)
+                                    remaining[0] -= 1
+                                    lock.notify_all()
+                            break             # keep arrival order: later requests wait too
+                    with lock:
+                        for r in taken:
+                            queues[key].remove(r)
+                        active[key] += len(taken)
+                    if not M.batch.active:
+                        with lock:                # queued work that does not fit yet: wait for
+                            lock.wait(0.005)      # another matrix's jobs to free memory
+                        continue
                     for job in M.batch.step():
-                        res = job.result()
                         rq = next(q for q in requests if q.rid == job.tag)
-                        out[job.tag] = Outcome(job.tag, rq.arrival, started[job.tag], now(),
-                                               res["nev"], float(res["res"].max()) if res["nev"] else 0.0,
-                                               res["lam"])
-            if not busy and i < len(pending):
-                time.sleep(max(0.0, min(0.002, pending[i].arrival - now())))
-        for M in self.mats.values():
-            M.batch.close()
-            M.batch = None
+                        oc = outcome(rq, started[job.tag], job.result())
+                        with lock:
+                            out[job.tag] = oc
+                            active[key] -= 1
+                            remaining[0] -= 1
+                            lock.notify_all()
+            except BaseException as e:        # surface the failure in the dispatcher
+                with lock:
+                    errors.append(e)
+                    lock.notify_all()
+
+        threads = [threading.Thread(target=worker, args=(k,), daemon=True) for k in self.mats]
+        for t in threads:
+            t.start()
+        try:
+            i = 0
+            while i < len(pending):
+                wait = pending[i].arrival - now()
+                if wait > 0:
+                    time.sleep(min(wait, 0.002))
+                    continue
+                with lock:
+                    while i < len(pending) and pending[i].arrival <= now():
+                        queues[pending[i].matrix].append(pending[i])
+                        i += 1
+                    lock.notify_all()
+                    if errors:
+                        break
+        finally:
+            for t in threads:
+                t.join()
+            for M in self.mats.values():
+                M.batch.close()
+                M.batch = None
+            native.set_device_budget(self.device, 0)
+        if errors:
+            raise errors[0]
         return [out[r.rid] for r in requests]
 
 

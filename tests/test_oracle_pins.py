@@ -743,7 +743,9 @@ def test_cheblantr_unreachable_tolerance_locks_nothing_unconverged(oracle_mod):
 
 
 def test_empty_slices_run_the_minimum_empty_length(oracle_mod):
-    # reading 14: a slice holding no eigenvalue ends only after max(2 ncycle, m/4) = 50 steps
+    # empty-cycle rule: a test with no Ritz value >= bar counts as stable only after a previous
+    # test of the cycle had none either and the cycle ran max(2 ncycle, m/4) steps, so a slice
+    # holding no eigenvalue ends only after max(2 ncycle, m/4) = 50 steps
     # (m = 200) in which no Ritz value reached bar: one such run for the non-restart solvers,
     # two candidate-free cycles for thick restart; standard and generalized solvers alike
     A, B = I.laplacian_2d(20), I.mass_matrix_2d(20)
