@@ -436,6 +436,24 @@ int64_t evsl_launch_count(const evsl_ctx *ctx);
 int evsl_set_device_budget(int device, size_t bytes);
 size_t evsl_device_used(int device);
 size_t evsl_mem_used(const evsl_ctx *ctx);
+
+/* Dense FP64 products (Algorithm 2's "compute candidate Ritz pairs" step forms Y = Q S; the
+ * Rayleigh-Ritz and Gram projections form W^T Z): C {=, -=, +=} op(A) B for DEVICE column-major
+ * FP64 matrices, op(A) = A (M x K, lda >= M) when trans_a = 0, op(A) = A^T (A is K x M,
+ * lda >= K) when trans_a = 1; B is K x N (ldb >= K); C is M x N (ldc >= M); mode 0 stores,
+ * 1 subtracts, 2 adds.  With the tensor-core path enabled (the default) the product runs on the
+ * BF16 tensor cores by exact digit splitting (Ozaki scheme I: nine 6-bit digits per element
+ * against per-row / per-column power-of-two scales, exact FP32 sums per 448-long chunk, exact
+ * 128-bit integer accumulation across chunks) and is rounded once to FP64: each element is
+ * within about 2^-52 of sum_k |a_ik| |b_kj| of the exact product, and the result does not
+ * depend on the tiling.  The solvers use the same path for their large products
+ * (2 M N K >= 1e9).  evsl_set_tensor_gemm(ctx, 0) switches them (and this call, mode 0 only)
+ * to the plain FP64 kernels.  Synchronous.  Workspace: the digits of at most 2 GiB of operand
+ * panels.  Errors: EVSL_ERR_ARG, EVSL_ERR_NOMEM, EVSL_ERR_TIMEOUT (a bounded wait inside the
+ * kernel's pipeline expired; C is then unspecified). */
+int evsl_dense_gemm(evsl_ctx *ctx, int trans_a, int64_t M, int N, int64_t K, const double *A, int64_t lda,
+                    const double *B, int64_t ldb, double *C, int64_t ldc, int mode);
+int evsl_set_tensor_gemm(evsl_ctx *ctx, int enable);
 /* evsl_set_graphs: 1 (the default) lets single-vector filter applications replay cached CUDA
  * graphs; 0 drops the cached graphs and makes every application launch its kernels directly.
  * Both give bitwise the same results. */

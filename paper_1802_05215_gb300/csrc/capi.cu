@@ -422,6 +422,31 @@ size_t evsl_device_used(int device) { return dev_used_bytes(device); }
 
 size_t evsl_mem_used(const evsl_ctx *c) { return c ? c->used : 0; }
 
+int evsl_set_tensor_gemm(evsl_ctx *c, int enable)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->tc_gemm = enable != 0;
+    return EVSL_OK;
+}
+
+int evsl_dense_gemm(evsl_ctx *c, int trans_a, int64_t M, int N, int64_t K, const double *A, int64_t lda,
+                    const double *B, int64_t ldb, double *C, int64_t ldc, int mode)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (M < 0 || N < 0 || K < 0 || mode < 0 || mode > 2 || (M > 0 && N > 0 && (!C || ldc < M)) ||
+        (M > 0 && N > 0 && K > 0 && (!A || !B || ldb < K || lda < (trans_a ? K : M))))
+        return ctx_fail(c, EVSL_ERR_ARG, "dense_gemm: bad arguments");
+    cudaSetDevice(c->device);
+    int st = c->tc_gemm ? gemm_tc(c, trans_a != 0, M, N, K, A, lda, B, ldb, C, ldc, mode)
+                        : (mode == 0 ? (trans_a ? gemm_tn(c, K, (int)M, N, A, lda, B, ldb, C, ldc)
+                                                : gemm_nn(c, M, N, (int)K, A, lda, B, ldb, C, ldc))
+                                     : ctx_fail(c, EVSL_ERR_ARG, "dense_gemm: modes 1 and 2 need the tensor-core path"));
+    if (st != EVSL_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? EVSL_OK : ctx_cuda(c, e, "dense_gemm");
+}
+
 int evsl_profile(evsl_ctx *c, int enable)
 {
     if (!c) return EVSL_ERR_ARG;

@@ -75,6 +75,7 @@ struct evsl_ctx {
     };
     std::vector<FilterGraph> fgraphs;
     bool graphs_off = false;  // set when capture is not possible on the context's stream
+    bool tc_gemm = true;      // large FP64 GEMMs on the tensor cores (digit splitting)
     // autotuned tile shape of the multi-column filter step, per (n, columns, precision)
     std::map<uint64_t, int> tune;
 };
@@ -100,6 +101,7 @@ enum WsSlot {
     WS_LAN_U, WS_LAN_Q, WS_LAN_Y, WS_LAN_Z, WS_LAN_VEC, WS_LAN_T, WS_LAN_S, WS_LAN_IDX,
     WS_JAC_PAIRS, WS_BIS, WS_TMP_STAGE, WS_LAN_G, WS_POL_V, WS_POL_W, WS_POL_B, WS_POL_S, WS_POL_Y, WS_POL_R, WS_TUNE, WS_POL_H,
     WS_GEN_BASIS, WS_GEN_VEC, WS_GEN_SCAL, WS_GEN_MU,
+    WS_OZ_A, WS_OZ_B, WS_OZ_E, WS_OZ_FLAG,
     WS_COUNT
 };
 
@@ -210,6 +212,11 @@ int gemm_tn(evsl_ctx *c, int64_t n, int p, int q, const double *A, int64_t lda,
 // dst[:, t] = src[:, idx[t]] (columns of length rows), idx device
 int gather_cols(evsl_ctx *c, int64_t rows, int k, const double *src, int64_t lds,
                 const int *idx, double *dst, int64_t ldd);
+// FP64-accurate GEMM on the tensor cores (ozaki_gemm.cu): C (M x N, ldc) {=, -=, +=} op(A) B with
+// op(A) = A (M x K, lda) or A^T (A K x M, lda), B K x N (ldb); mode 0 store, 1 subtract, 2 add.
+// Synchronous (reads back the pipeline's timeout flag).
+int gemm_tc(evsl_ctx *c, bool trans_a, int64_t M, int N, int64_t K, const double *A, int64_t lda, const double *B,
+            int64_t ldb, double *C, int64_t ldc, int mode);
 // Jacobi eigensolver for a dense symmetric m x m matrix (device, col-major, ld m).
 // On return Tm's diagonal holds eigenvalues, V (ld M, M = m rounded to even) the vectors.
 int jacobi_eig(evsl_ctx *c, int m, const double *Tdev_in, double *w_host, double *V, int *ldv,

@@ -112,11 +112,8 @@ __device__ __forceinline__ void cheb_epilogue(int64_t o, T acc, T xr, const T *x
 template <int MODE, bool HAT>
 constexpr bool needs_xr() { return MODE == 0 || (MODE == 1 && !HAT); }
 
-// Single vector: each nonzero is used once.  For slices up to WREG entries wide every index
-// and value load of the row is issued first, then every gather, so one memory latency of each
-// kind is exposed per row instead of one per unrolled group; the row's own operands of the
-// recurrence (x, w_{j-1}, y) are loaded up front as well.  The FMAs run in the same order as in
-// the block kernel, so both give bitwise the same column.
+// Single vector: each nonzero is used once, so nothing is cached in registers; the loop is
+// unrolled so that several index loads and gathers are in flight per warp.
 template <typename T, int MODE, bool HAT>
 __global__ void __launch_bounds__(TPB)
 k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
@@ -130,47 +127,11 @@ k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
     int w = (int)((sptr[s + 1] - b0) >> 5);
     const T *vp = val + b0 + lane;
     const int32_t *cp = col + b0 + lane;
-    const int64_t r = s * 32 + lane;
-    const bool live = r < n;
     T acc = T(0);
-    if (w <= WREG) {
-        int c[WREG];
-        T v[WREG], xv[WREG];
-#pragma unroll
-        for (int j = 0; j < WREG; j++)
-            if (j < w) {
-                c[j] = cp[32 * j];
-                v[j] = vp[32 * j];
-            }
-        const T xr = (live && needs_xr<MODE, HAT>()) ? x[r] : T(0);
-        const T xp = (live && MODE == 1) ? xprev[r] : T(0);
-        const T yo = (live && MODE == 1) ? y[r] : T(0);
-#pragma unroll
-        for (int j = 0; j < WREG; j++)
-            if (j < w) xv[j] = __ldg(x + c[j]);
-#pragma unroll
-        for (int j = 0; j < WREG; j++)
-            if (j < w) acc = fma_r(v[j], xv[j], acc);
-        if (live) {
-            T wv;
-            if (HAT)
-                wv = (MODE == 0) ? mul_r(T(0.5), acc) : sub_r(acc, xp);
-            else {
-                wv = mul_r(fma_r(-cc, xr, acc), sc);
-                if (MODE == 1) wv = sub_r(wv, xp);
-            }
-            if (MODE == 2) {
-                out[r] = acc;
-            } else {
-                out[r] = wv;
-                y[r] = (MODE == 0) ? fma_r(cj, wv, mul_r(c0, xr)) : fma_r(cj, wv, yo);
-            }
-        }
-        return;
-    }
 #pragma unroll 4
     for (int j = 0; j < w; j++) acc = fma_r(vp[32 * j], __ldg(x + cp[32 * j]), acc);
-    if (live)
+    int64_t r = s * 32 + lane;
+    if (r < n)
         cheb_epilogue<T, MODE, HAT>(r, acc, needs_xr<MODE, HAT>() ? x[r] : T(0), xprev, out, y, cc, sc, c0, cj);
 }
 
@@ -321,6 +282,39 @@ __device__ __forceinline__ void kpm_row_epilogue(int mode, int64_t r, int l, int
     }
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Per-warp staging buffer of one slice (slices up to WREG entries wide): entries and columns
+// in the slice's own column-major order, and the 32 row lengths.
+struct KpmStage {
+    float val[WREG * 32];
+    int32_t col[WREG * 32];
+    int32_t len[32];
+};
+
+// Copies slice s's entries (w <= WREG per row, 128 w bytes per array) and row lengths into st
+// with 16-byte asynchronous copies; sptr/val/col/rlen slices are 128-byte aligned.
+__device__ __forceinline__ void kpm_stage_issue(KpmStage &st, int64_t sbase, int w, int64_t s, int lane,
+                                                const float *__restrict__ val, const int32_t *__restrict__ col,
+                                                const int32_t *__restrict__ rlen)
+{
+    const int chunks = 8 * w;  // 16-byte pieces per array
+    for (int c = lane; c < chunks; c += 32) {
+        cp_async16(&st.val[4 * c], val + sbase + 4 * c);
+        cp_async16(&st.col[4 * c], col + sbase + 4 * c);
+    }
+    if (lane < 8) cp_async16(&st.len[4 * lane], rlen + s * 32 + 4 * lane);
+    cp_async_commit();
+}
+
 template <typename T, bool HAT, int PPL, bool DBL>
 __global__ void __launch_bounds__(TPB, 4)
 k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
@@ -331,68 +325,151 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
     using VL = typename VecN<T, PPL>::type;
     constexpr int LPR = 64 / PPL;   // lanes per row
     constexpr int RPI = 32 / LPR;   // rows per warp at a time
-    __shared__ double red[TPB / 32], red2[TPB / 32];
-    const int lane = threadIdx.x & 31;
+    constexpr int WPB = TPB / 32;
+    __shared__ double red[WPB], red2[WPB];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int sub = lane % LPR, rsub = lane / LPR;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nw = (nvec + 31) >> 5;
     double mom = 0.0, mom2 = 0.0;
-    for (int64_t s = warp; s < nslices; s += nwarps) {
-        const int64_t sbase = sptr[s];
-        const int w = (int)((sptr[s + 1] - sbase) >> 5);
-        T smom = T(0), smom2 = T(0);  // this lane's share of the slice, in the block's precision
-        // FP32 with mapped values only: the FP64 step is bound by the FP64 pipe, and the staged
-        // entries would not fit the register budget of the other variants
-        if (sizeof(T) == 4 && HAT && w <= WREG) {
-            // lane t holds row 32 s + t of the slice: its entries, columns and length
-            const int64_t rl = s * 32 + lane;
-            const int mylen = (rl < n) ? rlen[rl] : 0;
-            T mv[WREG];
-            int mc[WREG];
-#pragma unroll
-            for (int j = 0; j < WREG; j++) {
-                mv[j] = (j < w) ? val[sbase + 32 * (int64_t)j + lane] : T(0);
-                mc[j] = (j < w) ? col[sbase + 32 * (int64_t)j + lane] : 0;
+    // FP32 with mapped values: the block owns a contiguous range of slices (neighbour rows it
+    // gathers were mostly read by its own warps a moment earlier, from L1), and each warp stages
+    // its next slice's entries in shared memory while it works on the current one
+    constexpr bool STAGED = (sizeof(T) == 4) && HAT && (PPL == 4);
+    if constexpr (STAGED) {
+        __shared__ __align__(16) KpmStage stage[WPB][2];
+        const int64_t per = (nslices + gridDim.x - 1) / gridDim.x;
+        const int64_t s_begin = (int64_t)blockIdx.x * per, s_end = min(nslices, s_begin + per);
+        int64_t s = s_begin + wib;
+        int buf = 0;
+        // the first slice; a slice wider than WREG is handled directly (flagged by w_cur)
+        int64_t sb_cur = 0;
+        int w_cur = 0;
+        if (s < s_end) {
+            sb_cur = sptr[s];
+            w_cur = (int)((sptr[s + 1] - sb_cur) >> 5);
+            if (w_cur <= WREG) kpm_stage_issue(stage[wib][0], sb_cur, w_cur, s, lane, (const float *)val, col, rlen);
+        }
+        for (; s < s_end; s += WPB) {
+            const int64_t sn = s + WPB;
+            int64_t sb_next = 0;
+            int w_next = 0;
+            if (sn < s_end) {
+                sb_next = sptr[sn];
+                w_next = (int)((sptr[sn + 1] - sb_next) >> 5);
             }
-            for (int rr0 = 0; rr0 < 32; rr0 += 2 * RPI) {
-                const int rA = rr0 + rsub, rB = rr0 + RPI + rsub;
-                const int64_t gA = s * 32 + rA, gB = s * 32 + rB;
-                const int lenA = __shfl_sync(0xffffffffu, mylen, rA);
-                const int lenB = __shfl_sync(0xffffffffu, mylen, rB);
-                for (int l0 = 0; l0 < nvec; l0 += 64) {
-                    const int l = l0 + PPL * sub;
-                    const bool actA = (gA < n) && (l < nvec), actB = (gB < n) && (l < nvec);
-                    T aA[PPL], aB[PPL];
+            const bool staged_next = sn < s_end && w_next <= WREG;
+            if (staged_next)
+                kpm_stage_issue(stage[wib][buf ^ 1], sb_next, w_next, sn, lane, (const float *)val, col, rlen);
+            if (staged_next) cp_async_wait<1>();
+            else cp_async_wait<0>();
+            __syncwarp();
+            T smom = T(0), smom2 = T(0);
+            if (w_cur <= WREG) {
+                const KpmStage &st = stage[wib][buf];
+                for (int rr0 = 0; rr0 < 32; rr0 += 2 * RPI) {
+                    const int rA = rr0 + rsub, rB = rr0 + RPI + rsub;
+                    const int64_t gA = s * 32 + rA, gB = s * 32 + rB;
+                    const int lenA = st.len[rA], lenB = st.len[rB];
+                    for (int l0 = 0; l0 < nvec; l0 += 64) {
+                        const int l = l0 + PPL * sub;
+                        const bool actA = (gA < n) && (l < nvec), actB = (gB < n) && (l < nvec);
+                        const int64_t oA = gA * ld + l, oB = gB * ld + l;
+                        // the rows' own operands first: out may alias xprev, so these loads
+                        // must precede this iteration's stores
+                        T pA[PPL], pB[PPL];
+                        uint32_t wdA = 0, wdB = 0;
+                        if (mode == 1 && actA) *reinterpret_cast<VL *>(pA) = *reinterpret_cast<const VL *>(xprev + oA);
+                        if (mode == 1 && actB) *reinterpret_cast<VL *>(pB) = *reinterpret_cast<const VL *>(xprev + oB);
+                        if (!DBL && actA) wdA = bits[gA * nw + (l >> 5)];
+                        if (!DBL && actB) wdB = bits[gB * nw + (l >> 5)];
+                        T aA[PPL], aB[PPL];
 #pragma unroll
-                    for (int q = 0; q < PPL; q++) aA[q] = aB[q] = T(0);
+                        for (int q = 0; q < PPL; q++) aA[q] = aB[q] = T(0);
 #pragma unroll
-                    for (int j = 0; j < WREG; j++)
-                        if (j < w) {
-                            const T vA = __shfl_sync(0xffffffffu, mv[j], rA);
-                            const int cA = __shfl_sync(0xffffffffu, mc[j], rA);
-                            const T vB = __shfl_sync(0xffffffffu, mv[j], rB);
-                            const int cB = __shfl_sync(0xffffffffu, mc[j], rB);
-                            T xa[PPL], xb[PPL];
-                            const bool ua = actA && j < lenA, ub = actB && j < lenB;
-                            if (ua) *reinterpret_cast<VL *>(xa) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cA * ld + l));
-                            if (ub) *reinterpret_cast<VL *>(xb) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cB * ld + l));
-                            if (ua)
+                        for (int j = 0; j < WREG; j++)
+                            if (j < w_cur) {
+                                const int cA = st.col[32 * j + rA], cB = st.col[32 * j + rB];
+                                const T vA = st.val[32 * j + rA], vB = st.val[32 * j + rB];
+                                T xa[PPL], xb[PPL];
+                                const bool ua = actA && j < lenA, ub = actB && j < lenB;
+                                if (ua) *reinterpret_cast<VL *>(xa) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cA * ld + l));
+                                if (ub) *reinterpret_cast<VL *>(xb) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cB * ld + l));
+                                if (ua)
 #pragma unroll
-                                for (int q = 0; q < PPL; q++) aA[q] += vA * xa[q];
-                            if (ub)
+                                    for (int q = 0; q < PPL; q++) aA[q] += vA * xa[q];
+                                if (ub)
 #pragma unroll
-                                for (int q = 0; q < PPL; q++) aB[q] += vB * xb[q];
+                                    for (int q = 0; q < PPL; q++) aB[q] += vB * xb[q];
+                            }
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            const bool act = h ? actB : actA;
+                            if (!act) continue;
+                            const T *a = h ? aB : aA;
+                            const T *pv = h ? pB : pA;
+                            const uint32_t word = h ? wdB : wdA;
+                            T wv[PPL];
+#pragma unroll
+                            for (int q = 0; q < PPL; q++) wv[q] = (mode == 1) ? a[q] - pv[q] : T(0.5) * a[q];
+                            *reinterpret_cast<VL *>(out + (h ? oB : oA)) = *reinterpret_cast<const VL *>(wv);
+                            if (DBL) {
+                                T xo[PPL];   // x is read-only and never aliased by out
+                                *reinterpret_cast<VL *>(xo) = *reinterpret_cast<const VL *>(x + (h ? oB : oA));
+#pragma unroll
+                                for (int q = 0; q < PPL; q++) {
+                                    smom += wv[q] * xo[q];
+                                    smom2 += wv[q] * wv[q];
+                                }
+                            } else {
+                                const int b = l & 31;
+#pragma unroll
+                                for (int q = 0; q < PPL; q++)
+                                    if (l + q < nvec) smom += ((word >> (b + q)) & 1u) ? -wv[q] : wv[q];
+                            }
                         }
-                    if (actA)
-                        kpm_row_epilogue<T, HAT, PPL, DBL>(mode, gA, l, nvec, ld, nw, bits, x, xprev, out, cc, sc, aA,
-                                                          smom, smom2);
-                    if (actB)
-                        kpm_row_epilogue<T, HAT, PPL, DBL>(mode, gB, l, nvec, ld, nw, bits, x, xprev, out, cc, sc, aB,
-                                                          smom, smom2);
+                    }
+                }
+            } else {
+                for (int rr0 = 0; rr0 < 32; rr0 += RPI) {
+                    const int rr = rr0 + rsub;
+                    const int64_t r = s * 32 + rr;
+                    const int len = (r < n) ? rlen[r] : 0;
+                    for (int l0 = 0; l0 < nvec; l0 += 64) {
+                        const int l = l0 + PPL * sub;
+                        const bool act = (r < n) && (l < nvec);
+                        T a[PPL];
+#pragma unroll
+                        for (int q = 0; q < PPL; q++) a[q] = T(0);
+                        for (int j = 0; j < len; j++) {
+                            const int64_t e = sb_cur + 32 * (int64_t)j + rr;
+                            const T v = val[e];
+                            const int cj = col[e];
+                            if (act) {
+                                T xv[PPL];
+                                *reinterpret_cast<VL *>(xv) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cj * ld + l));
+#pragma unroll
+                                for (int q = 0; q < PPL; q++) a[q] += v * xv[q];
+                            }
+                        }
+                        if (act)
+                            kpm_row_epilogue<T, HAT, PPL, DBL>(mode, r, l, nvec, ld, nw, bits, x, xprev, out, cc, sc, a,
+                                                              smom, smom2);
+                    }
                 }
             }
-        } else {
+            mom += (double)smom;
+            mom2 += (double)smom2;
+            __syncwarp();            // the buffer just read is the next copy's target
+            buf ^= 1;
+            sb_cur = sb_next;
+            w_cur = w_next;
+        }
+    } else {
+        const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+        const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t s = warp; s < nslices; s += nwarps) {
+            const int64_t sbase = sptr[s];
+            T smom = T(0), smom2 = T(0);  // this lane's share of the slice, in the block's precision
             for (int rr0 = 0; rr0 < 32; rr0 += RPI) {
                 const int rr = rr0 + rsub;
                 const int64_t r = s * 32 + rr;
@@ -403,15 +480,31 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                     T a[PPL];
 #pragma unroll
                     for (int q = 0; q < PPL; q++) a[q] = T(0);
-                    for (int j = 0; j < len; j++) {
-                        const int64_t e = sbase + 32 * (int64_t)j + rr;
-                        const T v = val[e];
-                        const int cj = col[e];
-                        if (act) {
-                            T xv[PPL];
-                            *reinterpret_cast<VL *>(xv) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cj * ld + l));
+                    if (len <= WREG) {
 #pragma unroll
-                            for (int q = 0; q < PPL; q++) a[q] += v * xv[q];
+                        for (int j = 0; j < WREG; j++)
+                            if (j < len) {
+                                const int64_t e = sbase + 32 * (int64_t)j + rr;
+                                const T v = val[e];
+                                const int cj = col[e];
+                                if (act) {
+                                    T xv[PPL];
+                                    *reinterpret_cast<VL *>(xv) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cj * ld + l));
+#pragma unroll
+                                    for (int q = 0; q < PPL; q++) a[q] += v * xv[q];
+                                }
+                            }
+                    } else {
+                        for (int j = 0; j < len; j++) {
+                            const int64_t e = sbase + 32 * (int64_t)j + rr;
+                            const T v = val[e];
+                            const int cj = col[e];
+                            if (act) {
+                                T xv[PPL];
+                                *reinterpret_cast<VL *>(xv) = __ldg(reinterpret_cast<const VL *>(x + (int64_t)cj * ld + l));
+#pragma unroll
+                                for (int q = 0; q < PPL; q++) a[q] += v * xv[q];
+                            }
                         }
                     }
                     if (act)
@@ -419,9 +512,9 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                                                           smom, smom2);
                 }
             }
+            mom += (double)smom;
+            mom2 += (double)smom2;
         }
-        mom += (double)smom;
-        mom2 += (double)smom2;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -429,13 +522,13 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
         if (DBL) mom2 += __shfl_xor_sync(0xffffffffu, mom2, off);
     }
     if (lane == 0) {
-        red[threadIdx.x >> 5] = mom;
-        red2[threadIdx.x >> 5] = mom2;
+        red[wib] = mom;
+        red2[wib] = mom2;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0, t2 = 0.0;
-        for (int i = 0; i < TPB / 32; i++) {
+        for (int i = 0; i < WPB; i++) {
             t += red[i];
             t2 += red2[i];
         }
@@ -531,7 +624,7 @@ static int sell_build(evsl_ctx *c, DevMatrix &M, bool primary, const char *what,
     for (int64_t p = 0; p < nnz; p++)
         if (ci[p] < 0 || ci[p] >= n)
             return ctx_fail(c, EVSL_ERR_ARG, "%s: column index %d out of range at %lld", what, ci[p], (long long)p);
-    std::vector<int32_t> rlen(n);
+    std::vector<int32_t> rlen(nslices * 32, 0);   // padded to whole slices: rows past n have length 0
     bool has_diag = true;
     for (int64_t r = 0; r < n; r++) {
         rlen[r] = (int32_t)(rp[r + 1] - rp[r]);
@@ -554,7 +647,7 @@ static int sell_build(evsl_ctx *c, DevMatrix &M, bool primary, const char *what,
         (st = ctx_alloc(c, (void **)&A.col, sizeof(int32_t) * ns)) ||
         (st = ctx_alloc(c, (void **)&A.val, sizeof(double) * ns)) ||
         (st = ctx_alloc(c, (void **)&A.val32, sizeof(float) * ns)) ||
-        (st = ctx_alloc(c, (void **)&A.rlen, sizeof(int32_t) * n))) {
+        (st = ctx_alloc(c, (void **)&A.rlen, sizeof(int32_t) * nslices * 32))) {
         release();
         return st;
     }
@@ -575,7 +668,8 @@ static int sell_build(evsl_ctx *c, DevMatrix &M, bool primary, const char *what,
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ci, ci, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_cv, cv, sizeof(double) * nnz, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(A.rlen, rlen.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(A.rlen, rlen.data(), sizeof(int32_t) * nslices * 32, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         k_sell_fill<double><<<blocks_for(nslices * 32, 256), 256, 0, s>>>(n, nslices, d_rp, d_ci, d_cv,
                                                                           A.sptr, A.col, A.val, A.val32);
@@ -616,7 +710,7 @@ void dev_matrix_free(evsl_ctx *c, DevMatrix &A)
     ctx_free(c, A.col, sizeof(int32_t) * A.nstored);
     ctx_free(c, A.val, sizeof(double) * A.nstored);
     ctx_free(c, A.val32, sizeof(float) * A.nstored);
-    ctx_free(c, A.rlen, sizeof(int32_t) * A.n);
+    ctx_free(c, A.rlen, sizeof(int32_t) * A.nslices * 32);
     ctx_free(c, A.vhat, sizeof(double) * A.nstored);
     ctx_free(c, A.vhat32, sizeof(float) * A.nstored);
     A = DevMatrix();

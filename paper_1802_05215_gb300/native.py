@@ -118,6 +118,8 @@ def load(build_if_missing: bool = True):
         "evsl_set_device_budget": (i32, [i32, sz]),
         "evsl_device_used": (sz, [i32]),
         "evsl_mem_used": (sz, [P]),
+        "evsl_dense_gemm": (i32, [P, i32, i64, i32, i64, P, i64, P, i64, P, i64, i32]),
+        "evsl_set_tensor_gemm": (i32, [P, i32]),
         "evsl_set_graphs": (i32, [P, i32]),
         "evsl_profile": (i32, [P, i32]),
         "evsl_profile_get": (i32, [P, i32, P, P]),
@@ -495,6 +497,21 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.lib.evsl_launch_count(self.h))
+
+    def dense_gemm(self, A, B, C, trans_a=False, mode=0):
+        """C {=, -=, +=} op(A) B for device tensors holding column-major FP64 matrices: pass
+        torch tensors of shape (cols, rows) (row j = column j); op(A) = A or A^T."""
+        ka, ra = A.shape            # columns, rows of the column-major A
+        n_b, k_b = B.shape
+        M = ka if trans_a else ra
+        K = ra if trans_a else ka
+        assert k_b == K and C.shape == (n_b, M)
+        self._check(self.lib.evsl_dense_gemm(self.h, int(trans_a), M, n_b, K, _addr(A), ra, _addr(B), k_b,
+                                             _addr(C), M, mode), "dense_gemm")
+
+    def set_tensor_gemm(self, enable: bool):
+        """Large FP64 products on the tensor cores (default) or on the plain FP64 kernels."""
+        self._check(self.lib.evsl_set_tensor_gemm(self.h, int(enable)), "set_tensor_gemm")
 
     def mem_used(self) -> int:
         """Device bytes this context holds."""
