@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1802_05215_gb300 import inputs  # noqa: E402
-from paper_1802_05215_gb300.schedule import assign_slices, slice_costs  # noqa: E402
+from paper_1802_05215_gb300 import partition  # noqa: E402
 
 WORKLOAD = "lap3d_100"
 XI, ETA, NSLICES = 0.20, 0.60, 10
@@ -214,31 +214,31 @@ def run_ours(args):
     ctx = native.Context(local)
     ctx.set_csr(A)
 
+    backend = partition.NativeBackend(ctx, n)
+
     def one_step(t: int, e2e: bool):
-        """Whole path for this rank's t-th slice (LPT assignment, cycled)."""
-        s = owned[t % len(owned)]
+        """Whole path for this rank's t-th slice: the partition layer's plan (bounds on rank 0,
+        KPM probes split over the ranks, slicing on rank 0, LPT assignment), then the slice."""
         if e2e:
             ctx.set_csr(Apin)                       # host -> device copy of the inputs
-        lo, hi = ctx.bounds(BOUNDS_STEPS, SEED)
-        mu = ctx.kpm_dos(KPM_DEG, KPM_NVEC, SEED, lo, hi)
-        sli, est = native.slice_by_dos(mu, n, lo, hi, XI, ETA, NSLICES)
-        a, b = sli[s], sli[s + 1]
-        f = native.cheb_filter_build(a, b, lo, hi)
-        m = lanczos_m(est[s])
+        p = partition.plan(backend, XI, ETA, NSLICES, KPM_DEG, KPM_NVEC, SEED, BOUNDS_STEPS)
+        own = p.owned[rank] or [rank % NSLICES]
+        s = own[t % len(own)]
+        a, b = p.slice(s)
+        f = native.cheb_filter_build(a, b, p.lmin, p.lmax)
+        m = lanczos_m(p.est[s])
         cap = int(m)
         Ybuf = Yhost[:cap * n] if e2e else Ydev[:cap * n]
         r = ctx.chebLanTr(a, b, f, m=m, tol=TOL, seed=SEED, cap=cap, Y=Ybuf,
                           right_closed=(s == NSLICES - 1))
-        return dict(slice=s, a=a, b=b, deg=f.deg, m=m, nev=r["nev"], est=float(est[s]),
+        return dict(slice=s, a=a, b=b, deg=f.deg, m=m, nev=r["nev"], est=float(p.est[s]),
+                    lam=r["lam"], res=r["res"], status=r["status"],
                     res_max=float(r["res"].max()) if r["nev"] else 0.0, stats=r["stats"])
 
     # the largest Krylov dimension any slice can use bounds the eigenvector buffers
-    lo, hi = ctx.bounds(BOUNDS_STEPS, SEED)
-    mu = ctx.kpm_dos(KPM_DEG, KPM_NVEC, SEED, lo, hi)
-    sli0, est0 = native.slice_by_dos(mu, n, lo, hi, XI, ETA, NSLICES)
-    capmax = lanczos_m(float(np.max(est0)))
-    degs = [native.cheb_filter_build(sli0[i], sli0[i + 1], lo, hi).deg for i in range(NSLICES)]
-    owned = assign_slices(slice_costs(est0, degs), world)[rank] or [rank % NSLICES]
+    p0 = partition.plan(backend, XI, ETA, NSLICES, KPM_DEG, KPM_NVEC, SEED, BOUNDS_STEPS)
+    lo, hi = p0.lmin, p0.lmax
+    capmax = lanczos_m(float(np.max(p0.est)))
     Ydev = torch.empty(capmax * n, dtype=torch.float64, device="cuda")
     Yhost = torch.empty(capmax * n, dtype=torch.float64).pin_memory().numpy()
 
@@ -290,7 +290,11 @@ def run_ours(args):
         step += 1
     barrier()
     e2e_total, e2e_s, _ = whole_job_rate(float(sum(r["nev"] for r in e2e_recs)), time.perf_counter() - t0, "cuda")
-    check_counts(recs + e2e_recs, 3, 100, NSLICES)
+    # every rank's slice results on rank 0 (partition layer): counts checked there against the
+    # closed form of the whole run, eigenvalues of all ranks included
+    allrecs = partition.gather([{k: v for k, v in r.items() if k != "stats"} for r in recs + e2e_recs])
+    if rank == 0:
+        check_counts([r for part in allrecs for r in part], 3, 100, NSLICES)
     h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.val.nbytes
     d2h = float(np.mean([r["nev"] * n * 8 for r in e2e_recs]))
 
@@ -307,7 +311,9 @@ def run_ours(args):
 
     result = None
     if rank == 0:
-        cpu = cpu_baseline(A, recs[0], lo, hi) if (world == 1 and not args.no_cpu) else None
+        r0 = recs[0]
+        cpu = (cpu_baseline(A, r0["slice"], r0["a"], r0["b"], lo, hi, r0["est"])
+               if (world == 1 and not args.no_cpu) else None)
         lat = [r["latency_s"] for r in recs]
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -328,7 +334,7 @@ def run_ours(args):
             "slice_latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "kernel_ms": {k: v[1] for k, v in prof.items()},
             "kernel_launches": {k: v[0] for k, v in prof.items()},
-            "steps_detail": [{k: v for k, v in r.items() if k != "stats"} | {
+            "steps_detail": [{k: v for k, v in r.items() if k not in ("stats", "lam", "res")} | {
                 "niter": r["stats"]["niter"], "t_filter": r["stats"]["t_filter"],
                 "t_orth": r["stats"]["t_orth"], "t_restart": r["stats"]["t_restart"],
                 "t_total": r["stats"]["t_total"]} for r in recs],
@@ -341,65 +347,146 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------------------------------
-def cpu_baseline(A, rec, lo, hi, budget_s: float = 20.0):
-    """The oracle, as it stands, on a bounded sample of the same slice: one filter application
-    of the slice's degree and full reorthogonalisations of one vector against a sample of
-    basis columns, extrapolated with the GPU run's own step count and mean basis width."""
+# CPU baseline: the FP64 oracle, as it stands, on the host cores.  A whole 100^3 slice takes the
+# oracle hours, so both bench arms time the same bounded sample of a slice and extrapolate it the
+# same way; config 1 (the 2-D 100^2 case) is small enough to run end to end.
+STEPS_PER_PAIR = 4.8   # Lanczos steps per locked pair in the extrapolation (4.6-4.8 in the GPU runs)
+
+
+def host_info() -> tuple[int, str]:
+    """(usable host threads, CPU model) of this machine."""
+    nproc = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return nproc, model or "unknown"
+
+
+def oracle_slice_sample(A, a: float, b: float, lo: float, hi: float, est: float, threads: int) -> dict:
+    """On `threads` host threads: one filter application of the slice's degree and one CGS pass
+    of a vector against 64 columns, extrapolated to a slice of est pairs: 4.8 est Lanczos steps,
+    each one filter application and one reorthogonalisation against the mean basis
+    (est + m) / 2 (locked vectors grow to est, the Krylov basis to m = 2 est + 40), plus the
+    restarts' Ritz vectors (m x est columns per restart, one restart per m steps) at the
+    measured cost per column."""
+    import oracle
+    oracle.set_threads(threads)
+    try:
+        n = A.n
+        pol = oracle.filter_build(a, b, lo, hi)
+        x = np.random.default_rng(0).standard_normal(n)
+        t0 = time.perf_counter()
+        oracle.filter_apply(A, lo, hi, pol["coef"], x)
+        t_filter = time.perf_counter() - t0
+        ncol = 64
+        B = np.asfortranarray(np.linalg.qr(np.random.default_rng(1).standard_normal((n, ncol)))[0])
+        z = np.random.default_rng(2).standard_normal(n)
+        t0 = time.perf_counter()
+        oracle.reorth(z, B)
+        t_col = (time.perf_counter() - t0) / ncol
+    finally:
+        oracle.set_threads(1)
+    m = lanczos_m(est)
+    niter = STEPS_PER_PAIR * est
+    mean_cols = 0.5 * (est + m)
+    restarts = max(1.0, niter / m)
+    t_slice = niter * (t_filter + t_col * mean_cols) + restarts * 0.5 * m * est * t_col
+    return {"threads": threads, "deg": pol["deg"], "t_filter_s": t_filter, "t_reorth_per_column_s": t_col,
+            "steps": niter, "mean_basis": mean_cols, "restarts": restarts, "slice_s": t_slice,
+            "value": est / t_slice}
+
+
+def oracle_config1(threads: int) -> dict:
+    """Config 1 end to end on the oracle: the 2-D 100^2 Laplacian on [0.40, 0.48] (69
+    eigenvalues): bounds, KPM (degree 80, 20 probes), one slice, filter, thick-restart Lanczos."""
+    import oracle
+    w = inputs.workload("lap2d_100")
+    A = w["matrix"]()
+    oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        lo, hi = oracle.bounds(A, BOUNDS_STEPS, SEED)
+        mu = oracle.kpm_moments(A, w["kpm_deg"], w["kpm_nvec"], SEED, lo, hi)
+        sli, est = oracle.slicer(mu, lo, hi, w["xi"], w["eta"], 1)
+        pol = oracle.filter_build(sli[0], sli[1], lo, hi)
+        r = oracle.cheblantr(A, sli[0], sli[1], pol, m=lanczos_m(est[0]), tol=TOL, seed=SEED)
+        secs = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    ok = int(np.count_nonzero(r["res"] <= TOL))
+    return {"threads": threads, "eigenpairs": ok, "exact_count": laplacian_count(2, 100, w["xi"], w["eta"], True),
+            "seconds": secs, "value": ok / secs, "status": int(r["status"])}
+
+
+def cpu_baseline(A, s: int, a: float, b: float, lo: float, hi: float, est: float) -> dict:
+    """The oracle on this host on a bounded sample of slice s (single thread and all threads,
+    the same extrapolation in both bench arms) and config 1 run end to end."""
     import oracle
     oracle.build()
-    n = A.n
-    pol = oracle.filter_build(rec["a"], rec["b"], lo, hi)
-    x = np.random.default_rng(0).standard_normal(n)
-    t0 = time.perf_counter()
-    oracle.filter_apply(A, lo, hi, pol["coef"], x)
-    t_filter = time.perf_counter() - t0
-    ncol = 64
-    B = np.asfortranarray(np.linalg.qr(np.random.default_rng(1).standard_normal((n, ncol)))[0])
-    z = np.random.default_rng(2).standard_normal(n)
-    t0 = time.perf_counter()
-    oracle.reorth(z, B)
-    t_orth_col = (time.perf_counter() - t0) / ncol
-    niter = rec["stats"]["niter"]
-    mean_cols = rec["nev"] / 2.0 + rec["m"] / 2.0      # locked vectors grow to nev, basis to m
-    t_slice = niter * (t_filter + t_orth_col * mean_cols)
-    return {"value": rec["nev"] / t_slice, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"slice {rec['slice']}: one degree-{pol['deg']} filter application "
-                       f"({t_filter:.2f} s) + one CGS reorthogonalisation against {ncol} columns, "
-                       f"extrapolated to the GPU run's {niter} Lanczos steps at a mean basis of "
-                       f"{mean_cols:.0f} columns (restarts not counted)"),
-            "extrapolated_slice_s": t_slice}
+    nproc, model = host_info()
+    one = oracle_slice_sample(A, a, b, lo, hi, est, 1)
+    allc = oracle_slice_sample(A, a, b, lo, hi, est, nproc) if nproc > 1 else one
+    c1 = [oracle_config1(1)] + ([oracle_config1(nproc)] if nproc > 1 else [])
+    return {"value": allc["value"], "unit": UNIT, "cores": nproc, "kind": "oracle", "cpu_model": model,
+            "sample": (f"slice {s} ({est:.0f} estimated pairs): one degree-{allc['deg']} filter application and "
+                       f"one CGS pass against 64 columns on {nproc} threads, extrapolated to "
+                       f"{STEPS_PER_PAIR} x est Lanczos steps at a mean basis of {allc['mean_basis']:.0f} "
+                       f"columns plus {allc['restarts']:.1f} restarts' Ritz vectors"),
+            "extrapolated_slice_s": allc["slice_s"], "all_threads": allc, "single_thread": one,
+            "config1_end_to_end": c1}
 
 
 def run_reference(args):
-    """Reference arm: the oracle, timed on the host cores, on the same metric and workload."""
+    """Reference arm: the oracle, timed on the host cores, on the same metric and workload: each
+    step samples the slice the GPU arm's step of the same index solves (slice t mod 10) on all
+    host threads and extrapolates it as cpu_baseline does; the single-thread sample and config 1
+    end to end are reported beside it."""
     rank, world, _ = dist_env()
     if rank != 0:
         return None
     import oracle
     oracle.build()
+    nproc, model = host_info()
     A = inputs.workload(WORKLOAD)["matrix"]()
-    lo, hi = oracle.bounds(A, BOUNDS_STEPS, SEED)
-    # the DOS slicing of the reference arm with a reduced probe count keeps a step bounded
-    mu = oracle.kpm_moments(A, KPM_DEG, 2, SEED, lo, hi)
-    sli, est = oracle.slicer(mu, lo, hi, XI, ETA, NSLICES)
+    oracle.set_threads(nproc)
+    try:
+        lo, hi = oracle.bounds(A, BOUNDS_STEPS, SEED)
+        mu = oracle.kpm_moments(A, KPM_DEG, KPM_NVEC, SEED, lo, hi)
+        sli, est = oracle.slicer(mu, lo, hi, XI, ETA, NSLICES)
+    finally:
+        oracle.set_threads(1)
     vals = []
     for t in range(args.warmup + args.steps):
         s = t % NSLICES
-        m = lanczos_m(est[s])
-        nev_est = float(est[s])
-        rec = {"slice": s, "a": sli[s], "b": sli[s + 1], "m": m, "nev": nev_est,
-               "stats": {"niter": int(3 * nev_est)}}
-        cb = cpu_baseline(A, rec, lo, hi)
+        smp = oracle_slice_sample(A, sli[s], sli[s + 1], lo, hi, float(est[s]), nproc)
         if t >= args.warmup:
-            vals.append(cb)
-    value = float(np.mean([v["value"] for v in vals]))
+            vals.append((s, smp))
+    value = float(np.mean([v[1]["value"] for v in vals]))
+    s0 = args.warmup % NSLICES
+    full = cpu_baseline(A, s0, sli[s0], sli[s0 + 1], lo, hi, float(est[s0]))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "3-D 7-point Laplacian 100^3, [0.20,0.60], 10 slices"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": vals[0]["sample"] + "; step count taken as 3x the DOS "
-                                                          "estimate of the slice"},
+           "config": {"workload": "3-D 7-point Laplacian 100^3 (n=1e6, nnz=6.94e6), [0.20,0.60] "
+                                  "in 10 KPM-DOS slices (degree 120, 40 probes), Jackson filter, "
+                                  "FP64 thick-restart Lanczos per slice"},
+           "cpu_baseline": dict(full, value=value,
+                                sample=f"per step: {full['sample'].split(':', 1)[1].strip()}; "
+                                       f"the mean over steps {args.warmup}..{args.warmup + args.steps - 1}"),
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return out

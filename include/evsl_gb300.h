@@ -94,6 +94,18 @@ int evsl_kpm_dos(evsl_ctx *ctx, int degree, int nvec, uint64_t seed, double lmin
 int evsl_kpm_dos_doubling(evsl_ctx *ctx, int degree, int nvec, uint64_t seed, double lmin, double lmax,
                           evsl_precision prec, double *mu);
 
+/* Per-probe KPM sums (Sec. 2.1: the terms of the estimator before averaging), for spreading the
+ * probes over processes (Sec. 2.6's first level of parallelism): for probes first .. first +
+ * nprobe - 1, the same probes as evsl_kpm_dos (probe index first + l draws its signs at counter
+ * (first + l) n + i),
+ *     out[l * (degree + 1) + k] = v_{first+l}^T T_k(Ahat) v_{first+l},   k = 0..degree.
+ * Each probe's values are formed in an order that depends on n only, not on first or nprobe,
+ * so gathering every process's rows and adding them in probe order gives the same moments
+ * bitwise however the probes were split.  out: HOST array of nprobe (degree + 1) doubles.
+ * prec as in evsl_kpm_dos.  Errors: EVSL_ERR_ARG, EVSL_ERR_STATE without a matrix. */
+int evsl_kpm_probe_moments(evsl_ctx *ctx, int degree, int64_t first, int nprobe, uint64_t seed, double lmin,
+                           double lmax, evsl_precision prec, double *out);
+
 /* DOS slicer (Sec. 2.1, Eq. (2.2); spslicer).  Pure host function, no context.  From the
  * Jackson-damped KPM density it places npts evenly spaced points on [xi, eta], and puts the
  * slice ends t_1..t_{ns-1} where the cumulative count crosses i/ns of the total (first crossing,

@@ -21,21 +21,53 @@ _lib = None
 DAMP_NONE, DAMP_JACKSON, DAMP_SIGMA = 0, 1, 2
 
 
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_libs = {}
+_threads = 1
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    """Compile the oracle with gcc (-O2, no FMA contraction), once plain and once with OpenMP.
+    The loops the OpenMP build runs in parallel (SpMV rows, elementwise updates, independent
+    dot products) carry no reduction, so both builds give bitwise the same results; the
+    OpenMP one only serves the multi-core CPU baseline."""
+    for lib, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+            tmp = lib + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+                                   "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, lib)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Run the oracle on n host threads (n <= 1: the plain single-threaded build).  Returns the
+    previous setting."""
+    global _threads, _lib
+    prev = _threads
+    _threads = max(1, int(n))
+    _lib = None
+    if _threads > 1:
+        build()
+        gomp = C.CDLL("libgomp.so.1", mode=C.RTLD_GLOBAL)
+        gomp.omp_set_num_threads(_threads)
+    return prev
+
+
+def threads() -> int:
+    return _threads
 
 
 def _load():
     global _lib
     if _lib is None:
         build()
-        _lib = C.CDLL(_LIB)
+        path = _LIB_OMP if _threads > 1 else _LIB
+        if path in _libs:
+            _lib = _libs[path]
+            return _lib
+        _lib = C.CDLL(path)
+        _libs[path] = _lib
         d, i32, i64, u64 = C.c_double, C.c_int, C.c_int64, C.c_uint64
         P = C.c_void_p
         _lib.orc_draw.restype = u64
@@ -49,6 +81,8 @@ def _load():
         _lib.orc_bounds.argtypes = [i64, P, P, P, i32, u64, P, P]
         _lib.orc_kpm_moments.restype = i32
         _lib.orc_kpm_moments.argtypes = [i64, P, P, P, i32, i32, u64, d, d, P]
+        _lib.orc_kpm_probe_moments.restype = i32
+        _lib.orc_kpm_probe_moments.argtypes = [i64, P, P, P, i32, i64, i32, u64, d, d, P]
         _lib.orc_kpm_moments_doubling.restype = i32
         _lib.orc_kpm_moments_doubling.argtypes = [i64, P, P, P, i32, i32, u64, d, d, P]
         _lib.orc_jackson.argtypes = [i32, P]
@@ -155,6 +189,15 @@ def kpm_moments(A, degree: int, nvec: int, seed: int, lmin: float, lmax: float) 
     mu = np.empty(degree + 1)
     _load().orc_kpm_moments(*_csr_args(A), degree, nvec, seed, lmin, lmax, _p(mu))
     return mu
+
+
+def kpm_probe_moments(A, degree: int, first: int, nprobe: int, seed: int, lmin: float,
+                      lmax: float) -> np.ndarray:
+    """Per-probe KPM sums v_l^T T_k(Ahat) v_l for probes first..first+nprobe-1 (Sec. 2.1, the
+    estimator's terms before averaging): an nprobe x (degree + 1) array."""
+    out = np.empty((nprobe, degree + 1))
+    _load().orc_kpm_probe_moments(*_csr_args(A), degree, first, nprobe, seed, lmin, lmax, _p(out))
+    return out
 
 
 def jackson(M: int) -> np.ndarray:

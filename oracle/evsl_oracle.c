@@ -6,7 +6,10 @@
  * leg may load this code.  It shares nothing with the CUDA path: no headers, no helpers, no
  * tables.  Every loop is written in the order the paper states the method, without blocking,
  * fusion or reordering, so that it can be read against the paper.  Built with
- * -ffp-contract=off (no fused multiply-add).
+ * -ffp-contract=off (no fused multiply-add).  The `omp parallel for` pragmas mark loops
+ * without reductions (SpMV rows, elementwise updates, independent dot products); a build with
+ * -fopenmp runs them on several host threads with bitwise the same results, for the
+ * multi-core CPU baseline, and a build without it ignores them.
  *
  * Contents (paper passage in brackets):
  *   SplitMix64 counter-based draws  [seeded inputs; Steele-Lea-Flood 2014]
@@ -14,7 +17,8 @@
  *   dense symmetric eigensolver      [Householder tridiagonalisation + implicit symmetric QR
  *                                     with Wilkinson shift, Golub & Van Loan Sec. 8.3]
  *   spectral bounds by Lanczos       [Sec. 2.2.1 text after Eq. (2.3); LanTrbounds Sec. 3.1]
- *   KPM moments, Jackson damping, cumulative DOS, slicer  [Sec. 2.1, Eqs. (2.1)-(2.2)]
+ *   KPM moments (and per-probe sums), Jackson damping, cumulative DOS, slicer
+ *                                    [Sec. 2.1, Eqs. (2.1)-(2.2)]
  *   Chebyshev filter build           [Sec. 2.2.1, Eqs. (2.3)-(2.6)]
  *   filter application               [Eq. (2.4) with the mapping of Eq. (2.3)]
  *   filtered thick-restart Lanczos with locking  [Sec. 2.3, Eqs. (2.10)-(2.11); Algorithm 2]
@@ -74,6 +78,7 @@ typedef struct {
 
 static void orc_matvec(const orc_csr *A, const double *x, double *y)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < A->n; i++) {
         double s = 0.0;
         for (int64_t p = A->rp[i]; p < A->rp[i + 1]; p++)
@@ -102,6 +107,7 @@ static double orc_nrm2(int64_t n, const double *x) { return sqrt(orc_dot(n, x, x
 static void orc_mapped_matvec(const orc_csr *A, double c, double d, const double *x, double *y)
 {
     orc_matvec(A, x, y);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < A->n; i++) y[i] = (y[i] - c * x[i]) / d;
 }
 
@@ -253,14 +259,18 @@ static int orc_reorth(int64_t n, double *z, const double *B1, int nc1, const dou
     int passes = 0;
     for (int pass = 0; pass < 2; pass++) {
         double before = orc_nrm2(n, z);
+#pragma omp parallel for schedule(dynamic, 4)
         for (int j = 0; j < nc1; j++) h[j] = orc_dot(n, B1 + (size_t)j * n, z);
+#pragma omp parallel for schedule(dynamic, 4)
         for (int j = 0; j < nc2; j++) h[nc1 + j] = orc_dot(n, B2 + (size_t)j * n, z);
         for (int j = 0; j < nc1; j++) {
             const double *b = B1 + (size_t)j * n;
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < n; i++) z[i] -= h[j] * b[i];
         }
         for (int j = 0; j < nc2; j++) {
             const double *b = B2 + (size_t)j * n;
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < n; i++) z[i] -= h[nc1 + j] * b[i];
         }
         passes++;
@@ -359,6 +369,42 @@ int orc_kpm_moments(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
         }
     }
     for (int k = 0; k <= M; k++) mu[k] /= nvec;
+    free(vl); free(w0); free(w1); free(w2);
+    return 0;
+}
+
+/* Per-probe KPM sums (Sec. 2.1, the terms of the estimator above before the average):
+ *   out[l*(M+1) + k] = v_{first+l}^T T_k(Ahat) v_{first+l},  l = 0..nprobe-1, k = 0..M,
+ * for the same Rademacher probes as orc_kpm_moments (probe index first+l draws its signs at
+ * counter (first+l)*n + i).  Summing rows 0..nvec-1 in order and dividing by nvec reproduces
+ * orc_kpm_moments exactly; a split of the probes over processes therefore only has to gather
+ * these rows.                                                                              */
+int orc_kpm_probe_moments(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                          int M, int64_t first, int nprobe, uint64_t seed, double lmin, double lmax,
+                          double *out)
+{
+    orc_csr A = {n, rp, ci, v};
+    double c = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+    double *vl = malloc(sizeof(double) * n), *w0 = malloc(sizeof(double) * n),
+           *w1 = malloc(sizeof(double) * n), *w2 = malloc(sizeof(double) * n);
+    for (int l = 0; l < nprobe; l++) {
+        double *o = out + (int64_t)l * (M + 1);
+        const uint64_t probe = (uint64_t)(first + l);
+        for (int64_t i = 0; i < n; i++)
+            vl[i] = orc_sign(orc_draw(seed, ORC_STREAM_KPM, probe * (uint64_t)n + (uint64_t)i));
+        memcpy(w0, vl, sizeof(double) * n);
+        o[0] = orc_dot(n, vl, w0);
+        if (M >= 1) {
+            orc_mapped_matvec(&A, c, d, w0, w1);
+            o[1] = orc_dot(n, vl, w1);
+        }
+        for (int k = 1; k < M; k++) {
+            orc_mapped_matvec(&A, c, d, w1, w2);
+            for (int64_t i = 0; i < n; i++) w2[i] = 2.0 * w2[i] - w0[i];
+            o[k + 1] = orc_dot(n, vl, w2);
+            double *t = w0; w0 = w1; w1 = w2; w2 = t;
+        }
+    }
     free(vl); free(w0); free(w1); free(w2);
     return 0;
 }
@@ -553,8 +599,11 @@ static void orc_filter_apply_csr(const orc_csr *A, double c, double d, int deg,
     for (int64_t i = 0; i < n; i++) y[i] += coef[1] * w1[i];
     for (int j = 1; j < deg; j++) {
         orc_mapped_matvec(A, c, d, w1, w2);
-        for (int64_t i = 0; i < n; i++) w2[i] = 2.0 * w2[i] - w0[i];
-        for (int64_t i = 0; i < n; i++) y[i] += coef[j + 1] * w2[i];
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; i++) {
+            w2[i] = 2.0 * w2[i] - w0[i];
+            y[i] += coef[j + 1] * w2[i];
+        }
         double *t = w0; w0 = w1; w1 = w2; w2 = t;
     }
 }

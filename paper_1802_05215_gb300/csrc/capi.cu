@@ -255,6 +255,18 @@ int evsl_kpm_dos_doubling(evsl_ctx *c, int degree, int nvec, uint64_t seed, doub
     return drv_kpm(c, degree, nvec, seed, lmin, lmax, prec, mu, true);
 }
 
+int evsl_kpm_probe_moments(evsl_ctx *c, int degree, int64_t first, int nprobe, uint64_t seed, double lmin,
+                           double lmax, evsl_precision prec, double *out)
+{
+    if (!c) return EVSL_ERR_ARG;
+    c->err.clear();
+    if (!out || degree < 0 || first < 0 || nprobe < 1 || !(lmax > lmin) || (prec != EVSL_FP64 && prec != EVSL_FP32))
+        return ctx_fail(c, EVSL_ERR_ARG, "kpm_probe_moments: bad arguments");
+    if (c->A.n == 0) return ctx_fail(c, EVSL_ERR_STATE, "kpm_probe_moments: no matrix set");
+    cudaSetDevice(c->device);
+    return drv_kpm_probe(c, degree, first, nprobe, seed, lmin, lmax, prec, out);
+}
+
 int evsl_slice_by_dos(const double *mu, int degree, int64_t n, double lmin, double lmax,
                       double xi, double eta, int nslices, int npts, double *sli, double *est)
 {

@@ -150,8 +150,16 @@ int spmv_f64(evsl_ctx *c, int nvec, const double *X, double *Y);
 // KPM: fill W0 with the probes, then steps
 // KPM probe blocks are row-major with leading dimension kpm_ld(nvec) (nvec rounded up to 4)
 int kpm_ld(int nvec);
-int kpm_init_f64(evsl_ctx *c, int nvec, uint64_t seed, double *W0);
-int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0);
+// probes first .. first + nvec - 1 (global probe indices of the KPM random stream)
+int kpm_init_f64(evsl_ctx *c, int nvec, uint64_t seed, double *W0, uint64_t first = 0);
+int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0, uint64_t first = 0);
+// out[l] = sum_r v_l[r] W[r, l] for the np probes of the block made by kpm_init (fixed order per
+// probe); part: kpm_probe_dot_blocks(c) * np doubles of scratch
+int kpm_probe_dots_f64(evsl_ctx *c, int np, const double *W, double *part, double *out);
+int kpm_probe_dots_f32(evsl_ctx *c, int np, const float *W, double *part, double *out);
+int kpm_probe_dot_blocks(evsl_ctx *c);
+int drv_kpm_probe(evsl_ctx *c, int degree, int64_t first, int nprobe, uint64_t seed, double lmin, double lmax,
+                  evsl_precision prec, double *out);
 // mode 0: out = (A x - cc x) sc; mode 1: out = (A x - cc x) sc - xprev.  Writes, for moment
 // index k, per-block partial sums of sum_l sum_i v_l[i] out_l[i] into part + k*nblk.
 int kpm_step_f64(evsl_ctx *c, int mode, int nvec, uint64_t seed, const double *x,

@@ -540,7 +540,7 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
 // Probes in the row-major layout: W0[r * ld + l] = sign of draw(seed, KPM, l * n + r) for
 // l < nvec, 0 for the padding probes; one warp builds one sign word of one row.
 template <typename T>
-__global__ void k_kpm_init(int64_t n, int nvec, int ld, uint64_t key, T *W0, uint32_t *bits)
+__global__ void k_kpm_init(int64_t n, int nvec, int ld, uint64_t key, uint64_t first, T *W0, uint32_t *bits)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int nw = (nvec + 31) >> 5;
@@ -550,7 +550,7 @@ __global__ void k_kpm_init(int64_t n, int nvec, int ld, uint64_t key, T *W0, uin
     const int l = (int)(t - r * nw * 32);
     bool neg = false;
     if (l < nvec) {
-        uint64_t v = sm_draw(key, (uint64_t)l * (uint64_t)n + (uint64_t)r);
+        uint64_t v = sm_draw(key, (first + (uint64_t)l) * (uint64_t)n + (uint64_t)r);
         neg = (v >> 63) != 0;
     }
     if (l < ld) W0[r * ld + l] = (l < nvec) ? (neg ? T(-1) : T(1)) : T(0);
@@ -1011,20 +1011,82 @@ static uint32_t *kpm_bits(evsl_ctx *c, int nvec, int *st)
 }
 
 template <typename T>
-static int kpm_init_t(evsl_ctx *c, int nvec, uint64_t seed, T *W0)
+static int kpm_init_t(evsl_ctx *c, int nvec, uint64_t seed, T *W0, uint64_t first = 0)
 {
     int st = EVSL_OK;
     uint32_t *bits = kpm_bits(c, nvec, &st);
     if (st) return st;
     const int64_t total = c->A.n * (int64_t)(((nvec + 31) >> 5) * 32);
     k_kpm_init<T><<<blocks_for(total, 256), 256, 0, c->stream>>>(c->A.n, nvec, kpm_ld(nvec),
-                                                                 sm_key(seed, SM_STREAM_KPM), W0, bits);
+                                                                 sm_key(seed, SM_STREAM_KPM), first, W0, bits);
     c->launches++;
     return check_launch(c, "kpm_init");
 }
 
-int kpm_init_f64(evsl_ctx *c, int nvec, uint64_t seed, double *W0) { return kpm_init_t(c, nvec, seed, W0); }
-int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0) { return kpm_init_t(c, nvec, seed, W0); }
+int kpm_init_f64(evsl_ctx *c, int nvec, uint64_t seed, double *W0, uint64_t first)
+{
+    return kpm_init_t(c, nvec, seed, W0, first);
+}
+int kpm_init_f32(evsl_ctx *c, int nvec, uint64_t seed, float *W0, uint64_t first)
+{
+    return kpm_init_t(c, nvec, seed, W0, first);
+}
+
+// Per-probe sums sum_r v_l[r] W[r, l] of a row-major probe block (ld columns): block b adds its
+// KPM_DOT_ROWS rows in order for every probe, then out[l] = sum_b part[b][l] in block order.
+// The order of every probe's sum depends on n only, not on which other probes share the block.
+constexpr int KPM_DOT_ROWS = 2048;
+
+template <typename T>
+__global__ void k_kpm_probe_dots(int64_t n, int np, int ld, const uint32_t *__restrict__ bits,
+                                 const T *__restrict__ W, double *__restrict__ part)
+{
+    const int nw = (np + 31) >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * KPM_DOT_ROWS, r1 = min(n, r0 + KPM_DOT_ROWS);
+    for (int l = threadIdx.x; l < np; l += blockDim.x) {
+        double s = 0.0;
+        for (int64_t r = r0; r < r1; r++) {
+            const double w = (double)W[r * ld + l];
+            s += ((bits[r * nw + (l >> 5)] >> (l & 31)) & 1u) ? -w : w;
+        }
+        part[(int64_t)blockIdx.x * np + l] = s;
+    }
+}
+
+__global__ void k_kpm_probe_reduce(int np, int nblk, const double *__restrict__ part, double *__restrict__ out)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= np) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += part[(int64_t)b * np + l];
+    out[l] = s;
+}
+
+template <typename T>
+static int kpm_probe_dots_t(evsl_ctx *c, int np, const T *W, double *part, double *out)
+{
+    const int64_t n = c->A.n;
+    const int nblk = (int)((n + KPM_DOT_ROWS - 1) / KPM_DOT_ROWS);
+    int st = EVSL_OK;
+    uint32_t *bits = kpm_bits(c, np, &st);
+    if (st) return st;
+    k_kpm_probe_dots<T><<<nblk, 128, 0, c->stream>>>(n, np, kpm_ld(np), bits, W, part);
+    c->launches++;
+    EVSL_TRY(check_launch(c, "kpm_probe_dots"));
+    k_kpm_probe_reduce<<<blocks_for(np, 128), 128, 0, c->stream>>>(np, nblk, part, out);
+    c->launches++;
+    return check_launch(c, "kpm_probe_reduce");
+}
+
+int kpm_probe_dots_f64(evsl_ctx *c, int np, const double *W, double *part, double *out)
+{
+    return kpm_probe_dots_t(c, np, W, part, out);
+}
+int kpm_probe_dots_f32(evsl_ctx *c, int np, const float *W, double *part, double *out)
+{
+    return kpm_probe_dots_t(c, np, W, part, out);
+}
+int kpm_probe_dot_blocks(evsl_ctx *c) { return (int)((c->A.n + KPM_DOT_ROWS - 1) / KPM_DOT_ROWS); }
 
 template <typename T, bool DBL>
 static void launch_kpm(evsl_ctx *c, bool hat, const T *val, int mode, int nvec, int ld, const uint32_t *bits,

@@ -470,6 +470,73 @@ static int kpm_run(evsl_ctx *c, int M, int nvec, uint64_t seed, double lmin, dou
     return EVSL_OK;
 }
 
+// Per-probe KPM sums for probes first .. first + np - 1: the same recurrence as kpm_run on a
+// block of only these probes, with each probe's dot product v_l^T w_k formed separately in a
+// fixed order (kpm_probe_dots), so that a probe's values do not depend on the block it is in.
+template <typename T>
+static int kpm_probe_run(evsl_ctx *c, int M, int64_t first, int np, uint64_t seed, double lmin, double lmax,
+                         double *out)
+{
+    const int64_t n = c->A.n, N = n * (int64_t)kpm_ld(np);
+    const double cc = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+    int st = EVSL_OK;
+    T *W0 = (T *)ctx_ws(c, WS_W0, sizeof(T) * N, &st);
+    if (st) return st;
+    T *W1 = (T *)ctx_ws(c, WS_W1, sizeof(T) * N, &st);
+    if (st) return st;
+    const int nb = kpm_nblocks(c);
+    double *part = (double *)ctx_ws(c, WS_KPM_PART, sizeof(double) * (size_t)(M + 1) * nb, &st);
+    if (st) return st;
+    const int nd = kpm_probe_dot_blocks(c);
+    double *dpart = (double *)ctx_ws(c, WS_GEN_MU, sizeof(double) * ((size_t)nd * np + (size_t)(M + 1) * np), &st);
+    if (st) return st;
+    double *dk = dpart + (size_t)nd * np;      // (M + 1) x np: row k = the probes' sums of step k
+    const bool hat = ensure_mapped(c, cc, d, &st);
+    if (st) return st;
+    auto dots = [&](const T *W, int k) {
+        if constexpr (sizeof(T) == 8) return kpm_probe_dots_f64(c, np, (const double *)W, dpart, dk + (size_t)k * np);
+        else return kpm_probe_dots_f32(c, np, (const float *)W, dpart, dk + (size_t)k * np);
+    };
+    if constexpr (sizeof(T) == 8)
+        EVSL_TRY(kpm_init_f64(c, np, seed, (double *)W0, (uint64_t)first));
+    else
+        EVSL_TRY(kpm_init_f32(c, np, seed, (float *)W0, (uint64_t)first));
+    ProfGroup g;
+    prof_begin(c, EVSL_K_KPM_STEP, &g);
+    T *prev = W0, *cur = W1;
+    for (int k = 1; k <= M; k++) {
+        if constexpr (sizeof(T) == 8) {
+            if (k == 1)
+                EVSL_TRY(kpm_step_f64(c, 0, np, seed, (double *)W0, nullptr, (double *)W1, cc, 1.0 / d, part, 1, nb, hat));
+            else
+                EVSL_TRY(kpm_step_f64(c, 1, np, seed, (double *)cur, (double *)prev, (double *)prev, cc, 2.0 / d, part, k, nb, hat));
+        } else {
+            if (k == 1)
+                EVSL_TRY(kpm_step_f32(c, 0, np, seed, (float *)W0, nullptr, (float *)W1, cc, 1.0 / d, part, 1, nb, hat));
+            else
+                EVSL_TRY(kpm_step_f32(c, 1, np, seed, (float *)cur, (float *)prev, (float *)prev, cc, 2.0 / d, part, k, nb, hat));
+        }
+        if (k >= 2) std::swap(prev, cur);
+        // the newest block: W1 after step 1, `cur` after the swap of every later step
+        EVSL_TRY(dots(k == 1 ? W1 : cur, k));
+    }
+    prof_end(c, &g, M);
+    std::vector<double> h((size_t)(M + 1) * np, 0.0);
+    if (M >= 1) EVSL_TRY(d2h(c, h.data() + np, dk + np, sizeof(double) * (size_t)M * np));
+    for (int l = 0; l < np; l++) {
+        out[(size_t)l * (M + 1)] = (double)n;   // v^T v = n exactly for Rademacher probes
+        for (int k = 1; k <= M; k++) out[(size_t)l * (M + 1) + k] = h[(size_t)k * np + l];
+    }
+    return EVSL_OK;
+}
+
+int drv_kpm_probe(evsl_ctx *c, int degree, int64_t first, int nprobe, uint64_t seed, double lmin, double lmax,
+                  evsl_precision prec, double *out)
+{
+    if (prec == EVSL_FP64) return kpm_probe_run<double>(c, degree, first, nprobe, seed, lmin, lmax, out);
+    return kpm_probe_run<float>(c, degree, first, nprobe, seed, lmin, lmax, out);
+}
+
 int drv_kpm(evsl_ctx *c, int degree, int nvec, uint64_t seed, double lmin, double lmax,
             evsl_precision prec, double *mu, bool doubling)
 {

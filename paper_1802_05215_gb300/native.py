@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         "evsl_bounds": (i32, [P, i32, u64, P, P]),
         "evsl_kpm_dos": (i32, [P, i32, i32, u64, d, d, i32, P]),
         "evsl_kpm_dos_doubling": (i32, [P, i32, i32, u64, d, d, i32, P]),
+        "evsl_kpm_probe_moments": (i32, [P, i32, i64, i32, u64, d, d, i32, P]),
         "evsl_slice_by_dos": (i32, [P, i32, i64, d, d, d, d, i32, i32, P, P]),
         "evsl_cheb_filter_build": (i32, [d, d, d, d, P, P, P, i32]),
         "evsl_filter_apply": (i32, [P, P, i32, P, P, i32]),
@@ -370,6 +371,15 @@ class Context:
         fn = self.lib.evsl_kpm_dos_doubling if doubling else self.lib.evsl_kpm_dos
         self._check(fn(self.h, degree, nvec, seed, lmin, lmax, prec, _addr(mu)), "kpm_dos")
         return mu
+
+    def kpm_probe_moments(self, degree, first, nprobe, seed, lmin, lmax, prec=FP64):
+        """Per-probe KPM sums v_l^T T_k(Ahat) v_l of probes first .. first + nprobe - 1 (Sec. 2.1):
+        an nprobe x (degree + 1) array whose rows, gathered from any split of the probes and
+        added in probe order, give the same moments bitwise."""
+        out = np.zeros((nprobe, degree + 1))
+        self._check(self.lib.evsl_kpm_probe_moments(self.h, degree, first, nprobe, seed, lmin, lmax, prec,
+                                                    _addr(out)), "kpm_probe_moments")
+        return out
 
     def filter_apply(self, filt: Filter, X, Y, prec=FP64):
         """Y = rho(Ahat) X (Eq. (2.4)) for device blocks X, Y (n x nvec column-major, e.g. torch tensors

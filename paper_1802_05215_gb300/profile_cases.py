@@ -5,8 +5,9 @@
     python -m paper_1802_05215_gb300.profile_cases kpm       # KPM moment step, FP64 then FP32
     python -m paper_1802_05215_gb300.profile_cases multi     # 16-slice batched filter step, FP32
     python -m paper_1802_05215_gb300.profile_cases gen       # generalized step: solves with p(B)
+    python -m paper_1802_05215_gb300.profile_cases gemm      # tensor-core FP64 GEMM, Ritz shape
 
-Each case but `gen` runs on the 100^3 7-point Laplacian (n = 1e6, nnz = 6.94e6); `gen` uses the
+Each case but `gen` and `gemm` runs on the 100^3 7-point Laplacian (n = 1e6, nnz = 6.94e6); `gen` uses the
 1000^2 linear-element mass matrix (n = 1e6, nnz = 8.99e6).  Each prints the number of kernels
 the library launched.
 """
@@ -86,7 +87,36 @@ def gen():
     return ctx
 
 
-CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "gen": gen}
+def gemm():
+    """The restart's Ritz-vector product Y = Q S in the shape of a 100^3 slice scaled to
+    n = 100,000 rows (k = 1320 basis vectors, l = 720 candidates): one untimed and three timed
+    products on the tensor cores (digit splitting included), then three with the FP64 kernel;
+    prints the FP64-equivalent rate 2 n k l / time of each."""
+    import torch
+    from . import native
+    n, k, l = 100_000, 1320, 720
+    g = torch.Generator(device="cuda").manual_seed(0)
+    Q = torch.randn(k, n, dtype=torch.float64, device="cuda", generator=g) / n ** 0.5
+    S = torch.randn(l, k, dtype=torch.float64, device="cuda", generator=g) / k ** 0.5
+    Y = torch.empty(l, n, dtype=torch.float64, device="cuda")
+    ctx = native.Context(0)
+    for tc in (True, False):
+        ctx.set_tensor_gemm(tc)
+        ctx.dense_gemm(Q, S, Y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(3):
+            ctx.dense_gemm(Q, S, Y)
+        e1.record()
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) * 1e-3 / 3
+        print(f"gemm {'tensor-core' if tc else 'fp64 kernel'}: n={n} k={k} l={l}: {s * 1e3:.2f} ms = "
+              f"{2 * n * k * l / s / 1e12:.2f} TFLOP/s (FP64-equivalent)")
+    return ctx
+
+
+CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "gen": gen, "gemm": gemm}
 
 if __name__ == "__main__":
     name = sys.argv[1] if len(sys.argv) > 1 else "cheb"
