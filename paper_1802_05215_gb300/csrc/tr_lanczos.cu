@@ -255,6 +255,9 @@ public:
             cudaEventRecord(e1_, c_->stream);
             cudaEventSynchronize(e1_);
             t_restart_ += ev_ms(e0_, e1_) * 1e-3;
+            // the polish could not bring every in-slice pair to tol: solve the slice again with
+            // the FP64 filter, so that the result is the plain FP64 method's
+            if (status_ == EVSL_ERR_NOCONV) EVSL_TRY(resolve_fp64());
         }
         std::vector<int> perm(nlock_);
         std::iota(perm.begin(), perm.end(), 0);
@@ -779,6 +782,7 @@ private:
         int kb0 = 0;
         EVSL_TRY(orthonormalize(Q, k0, Ys, &kb0));
         std::vector<double> th, r2;
+        double best_rmax = 0.0;
         for (int cyc = 0; cyc < POLISH_CYCLES && kb0 > 0; cyc++) {
             // block Krylov basis Q[:, :Kt] and R = rho(Ahat) Q
             int off = 0, kb = kb0, Kt = 0;
@@ -877,6 +881,10 @@ private:
                 fprintf(stderr, "[evsl] polish cycle %d: basis=%d selected=%d pending=%d in_slice=%d max_res=%.3e\n",
                         cyc, Kt, ks, (int)pending, nin, rmax);
             if (ok || cyc + 1 == POLISH_CYCLES) break;
+            // a cycle that made the worst residual ten times larger has picked up mixtures
+            // of eigenvectors; more cycles would not recover, the caller falls back to FP64
+            if (cyc > 0 && rmax > 10.0 * best_rmax) break;
+            best_rmax = cyc == 0 ? rmax : std::min(best_rmax, rmax);
             // restart from the k0 Ritz vectors of rho with the largest mu
             kb0 = kr;
             EVSL_TRY(gemm_nn(c_, n_, kb0, Kt, Q, n_, Stop, Kt, Ys, n_));
@@ -910,6 +918,43 @@ private:
         nlock_ = (int)keep.size();
         if (nconv > cap_) status_ = EVSL_ERR_CAPACITY;
         else if (!all && status_ == EVSL_OK) status_ = EVSL_ERR_NOCONV;
+        return EVSL_OK;
+    }
+
+    // The FP32-filter run's fallback: a fresh FP64 thick-restart run of the same slice (its
+    // basis memory replaces this run's Krylov basis, which is no longer needed); its pairs,
+    // status and step counts become this run's.
+    int resolve_fp64()
+    {
+        if (verbose_) fprintf(stderr, "[evsl] FP64 polish left pairs above tol: the slice is solved again in FP64\n");
+        ctx_free(c_, Q_, sizeof(double) * n_ * (m_ + 1));
+        Q_ = nullptr;
+        evsl_lan_opts o = o_;
+        o.prec = EVSL_FP64;
+        SliceSolver S(c_, a_, b_, pol_, o, m_, cap_, right_closed_);
+        EVSL_TRY(S.init());
+        int st = EVSL_OK;
+        double *y = (double *)ctx_ws(c_, WS_LAN_VEC, sizeof(double) * n_ * 3, &st);
+        if (st) return st;
+        while (!S.done()) {
+            cudaEventRecord(e0_, c_->stream);
+            EVSL_TRY(filter_apply_dev(c_, pol_, 1, S.input(), y, EVSL_FP64, y + n_, y + 2 * n_, nullptr));
+            cudaEventRecord(e1_, c_->stream);
+            cudaEventSynchronize(e1_);
+            EVSL_TRY(S.consume(y, ev_ms(e0_, e1_) * 1e-3));
+        }
+        nlock_ = S.nlock_;
+        lam_l_ = S.lam_l_;
+        res_l_ = S.res_l_;
+        status_ = S.status_;
+        if (nlock_ > 0) EVSL_TRY(d2d(c_, U_, S.U_, sizeof(double) * n_ * nlock_));
+        its_ += S.its_;
+        nmv_ += S.nmv_;
+        npass_ += S.npass_;
+        nrestart_ += S.nrestart_;
+        t_filter_ += S.t_filter_;
+        t_orth_ += S.t_orth_;
+        t_restart_ += S.t_restart_;
         return EVSL_OK;
     }
 
