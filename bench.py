@@ -618,8 +618,8 @@ def run_serving(args):
         mats, reqs, spectra = serving_stream_5()
         desc = (f"{len(reqs)} Poisson-arriving slice requests (mean gap 1 s, 20..400 eigenvalues) over 2-D "
                 "Laplacians n = 1e4..1e6, 3-D Laplacians n = 1e5..1e6 and Anderson models W = 1.5..7.5, "
-                "n = 3e4..1e6, admitted under one 160 GiB HBM budget")
-        budget = 160 << 30
+                "n = 3e4..1e6, admitted under one 200 GiB HBM budget")
+        budget = 200 << 30
     server = serve.Server(mats, hbm_budget=budget, prec=native.FP32)
     server.run(reqs[:2], batched=True)                     # warm-up (module load, workspaces)
     modes = [("plain_fp64_fifo", False, native.FP64), ("batched_fp64", True, native.FP64),

@@ -718,17 +718,34 @@ int colscale_inv_sqrt(evsl_ctx *c, int64_t n, int k, double *Y, const double *nr
 }
 
 // Large products go to the tensor-core GEMM (FP64-accurate digit splitting); small ones, whose
-// splitting and launch costs would dominate, stay on the FP64 kernels below.
+// splitting and launch costs would dominate, stay on the FP64 kernels below, and so does a
+// product whose digit workspace does not fit under the HBM budget (same result to rounding).
 static bool use_tc(const evsl_ctx *c, int64_t M, int64_t N, int64_t K)
 {
     return c->tc_gemm && M >= 128 && N >= 16 && K >= 32 && 2.0 * (double)M * (double)N * (double)K >= 1e9;
+}
+
+static int try_tc(evsl_ctx *c, bool trans_a, int64_t M, int N, int64_t K, const double *A, int64_t lda,
+                  const double *B, int64_t ldb, double *C, int64_t ldc, int mode, bool *done)
+{
+    *done = false;
+    if (!use_tc(c, M, N, K)) return EVSL_OK;
+    const int st = gemm_tc(c, trans_a, M, N, K, A, lda, B, ldb, C, ldc, mode);
+    if (st == EVSL_ERR_NOMEM) {
+        c->err.clear();
+        return EVSL_OK;
+    }
+    *done = true;
+    return st;
 }
 
 int gemm_nn(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t lda, const double *B,
             int64_t ldb, double *C, int64_t ldc)
 {
     if (n <= 0 || l <= 0) return EVSL_OK;
-    if (use_tc(c, n, l, k)) return gemm_tc(c, false, n, l, k, A, lda, B, ldb, C, ldc, 0);
+    bool done = false;
+    EVSL_TRY(try_tc(c, false, n, l, k, A, lda, B, ldb, C, ldc, 0, &done));
+    if (done) return EVSL_OK;
     dim3 grid((unsigned)((n + GB_M - 1) / GB_M), (unsigned)((l + GB_N - 1) / GB_N));
     k_gemm_nn<false><<<grid, 256, 0, c->stream>>>(n, l, k, A, lda, B, ldb, C, ldc);
     c->launches++;
@@ -739,7 +756,9 @@ int gemm_nn_sub(evsl_ctx *c, int64_t n, int l, int k, const double *A, int64_t l
                 int64_t ldb, double *C, int64_t ldc)
 {
     if (n <= 0 || l <= 0 || k <= 0) return EVSL_OK;
-    if (use_tc(c, n, l, k)) return gemm_tc(c, false, n, l, k, A, lda, B, ldb, C, ldc, 1);
+    bool done = false;
+    EVSL_TRY(try_tc(c, false, n, l, k, A, lda, B, ldb, C, ldc, 1, &done));
+    if (done) return EVSL_OK;
     dim3 grid((unsigned)((n + GB_M - 1) / GB_M), (unsigned)((l + GB_N - 1) / GB_N));
     k_gemm_nn<true><<<grid, 256, 0, c->stream>>>(n, l, k, A, lda, B, ldb, C, ldc);
     c->launches++;
@@ -758,7 +777,9 @@ int gemm_tn(evsl_ctx *c, int64_t n, int p, int q, const double *A, int64_t lda, 
             int64_t ldb, double *C, int64_t ldc)
 {
     if (p <= 0 || q <= 0) return EVSL_OK;
-    if (use_tc(c, p, q, n)) return gemm_tc(c, true, p, q, n, A, lda, B, ldb, C, ldc, 0);
+    bool done = false;
+    EVSL_TRY(try_tc(c, true, p, q, n, A, lda, B, ldb, C, ldc, 0, &done));
+    if (done) return EVSL_OK;
     int tiles = ((p + GB_M - 1) / GB_M) * ((q + GB_N - 1) / GB_N);
     int64_t nsplit = std::max<int64_t>(1, (4 * (int64_t)c->dev_sm_count + tiles - 1) / tiles);
     nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, n / 1024));

@@ -251,7 +251,15 @@ public:
     {
         if (mixed_ && nlock_ > 0) {
             cudaEventRecord(e0_, c_->stream);
-            EVSL_TRY(polish());
+            const int pst = polish();
+            if (pst == EVSL_ERR_NOMEM) {
+                // no room for the polish's block workspaces under the HBM budget: the FP64
+                // re-solve below needs only a basis like the one this run already held
+                c_->err.clear();
+                status_ = EVSL_ERR_NOCONV;
+            } else if (pst != EVSL_OK) {
+                return pst;
+            }
             cudaEventRecord(e1_, c_->stream);
             cudaEventSynchronize(e1_);
             t_restart_ += ev_ms(e0_, e1_) * 1e-3;
