@@ -211,9 +211,10 @@ int evsl_filter_apply_noalloc(evsl_ctx *ctx, const evsl_polfilt *pol, int nvec, 
  * Lanczos phase then locks at max(tol, 1e-6) (relaxed up to 1e-4 if candidates stall) in the slice
  * widened by that level times ||A||, and an FP64 polish (restarted block Krylov iteration with
  * the FP64 filter, Rayleigh-Ritz with A on the converged Ritz vectors of rho) brings the pairs to
- * tol and decides membership; pairs still above tol after the polish are dropped and the call
- * returns EVSL_ERR_NOCONV.  The polish holds about 6 n (p + max(16, p/4)) doubles of workspace
- * for p locked pairs. */
+ * tol and decides membership.  If the polish cannot bring every in-slice pair to tol (or its
+ * workspace does not fit under the HBM budget), the slice is solved again with the FP64 filter
+ * and that run's pairs are returned, so the FP32 mode never returns fewer pairs than the FP64
+ * one.  The polish holds about 6 n (p + max(16, p/4)) doubles of workspace for p locked pairs. */
 typedef struct {
     int m;                  /* Krylov dimension before a restart                        */
     int maxit;              /* limit on Lanczos steps (0 = 20*m)                        */
