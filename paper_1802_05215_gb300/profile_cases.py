@@ -6,8 +6,9 @@
     python -m paper_1802_05215_gb300.profile_cases multi     # 16-slice batched filter step, FP32
     python -m paper_1802_05215_gb300.profile_cases gen       # generalized step: solves with p(B)
     python -m paper_1802_05215_gb300.profile_cases gemm      # tensor-core FP64 GEMM, Ritz shape
+    python -m paper_1802_05215_gb300.profile_cases kpm160    # FP32 KPM step, Anderson 160^3, 64 probes
 
-Each case but `gen` and `gemm` runs on the 100^3 7-point Laplacian (n = 1e6, nnz = 6.94e6); `gen` uses the
+Each case but `gen`, `gemm` and `kpm160` runs on the 100^3 7-point Laplacian (n = 1e6, nnz = 6.94e6); `gen` uses the
 1000^2 linear-element mass matrix (n = 1e6, nnz = 8.99e6).  Each prints the number of kernels
 the library launched.
 """
@@ -87,6 +88,18 @@ def gen():
     return ctx
 
 
+def kpm160():
+    """KPM degree 4 with 64 probes in FP32 on the Anderson model 160^3 (W = 2, n = 4.1e6): the
+    probe-block shape of the 200^3 benchmark (every lane of a row active) at about 3 GB."""
+    from . import inputs, native
+    A = inputs.anderson_3d(160, 2.0, 0)
+    ctx = native.Context(0)
+    ctx.set_csr(A)
+    lo, hi = ctx.bounds(40, 0)
+    ctx.kpm_dos(4, 64, 0, lo, hi, prec=native.FP32)
+    return ctx
+
+
 def gemm():
     """The restart's Ritz-vector product Y = Q S in the shape of a 100^3 slice scaled to
     n = 100,000 rows (k = 1320 basis vectors, l = 720 candidates): one untimed and three timed
@@ -116,7 +129,7 @@ def gemm():
     return ctx
 
 
-CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "gen": gen, "gemm": gemm}
+CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "gen": gen, "gemm": gemm, "kpm160": kpm160}
 
 if __name__ == "__main__":
     name = sys.argv[1] if len(sys.argv) > 1 else "cheb"
