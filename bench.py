@@ -292,6 +292,8 @@ def run_ours(args):
     e2e_total, e2e_s, _ = whole_job_rate(float(sum(r["nev"] for r in e2e_recs)), time.perf_counter() - t0, "cuda")
     # every rank's slice results on rank 0 (partition layer): counts checked there against the
     # closed form of the whole run, eigenvalues of all ranks included
+    for r in recs + e2e_recs:
+        r["exact"] = laplacian_count(3, 100, r["a"], r["b"], r["slice"] == NSLICES - 1)
     allrecs = partition.gather([{k: v for k, v in r.items() if k != "stats"} for r in recs + e2e_recs])
     if rank == 0:
         check_counts([r for part in allrecs for r in part], 3, 100, NSLICES)

@@ -331,15 +331,18 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
     const int sub = lane % LPR, rsub = lane / LPR;
     const int nw = (nvec + 31) >> 5;
     double mom = 0.0, mom2 = 0.0;
-    // FP32 with mapped values: the block owns a contiguous range of slices (neighbour rows it
-    // gathers were mostly read by its own warps a moment earlier, from L1), and each warp stages
-    // its next slice's entries in shared memory while it works on the current one
+    // FP32 with mapped values: each warp stages its next slice's entries in shared memory while
+    // it works on the current one.  Slices are taken grid-stride, so the warps of the whole grid
+    // work on one contiguous band of rows at a time and a neighbour row far away in the ordering
+    // (the +-nx^2 planes of a 3-D stencil) is read by the bands before and after it while it is
+    // still in L2; a contiguous range per block would spread the concurrent rows over the whole
+    // matrix and read such rows from HBM again.
     constexpr bool STAGED = (sizeof(T) == 4) && HAT && (PPL == 4);
     if constexpr (STAGED) {
         __shared__ __align__(16) KpmStage stage[WPB][2];
-        const int64_t per = (nslices + gridDim.x - 1) / gridDim.x;
-        const int64_t s_begin = (int64_t)blockIdx.x * per, s_end = min(nslices, s_begin + per);
-        int64_t s = s_begin + wib;
+        const int64_t gstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        const int64_t s_end = nslices;
+        int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         int buf = 0;
         // the first slice; a slice wider than WREG is handled directly (flagged by w_cur)
         int64_t sb_cur = 0;
@@ -349,8 +352,8 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
             w_cur = (int)((sptr[s + 1] - sb_cur) >> 5);
             if (w_cur <= WREG) kpm_stage_issue(stage[wib][0], sb_cur, w_cur, s, lane, (const float *)val, col, rlen);
         }
-        for (; s < s_end; s += WPB) {
-            const int64_t sn = s + WPB;
+        for (; s < s_end; s += gstride) {
+            const int64_t sn = s + gstride;
             int64_t sb_next = 0;
             int w_next = 0;
             if (sn < s_end) {

@@ -24,9 +24,9 @@
 //    output element; the sum F_ij is exact, and C_ij = 2^(e_i + f_j - 66) F_ij is rounded once
 //    to FP64 at the end.  The result is deterministic and independent of the tiling.
 //
-// Kernel: one CTA per 128 x 48 output tile, 320 threads.  Warp 0 issues TMA loads of one K-step
-// (16 wide) of all nine A digit tiles (128 x 16) and B digit tiles (48 x 16) into a four-stage
-// shared-memory ring (32-byte swizzle); warp 1 owns the TMEM allocation and issues 15 MMAs per
+// Kernel: one CTA per 128 x 48 output tile, 320 threads.  Warp 0 issues TMA loads of one K-block
+// (32 wide) of all nine A digit tiles (128 x 32) and B digit tiles (48 x 32) into a two-stage
+// shared-memory ring (64-byte swizzle); warp 1 owns the TMEM allocation and issues 15 MMAs per
 // K-step of 16: for A digit s, one MMA multiplies it by up to five B digit tiles stacked along N
 // (N <= 240), writing diagonals s+t..s+t+4 at once (diagonal d lives in TMEM columns
 // 48 (d - 2) .. 48 (d - 1)); warps 2-9 drain the accumulators after each chunk and finally
@@ -48,14 +48,14 @@ constexpr int OZ_S = 9;             // digits per element
 constexpr int OZ_BETA = 6;          // bits per digit
 constexpr int OZ_BM = 128;          // tile rows (MMA M)
 constexpr int OZ_BN = 48;           // tile columns (per diagonal in TMEM)
-constexpr int OZ_BK = 16;           // K per pipeline stage: one MMA K-step (32-byte rows)
-constexpr int OZ_KC = 448;          // K per exact chunk (28 stages)
+constexpr int OZ_BK = 32;           // K per pipeline stage (64-byte rows)
+constexpr int OZ_KC = 448;          // K per exact chunk (14 stages)
 constexpr int OZ_KB_PER_CHUNK = OZ_KC / OZ_BK;
-constexpr int OZ_STAGES = 4;
-constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;                    // 4096 B per digit
-constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;                    // 1536 B per digit
-constexpr int OZ_STAGE_A = OZ_S * OZ_A_TILE;                    // 36864 B
-constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_TILE + OZ_B_TILE);  // 50688 B
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;                    // 8192 B per digit
+constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;                    // 3072 B per digit
+constexpr int OZ_STAGE_A = OZ_S * OZ_A_TILE;                    // 73728 B
+constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_TILE + OZ_B_TILE);  // 101376 B
 constexpr int OZ_TMEM_COLS = 512;
 constexpr int OZ_THREADS = 320;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024 /* barriers */ + 1024 /* alignment */;
@@ -190,17 +190,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Shared-memory matrix descriptor of a K-major tile with 32-byte rows (one K-step of 16 BF16)
-// and the 32-byte swizzle: start address >> 4 (bits 0-13), leading offset 16 B (unused when K
-// fits in the swizzle row), stride 256 B between 8-row groups (bits 32-45), fixed 0b001 in
-// bits 46-48, swizzle code 6.
-__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr)
+// Shared-memory matrix descriptor of a K-major tile with 64-byte rows and the 64-byte swizzle:
+// start address >> 4 (bits 0-13), leading offset 16 B (unused when K fits in the swizzle row),
+// stride 512 B between 8-row groups (bits 32-45), fixed 0b001 in bits 46-48, swizzle code 4.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr)
 {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(256 >> 4) << 32;
+    d |= (uint64_t)(512 >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)6 << 61;
+    d |= (uint64_t)4 << 61;
     return d;
 }
 
@@ -301,12 +300,11 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
-    // bars: full[0..STAGES), empty[0..STAGES), tmem_full, tmem_empty, done
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * OZ_STAGES + 4);
-    volatile int *abort_flag = (volatile int *)(bars + 2 * OZ_STAGES + 5);
-    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[OZ_STAGES]);
-    const uint32_t tmem_full = smem_u32(&bars[2 * OZ_STAGES]), tmem_empty = smem_u32(&bars[2 * OZ_STAGES + 1]),
-                   done = smem_u32(&bars[2 * OZ_STAGES + 2]);
+    // bars: full[0..1], empty[0..1], tmem_full, tmem_empty, done
+    uint32_t *tmem_slot = (uint32_t *)(bars + 8);
+    volatile int *abort_flag = (volatile int *)(bars + 9);
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[2]);
+    const uint32_t tmem_full = smem_u32(&bars[4]), tmem_empty = smem_u32(&bars[5]), done = smem_u32(&bars[6]);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * OZ_BN;
@@ -315,10 +313,10 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int nchunk = (nkb + OZ_KB_PER_CHUNK - 1) / OZ_KB_PER_CHUNK;
 
     if (threadIdx.x == 0) {
-        for (int st = 0; st < OZ_STAGES; st++) {
-            mbar_init(full0 + 8 * st, 1);
-            mbar_init(empty0 + 8 * st, 1);
-        }
+        mbar_init(full0, 1);
+        mbar_init(full0 + 8, 1);
+        mbar_init(empty0, 1);
+        mbar_init(empty0 + 8, 1);
         mbar_init(tmem_full, 1);
         mbar_init(tmem_empty, 8);
         mbar_init(done, 1);
@@ -341,8 +339,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         int issued = 0;
         if (lane == 0) {
             for (int it = 0; it < nkb; it++) {
-                const int st = it % OZ_STAGES;
-                const uint32_t par = ((it / OZ_STAGES) & 1) ^ 1;
+                const int st = it & 1;
+                const uint32_t par = ((it >> 1) & 1) ^ 1;
                 if (!mbar_wait(empty0 + 8 * st, par, abort_flag)) {
                     timed_out = true;
                     break;
@@ -356,7 +354,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             if (timed_out) {
                 // let the copies already issued land before the shared memory is released
                 for (int it = std::max(0, issued - OZ_STAGES); it < issued; it++)
-                    mbar_wait(full0 + 8 * (it % OZ_STAGES), (it / OZ_STAGES) & 1, nullptr);
+                    mbar_wait(full0 + 8 * (it & 1), (it >> 1) & 1, nullptr);
             }
         }
     } else if (warp == 1) {
@@ -364,13 +362,13 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (lane == 0) {
             int issued_any = 0;
             for (int it = 0; it < nkb && !timed_out; it++) {
-                const int st = it % OZ_STAGES;
+                const int st = it & 1;
                 const int kb = it % OZ_KB_PER_CHUNK, chunk = it / OZ_KB_PER_CHUNK;
                 if (kb == 0 && chunk > 0 && !mbar_wait(tmem_empty, (chunk - 1) & 1, abort_flag)) {
                     timed_out = true;
                     break;
                 }
-                if (!mbar_wait(full0 + 8 * st, (it / OZ_STAGES) & 1, abort_flag)) {
+                if (!mbar_wait(full0 + 8 * st, (it >> 1) & 1, abort_flag)) {
                     timed_out = true;
                     break;
                 }
@@ -382,8 +380,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll
                     for (int g = 0; g < OZ_NGRP; g++) {
                         const Grp gr = c_grp[g];
-                        const uint64_t ad = sdesc_sw32(sa + (gr.s - 1) * OZ_A_TILE + ks * 32);
-                        const uint64_t bd = sdesc_sw32(sb + (gr.t0 - 1) * OZ_B_TILE + ks * 32);
+                        const uint64_t ad = sdesc_sw64(sa + (gr.s - 1) * OZ_A_TILE + ks * 32);
+                        const uint64_t bd = sdesc_sw64(sb + (gr.t0 - 1) * OZ_B_TILE + ks * 32);
                         const uint32_t col = (uint32_t)((gr.s + gr.t0 - 2) * OZ_BN);
                         const uint32_t acc = (kb == 0 && ks == 0 && g < OZ_NINIT) ? 0u : 1u;
                         umma_bf16(tmem_base + col, ad, bd, idesc_bf16(OZ_BM, OZ_BN * gr.nb), acc);
@@ -499,7 +497,7 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 3-D map over digit planes [S][rows][kp] (BF16): box 16 (k) x box_rows x 9 planes, 32-byte
+// 3-D map over digit planes [S][rows][kp] (BF16): box 32 (k) x box_rows x 9 planes, 64-byte
 // swizzle, zero fill past K and past the rows
 bool make_map(CUtensorMap *map, const uint16_t *base, int64_t rows, int64_t K, int64_t kp, int box_rows)
 {
@@ -511,7 +509,7 @@ bool make_map(CUtensorMap *map, const uint16_t *base, int64_t rows, int64_t K, i
     cuuint32_t estr[3] = {1, 1, 1};
     std::memset(map, 0, sizeof(*map));
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)base, dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
