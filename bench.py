@@ -635,8 +635,9 @@ def run_serving(args):
     server.run(reqs[:2], batched=True)                     # warm-up (module load, workspaces)
     modes = [("plain_fp64_fifo", False, native.FP64), ("batched_fp64", True, native.FP64),
              ("batched_fp32", True, native.FP32)]
-    if args.modes:
-        modes = [m for m in modes if m[0] in args.modes.split(",")]
+    if args.modes:   # the listed modes, in the listed order
+        byname = {m[0]: m for m in modes}
+        modes = [byname[k] for k in args.modes.split(",") if k in byname]
     out, bad = {}, []
     for mode, batched, prec in modes:
         t0 = time.perf_counter()
