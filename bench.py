@@ -704,18 +704,22 @@ def run_anderson_batched(args):
         t_batch = time.perf_counter() - t0
         print(json.dumps({"mode": "batched_fp32", "seconds": t_batch, "eigenpairs": sum(r["nev"] for r in batch)}),
               file=sys.stderr, flush=True)
-        t0 = time.perf_counter()
-        batch64 = ctx.chebLanTr_batch(slices, filters, ms, caps=caps, prec=native.FP64, right_closed=rc,
-                                      Ys=Ys, tol=TOL, allow_partial=True)
-        t_batch64 = time.perf_counter() - t0
-        print(json.dumps({"mode": "batched_fp64", "seconds": t_batch64, "eigenpairs": sum(r["nev"] for r in batch64)}),
-              file=sys.stderr, flush=True)
+        batch64, t_batch64 = [], float("nan")
+        if not args.modes or "batched_fp64" in args.modes.split(","):
+            t0 = time.perf_counter()
+            batch64 = ctx.chebLanTr_batch(slices, filters, ms, caps=caps, prec=native.FP64, right_closed=rc,
+                                          Ys=Ys, tol=TOL, allow_partial=True)
+            t_batch64 = time.perf_counter() - t0
+            print(json.dumps({"mode": "batched_fp64", "seconds": t_batch64,
+                              "eigenpairs": sum(r["nev"] for r in batch64)}), file=sys.stderr, flush=True)
         plain, t_plain = [], 0.0
         for j, ((a, b), f, m, cap) in enumerate(zip(slices, filters, ms, caps)):
             t0 = time.perf_counter()
             plain.append(ctx.chebLanTr(a, b, f, m=m, cap=cap, tol=TOL, right_closed=rc[j], Y=Ys[j],
                                        allow_partial=True))
             t_plain += time.perf_counter() - t0
+            print(json.dumps({"mode": "plain_fp64", "slice": pick[j], "nev": plain[-1]["nev"],
+                              "seconds": t_plain}), file=sys.stderr, flush=True)
     nb = sum(r["nev"] for r in batch)
     npl = sum(r["nev"] for r in plain)
     line = {"metric": "eigenpairs/s at resid<=1e-8, batched FP32-filter vs plain FP64",
@@ -725,9 +729,10 @@ def run_anderson_batched(args):
                        "slices_run": pick},
             "batched_fp32": {"eigenpairs": nb, "seconds": t_batch,
                              "max_res": max(float(r["res"].max()) for r in batch if r["nev"])},
-            "batched_fp64": {"eigenpairs": sum(r["nev"] for r in batch64), "seconds": t_batch64,
-                             "eigenpairs_per_s": sum(r["nev"] for r in batch64) / t_batch64,
-                             "max_res": max(float(r["res"].max()) for r in batch64 if r["nev"])},
+            "batched_fp64": ({"eigenpairs": sum(r["nev"] for r in batch64), "seconds": t_batch64,
+                              "eigenpairs_per_s": sum(r["nev"] for r in batch64) / t_batch64,
+                              "max_res": max(float(r["res"].max()) for r in batch64 if r["nev"])}
+                             if batch64 else None),
             "plain_fp64": {"eigenpairs": npl, "seconds": t_plain, "eigenpairs_per_s": npl / t_plain,
                            "max_res": max(float(r["res"].max()) for r in plain if r["nev"])},
             "counts_batched": [r["nev"] for r in batch], "counts_plain": [r["nev"] for r in plain],
