@@ -57,6 +57,9 @@ def lanczos_m(est: float) -> int:
     return int(max(2 * est + 40, 100))
 
 
+NOMINAL_HBM_GBS = 7900.0    # GB300 HBM3e nominal bandwidth, reported beside the measured-peak fraction
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -308,6 +311,7 @@ def run_ours(args):
     roof = {"bound": "hbm", "kernel": "cheb_step (fused SpMV + recurrence + axpy, FP64, s=1)",
             "achieved": achieved, "peak": hbm, "peak_source": peak_kind, "unit": "GB/s",
             "frac": achieved / hbm if achieved else None,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS if achieved else None,
             "alg_bytes_per_launch": alg, "mean_launch_us": per_launch_s * 1e6,
             "traffic": profiled_traffic()}
 

@@ -16,6 +16,10 @@
  *   - Device memory is owned by the context and freed by evsl_destroy.
  *   - A context is bound to one CUDA device and one CUDA stream; use it from one host thread
  *     at a time.  Calls are synchronous with respect to the host unless stated otherwise.
+ *   - The context's own stream is created non-blocking: it does not wait for work queued on
+ *     other streams, the legacy default stream included.  Device buffers passed to a call must
+ *     be complete when the call is made: synchronise their producer first, or produce them on
+ *     the context's stream (evsl_set_stream).
  *   - Dense vectors and blocks are column-major (vector j of an n x k block starts at j*n).
  *   - Nothing in this library falls back to the CPU: without a usable GPU the calls that need
  *     one return EVSL_ERR_CUDA.

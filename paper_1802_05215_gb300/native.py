@@ -4,7 +4,9 @@ Every numerical step runs inside libevsl_gb300.so; this module converts numpy ar
 torch CUDA tensors to plain pointers.  Loading fails loudly if the library is missing: there
 is no CPU fallback.  Each function mirrors the C call of the same name; the passage of
 arXiv:1802.05215 it implements is given in its docstring (and beside its declaration in the
-header).
+header).  A context runs on its own non-blocking CUDA stream, which does not wait for torch's,
+so every CUDA tensor handed to a call is preceded by a synchronisation of torch's current stream
+on its device (tensors produced on other streams must be complete before the call).
 """
 from __future__ import annotations
 
@@ -134,10 +136,15 @@ def load(build_if_missing: bool = True):
 
 
 def _ptr(a) -> int:
-    """Address of a numpy array or a torch tensor (host or device)."""
+    """Address of a numpy array or a torch tensor (host or device).  Before a CUDA tensor is
+    handed over, torch's current stream on its device is synchronised: the context's own stream
+    does not wait for it, and the tensor may still be being written there."""
     if isinstance(a, np.ndarray):
         return a.ctypes.data
     if hasattr(a, "data_ptr"):
+        if getattr(a, "is_cuda", False):
+            import torch
+            torch.cuda.current_stream(a.device).synchronize()
         return a.data_ptr()
     raise TypeError(type(a))
 

@@ -176,3 +176,45 @@ def test_solver_results_agree_with_and_without_tensor_core_gemm(nat):
         assert np.all(np.abs(r["lam"] - ex) <= 1e-9 * np.abs(ex))
         assert r["res"].max() <= 1e-8
     assert np.max(np.abs(out[0]["lam"] - out[1]["lam"])) <= 1e-11
+
+
+def test_dense_gemm_largest_polish_shapes_3300(nat):
+    # the largest products the FP32-filter polish forms: a Gram projection C = W^T Z of two
+    # n x 3300 blocks (3300 x 3300 result, contraction split into panels) and a Ritz-vector product
+    # Y = Q S with Q of n x 3300 and S of 3300 x 3300 (rows split into panels).  Sampled entries
+    # against exact dot products; the whole result against cuBLAS DGEMM,
+    # ||C - C_dgemm||_F <= 1e-15 ||W||_F ||Z||_F.  The operands are made by torch kernels that may
+    # still be running on torch's stream when the call is made: the binding orders them
+    import torch
+    rng = np.random.default_rng(17)
+    g = torch.Generator(device="cuda").manual_seed(17)
+    n, k = 40_000, 3300
+
+    def block(rows, cols, spread):
+        X = torch.randn((cols, rows), generator=g, dtype=torch.float64, device="cuda")
+        return X * torch.exp2(torch.randint(-spread, spread + 1, (cols, 1), generator=g, device="cuda").double())
+
+    with nat.Context(0) as ctx:
+        W, Z = block(n, k, 20), block(n, k, 20)           # 3300 columns of length n each
+        C = torch.empty((k, k), dtype=torch.float64, device="cuda")
+        ctx.dense_gemm(W, Z, C, trans_a=True)
+        ref = Z @ W.T
+        assert torch.linalg.norm(C - ref) <= 1e-15 * torch.linalg.norm(W) * torch.linalg.norm(Z)
+        i, j = rng.integers(0, k, 60), rng.integers(0, k, 60)
+        Wi, Zj = W[torch.tensor(i)].cpu().numpy(), Z[torch.tensor(j)].cpu().numpy()
+        Cij = C[torch.tensor(j), torch.tensor(i)].cpu().numpy()
+        worst = max(abs(Cij[t] - _exact(Wi[t], Zj[t])[0]) / _exact(Wi[t], Zj[t])[1] for t in range(60))
+        assert worst <= 2.0 ** -51, worst
+        del W, Z, C, ref
+
+        Q = block(n, k, 0) / np.sqrt(n)                     # k columns of length n
+        S = block(k, k, 0) / np.sqrt(k)                     # k columns of length k
+        Y = torch.empty((k, n), dtype=torch.float64, device="cuda")
+        ctx.dense_gemm(Q, S, Y)
+        ref = S @ Q
+        assert torch.linalg.norm(Y - ref) <= 1e-15 * torch.linalg.norm(Q) * torch.linalg.norm(S)
+        r, c = rng.integers(0, n, 60), rng.integers(0, k, 60)
+        Qr, Sc = Q[:, torch.tensor(r)].cpu().numpy(), S[torch.tensor(c)].cpu().numpy()
+        Yrc = Y[torch.tensor(c), torch.tensor(r)].cpu().numpy()
+        worst = max(abs(Yrc[t] - _exact(Qr[:, t], Sc[t])[0]) / _exact(Qr[:, t], Sc[t])[1] for t in range(60))
+        assert worst <= 2.0 ** -51, worst
