@@ -36,7 +36,8 @@ constexpr double PI = 3.14159265358979323846;
 // HAT: val holds the mapped (2/h)(M - c I) and u = x, so acc is already 2 Mhat x and the
 // epilogue is out = acc / 2 (MODE 0) or out = acc - xprev (MODE 1); cc and sc are unused.
 // out may alias xprev (each row reads xprev[r] before writing out[r]); u is gathered across
-// rows and must not alias out or y.
+// rows and must not alias out or y.  The matrix entries are loaded with the evict-first policy,
+// so that the vectors, which the next step reads again, stay in L2 between launches.
 template <int MODE, bool HAT>
 __global__ void __launch_bounds__(GTPB)
 k_gen_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr, const int32_t *__restrict__ col,
@@ -52,7 +53,7 @@ k_gen_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr, const i
 #pragma unroll 4
     for (int j = 0; j < w; j++) {
         const int64_t p = b0 + 32 * (int64_t)j + lane;
-        acc = fma(val[p], u[col[p]], acc);
+        acc = fma(__ldcs(val + p), u[__ldcs(col + p)], acc);
     }
     const int64_t r = s * 32 + lane;
     if (r >= n) return;

@@ -113,7 +113,10 @@ template <int MODE, bool HAT>
 constexpr bool needs_xr() { return MODE == 0 || (MODE == 1 && !HAT); }
 
 // Single vector: each nonzero is used once, so nothing is cached in registers; the loop is
-// unrolled so that several index loads and gathers are in flight per warp.
+// unrolled so that several index loads and gathers are in flight per warp.  The matrix entries
+// are read with the evict-first (streaming) policy: they are the bulk of the bytes and are not
+// reused within a step, while the vectors (x, xprev, out, y: 4 n words) are read again by the
+// next step of the recurrence and can stay in L2 between launches when n is small enough.
 template <typename T, int MODE, bool HAT>
 __global__ void __launch_bounds__(TPB)
 k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
@@ -129,7 +132,7 @@ k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
     const int32_t *cp = col + b0 + lane;
     T acc = T(0);
 #pragma unroll 4
-    for (int j = 0; j < w; j++) acc = fma_r(vp[32 * j], __ldg(x + cp[32 * j]), acc);
+    for (int j = 0; j < w; j++) acc = fma_r(__ldcs(vp + 32 * j), __ldg(x + __ldcs(cp + 32 * j)), acc);
     int64_t r = s * 32 + lane;
     if (r < n)
         cheb_epilogue<T, MODE, HAT>(r, acc, needs_xr<MODE, HAT>() ? x[r] : T(0), xprev, out, y, cc, sc, c0, cj);
@@ -381,8 +384,10 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                         // must precede this iteration's stores
                         T pA[PPL], pB[PPL];
                         uint32_t wdA = 0, wdB = 0;
-                        if (mode == 1 && actA) *reinterpret_cast<VL *>(pA) = *reinterpret_cast<const VL *>(xprev + oA);
-                        if (mode == 1 && actB) *reinterpret_cast<VL *>(pB) = *reinterpret_cast<const VL *>(xprev + oB);
+                        // xprev and out are streamed once per step (evict-first), so that they
+                        // do not push the gathered x rows out of L2
+                        if (mode == 1 && actA) *reinterpret_cast<VL *>(pA) = __ldcs(reinterpret_cast<const VL *>(xprev + oA));
+                        if (mode == 1 && actB) *reinterpret_cast<VL *>(pB) = __ldcs(reinterpret_cast<const VL *>(xprev + oB));
                         if (!DBL && actA) wdA = bits[gA * nw + (l >> 5)];
                         if (!DBL && actB) wdB = bits[gB * nw + (l >> 5)];
                         T aA[PPL], aB[PPL];
@@ -414,7 +419,7 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                             T wv[PPL];
 #pragma unroll
                             for (int q = 0; q < PPL; q++) wv[q] = (mode == 1) ? a[q] - pv[q] : T(0.5) * a[q];
-                            *reinterpret_cast<VL *>(out + (h ? oB : oA)) = *reinterpret_cast<const VL *>(wv);
+                            __stcs(reinterpret_cast<VL *>(out + (h ? oB : oA)), *reinterpret_cast<const VL *>(wv));
                             if (DBL) {
                                 T xo[PPL];   // x is read-only and never aliased by out
                                 *reinterpret_cast<VL *>(xo) = *reinterpret_cast<const VL *>(x + (h ? oB : oA));

@@ -1,6 +1,7 @@
 """Small fixed workloads for profiling single kernels with ncu (a few launches, < 1 GB).
 
     python -m paper_1802_05215_gb300.profile_cases cheb      # filter step: FP64 then FP32
+    python -m paper_1802_05215_gb300.profile_cases steptime  # live per-launch time of the filter step
     python -m paper_1802_05215_gb300.profile_cases gemv      # Gram-Schmidt GEMV-T / GEMV-N
     python -m paper_1802_05215_gb300.profile_cases kpm       # KPM moment step, FP64 then FP32
     python -m paper_1802_05215_gb300.profile_cases multi     # 16-slice batched filter step, FP32
@@ -36,6 +37,39 @@ def cheb():
     ctx.filter_apply(f, X, Y, prec=native.FP64)
     ctx.filter_apply(f, X, Y, prec=native.FP32)
     torch.cuda.synchronize()
+    return ctx
+
+
+def steptime():
+    """Live per-launch time of the fused filter step, FP64 then FP32: ten applications of the
+    degree-217 filter of [0.349, 0.391] (one slice of the 100^3 benchmark) after two warm-up ones,
+    timed by the library's CUDA events on its own stream; prints time, algorithmic GB/s and the
+    fraction of the measured copy peak."""
+    import json
+    import os
+    import torch
+    native, A, ctx = _ctx()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    try:
+        peak = json.load(open(os.path.join(root, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        peak = 6800.0
+    lo, hi = ctx.bounds(80, 0)
+    f = native.cheb_filter_build(0.34906336788172704, 0.39063876503853284, lo, hi)
+    X = torch.randn(1, A.n, dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    for prec, b in [(native.FP64, 8), (native.FP32, 4)]:
+        for _ in range(2):
+            ctx.filter_apply(f, X, Y, prec=prec)
+        ctx.profile(True)
+        for _ in range(10):
+            ctx.filter_apply(f, X, Y, prec=prec)
+        nl, ms = ctx.profile_get(native.K_CHEB_STEP)
+        ctx.profile(False)
+        alg = A.nnz * (b + 4) + 8 * (A.n + 1) + 5 * A.n * b
+        us = ms / nl * 1e3
+        print(f"steptime {'fp64' if b == 8 else 'fp32'}: degree {f.deg}, {nl} launches, {us:.3f} us per launch = "
+              f"{alg / us / 1e3:.1f} GB/s algorithmic = {alg / us / 1e3 / peak:.4f} of {peak} GB/s", flush=True)
     return ctx
 
 
@@ -129,7 +163,7 @@ def gemm():
     return ctx
 
 
-CASES = {"cheb": cheb, "gemv": gemv, "kpm": kpm, "multi": multi, "gen": gen, "gemm": gemm, "kpm160": kpm160}
+CASES = {"cheb": cheb, "steptime": steptime, "gemv": gemv, "kpm": kpm, "multi": multi, "gen": gen, "gemm": gemm, "kpm160": kpm160}
 
 if __name__ == "__main__":
     name = sys.argv[1] if len(sys.argv) > 1 else "cheb"
