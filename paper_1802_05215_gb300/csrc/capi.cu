@@ -181,6 +181,9 @@ int evsl_create(evsl_ctx **out, int device, size_t hbm_budget_bytes)
     c->stream = c->own_stream;
     cudaDeviceGetAttribute(&c->dev_sm_count, cudaDevAttrMultiProcessorCount, device);
     if (c->dev_sm_count <= 0) c->dev_sm_count = 1;
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+    c->l2_bytes = l2 > 0 ? l2 : 0;
     *out = c;
     return EVSL_OK;
 }

@@ -66,6 +66,7 @@ struct evsl_ctx {
     int64_t prof_launches[EVSL_K_COUNT] = {0};
     double prof_ms[EVSL_K_COUNT] = {0};
     int dev_sm_count = 0;
+    int64_t l2_bytes = 0;               // the device's L2 size
     std::vector<evsl_batch *> batches;  // live batches, destroyed with the context
     // CUDA graphs of single-vector filter applications, keyed by filter, buffers and matrix
     struct FilterGraph {
@@ -170,6 +171,7 @@ int kpm_step_f32(evsl_ctx *c, int mode, int nvec, uint64_t seed, const float *x,
                  const float *xprev, float *out, double cc, double sc, double *part, int k,
                  int nblk, bool hat,
                  bool dbl = false);
+bool stream_matrix(const evsl_ctx *c, int64_t nstored, int64_t n, int value_bytes);
 int kpm_nblocks(evsl_ctx *c);
 int convert_f64_to_f32(evsl_ctx *c, int64_t count, const double *x, float *y);
 int convert_f32_to_f64(evsl_ctx *c, int64_t count, const float *x, double *y);

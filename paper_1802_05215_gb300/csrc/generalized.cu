@@ -36,9 +36,11 @@ constexpr double PI = 3.14159265358979323846;
 // HAT: val holds the mapped (2/h)(M - c I) and u = x, so acc is already 2 Mhat x and the
 // epilogue is out = acc / 2 (MODE 0) or out = acc - xprev (MODE 1); cc and sc are unused.
 // out may alias xprev (each row reads xprev[r] before writing out[r]); u is gathered across
-// rows and must not alias out or y.  The matrix entries are loaded with the evict-first policy,
-// so that the vectors, which the next step reads again, stay in L2 between launches.
-template <int MODE, bool HAT>
+// rows and must not alias out or y.  STREAM: the matrix entries are loaded with the evict-first
+// policy, so that the vectors, which the next step reads again, stay in L2 between launches
+// (chosen by the launcher when one step's bytes exceed half of L2; below that, the normal
+// policy keeps the matrix in L2 as well).
+template <int MODE, bool HAT, bool STREAM>
 __global__ void __launch_bounds__(GTPB)
 k_gen_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr, const int32_t *__restrict__ col,
            const double *__restrict__ val, const double *u, const double *x, const double *xprev,
@@ -53,7 +55,9 @@ k_gen_step(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr, const i
 #pragma unroll 4
     for (int j = 0; j < w; j++) {
         const int64_t p = b0 + 32 * (int64_t)j + lane;
-        acc = fma(__ldcs(val + p), u[__ldcs(col + p)], acc);
+        const double v = STREAM ? __ldcs(val + p) : val[p];
+        const int ci = STREAM ? __ldcs(col + p) : col[p];
+        acc = fma(v, u[ci], acc);
     }
     const int64_t r = s * 32 + lane;
     if (r >= n) return;
@@ -97,8 +101,13 @@ int gen_step(evsl_ctx *c, const DevMatrix &M, const double *u, const double *x, 
              double *out, double *y, double cc, double sc, double c0, double cj)
 {
     const unsigned grid = (unsigned)((M.nslices * 32 + GTPB - 1) / GTPB);
-    k_gen_step<MODE, HAT><<<grid, GTPB, 0, c->stream>>>(M.n, M.nslices, M.sptr, M.col, HAT ? M.vhat : M.val, u, x,
-                                                         xprev, out, y, cc, sc, c0, cj);
+    const double *v = HAT ? M.vhat : M.val;
+    if (stream_matrix(c, M.nstored, M.n, 8))
+        k_gen_step<MODE, HAT, true><<<grid, GTPB, 0, c->stream>>>(M.n, M.nslices, M.sptr, M.col, v, u, x, xprev, out,
+                                                                   y, cc, sc, c0, cj);
+    else
+        k_gen_step<MODE, HAT, false><<<grid, GTPB, 0, c->stream>>>(M.n, M.nslices, M.sptr, M.col, v, u, x, xprev, out,
+                                                                    y, cc, sc, c0, cj);
     c->launches++;
     return check_launch(c, "generalized sparse step");
 }

@@ -113,11 +113,12 @@ template <int MODE, bool HAT>
 constexpr bool needs_xr() { return MODE == 0 || (MODE == 1 && !HAT); }
 
 // Single vector: each nonzero is used once, so nothing is cached in registers; the loop is
-// unrolled so that several index loads and gathers are in flight per warp.  The matrix entries
-// are read with the evict-first (streaming) policy: they are the bulk of the bytes and are not
-// reused within a step, while the vectors (x, xprev, out, y: 4 n words) are read again by the
-// next step of the recurrence and can stay in L2 between launches when n is small enough.
-template <typename T, int MODE, bool HAT>
+// unrolled so that several index loads and gathers are in flight per warp.
+// STREAM: the matrix entries are read with the evict-first (streaming) policy.  When one step's
+// bytes exceed L2, the entries (the bulk of them, not reused within a step) then leave room
+// for the vectors (x, xprev, out, y), which the next step of the recurrence reads again.  When
+// everything fits in L2 the normal policy keeps the matrix there too (the launcher decides).
+template <typename T, int MODE, bool HAT, bool STREAM>
 __global__ void __launch_bounds__(TPB)
 k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
              const int32_t *__restrict__ col, const T *__restrict__ val,
@@ -132,7 +133,11 @@ k_cheb_step1(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
     const int32_t *cp = col + b0 + lane;
     T acc = T(0);
 #pragma unroll 4
-    for (int j = 0; j < w; j++) acc = fma_r(__ldcs(vp + 32 * j), __ldg(x + __ldcs(cp + 32 * j)), acc);
+    for (int j = 0; j < w; j++) {
+        const T v = STREAM ? __ldcs(vp + 32 * j) : vp[32 * j];
+        const int ci = STREAM ? __ldcs(cp + 32 * j) : cp[32 * j];
+        acc = fma_r(v, __ldg(x + ci), acc);
+    }
     int64_t r = s * 32 + lane;
     if (r < n)
         cheb_epilogue<T, MODE, HAT>(r, acc, needs_xr<MODE, HAT>() ? x[r] : T(0), xprev, out, y, cc, sc, c0, cj);
@@ -384,10 +389,8 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                         // must precede this iteration's stores
                         T pA[PPL], pB[PPL];
                         uint32_t wdA = 0, wdB = 0;
-                        // xprev and out are streamed once per step (evict-first), so that they
-                        // do not push the gathered x rows out of L2
-                        if (mode == 1 && actA) *reinterpret_cast<VL *>(pA) = __ldcs(reinterpret_cast<const VL *>(xprev + oA));
-                        if (mode == 1 && actB) *reinterpret_cast<VL *>(pB) = __ldcs(reinterpret_cast<const VL *>(xprev + oB));
+                        if (mode == 1 && actA) *reinterpret_cast<VL *>(pA) = *reinterpret_cast<const VL *>(xprev + oA);
+                        if (mode == 1 && actB) *reinterpret_cast<VL *>(pB) = *reinterpret_cast<const VL *>(xprev + oB);
                         if (!DBL && actA) wdA = bits[gA * nw + (l >> 5)];
                         if (!DBL && actB) wdB = bits[gB * nw + (l >> 5)];
                         T aA[PPL], aB[PPL];
@@ -419,7 +422,7 @@ k_kpm_step(int mode, int64_t n, int64_t nslices, const int64_t *__restrict__ spt
                             T wv[PPL];
 #pragma unroll
                             for (int q = 0; q < PPL; q++) wv[q] = (mode == 1) ? a[q] - pv[q] : T(0.5) * a[q];
-                            __stcs(reinterpret_cast<VL *>(out + (h ? oB : oA)), *reinterpret_cast<const VL *>(wv));
+                            *reinterpret_cast<VL *>(out + (h ? oB : oA)) = *reinterpret_cast<const VL *>(wv);
                             if (DBL) {
                                 T xo[PPL];   // x is read-only and never aliased by out
                                 *reinterpret_cast<VL *>(xo) = *reinterpret_cast<const VL *>(x + (h ? oB : oA));
@@ -756,14 +759,26 @@ static ChebTile current_tile(evsl_ctx *c, int nvec)
     return sizeof(T) == 8 ? TILES_F64[t] : TILES_F32[t];
 }
 
+// Whether one single-vector step's bytes (matrix entries, row offsets, five vector streams)
+// exceed half of L2, so that the matrix is better streamed evict-first (k_cheb_step1).
+bool stream_matrix(const evsl_ctx *c, int64_t nstored, int64_t n, int value_bytes)
+{
+    const double step = (double)nstored * (value_bytes + 4) + 8.0 * (n + 1) + 5.0 * n * value_bytes;
+    return c->l2_bytes > 0 && step > 0.5 * (double)c->l2_bytes;
+}
+
 template <typename T, int MODE, bool HAT>
 static void launch_cheb(evsl_ctx *c, unsigned grid, int nvec, const T *val, const T *x, const T *xprev,
                         T *out, T *y, T cc, T sc, T c0, T cj, const T *ctab, const T *c0tab)
 {
     const DevMatrix &A = c->A;
     if (nvec == 1 && !ctab) {
-        k_cheb_step1<T, MODE, HAT><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, x, xprev,
-                                                               out, y, cc, sc, c0, cj);
+        if (stream_matrix(c, A.nstored, A.n, (int)sizeof(T)))
+            k_cheb_step1<T, MODE, HAT, true><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, x,
+                                                                         xprev, out, y, cc, sc, c0, cj);
+        else
+            k_cheb_step1<T, MODE, HAT, false><<<grid, TPB, 0, c->stream>>>(A.n, A.nslices, A.sptr, A.col, val, x,
+                                                                          xprev, out, y, cc, sc, c0, cj);
         return;
     }
     const ChebTile tl = current_tile<T>(c, nvec);
