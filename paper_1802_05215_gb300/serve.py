@@ -125,6 +125,7 @@ class Server:
         lock = threading.Condition()
         queues: dict[str, list[Request]] = {k: [] for k in self.mats}
         active = {k: 0 for k in self.mats}        # admitted, unfinished jobs per matrix
+        adding = [0]                               # batch.add calls in progress (all workers)
         remaining = [len(requests)]
         errors: list[BaseException] = []
         for M in self.mats.values():
@@ -141,32 +142,36 @@ class Server:
                         if remaining[0] == 0 or errors:
                             return
                         admit = list(queues[key])
-                    # admission in arrival order, as the device budget allows
-                    taken = []
+                    # admission in arrival order, as the device budget allows; a job counts as
+                    # active from the moment its add starts, so that no other worker takes the
+                    # device for idle while this one is allocating
                     for r in admit:
+                        f = M.filter(r.a, r.b)
+                        with lock:
+                            adding[0] += 1
                         try:
-                            M.batch.add(r.a, r.b, M.filter(r.a, r.b), krylov_dim(r.est),
-                                        right_closed=r.right_closed, tag=r.rid)
-                            started[r.rid] = now()
-                            taken.append(r)
+                            M.batch.add(r.a, r.b, f, krylov_dim(r.est), right_closed=r.right_closed, tag=r.rid)
                         except native.EvslError as e:
+                            with lock:
+                                adding[0] -= 1
                             if e.code != -2:
                                 raise
                             with lock:
-                                idle = sum(active.values()) == 0 and not taken and not M.batch.active
-                            if idle:
-                                # nothing runs anywhere and it still does not fit: it never will
-                                with lock:
+                                idle = sum(active.values()) == 0 and adding[0] == 0 and not M.batch.active
+                                if idle:
+                                    # nothing runs or is being admitted anywhere and it still does
+                                    # not fit: it never will
                                     out[r.rid] = Outcome(r.rid, r.arrival, now(), now(), 0, 0.0,
                                                          np.zeros(0), -2, None)
                                     queues[key].remove(r)
                                     remaining[0] -= 1
                                     lock.notify_all()
                             break             # keep arrival order: later requests wait too
-                    with lock:
-                        for r in taken:
+                        started[r.rid] = now()
+                        with lock:
+                            adding[0] -= 1
+                            active[key] += 1
                             queues[key].remove(r)
-                        active[key] += len(taken)
                     if not M.batch.active:
                         with lock:                # queued work that does not fit yet: wait for
                             lock.wait(0.005)      # another matrix's jobs to free memory

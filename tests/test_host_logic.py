@@ -59,6 +59,7 @@ class _FakeNative:
         from paper_1802_05215_gb300 import native
         self.EvslError = native.EvslError
         self.budget, self.used = 0, 0
+        self.slow_n = 0                     # contexts of this order take 0.1 s in batch.add
         self.steps = {}
         self.overlap = 0                    # most batches stepping at once
         self._stepping = 0
@@ -97,6 +98,9 @@ class _FakeNative:
                     if fake.budget and fake.used + need > fake.budget:
                         raise fake.EvslError(-2, "no room")
                     fake.used += need
+                if fake.slow_n and self.ctx.n == fake.slow_n:
+                    import time
+                    time.sleep(0.1)           # the memory is taken, the call has not returned
                 job = Job(tag, need, max(1, int(b - a)))
                 self.active.append(job)
                 return job
@@ -153,3 +157,21 @@ def test_server_admission_refuses_what_never_fits_and_overlaps_matrices(monkeypa
     assert fake.used == 0 and fake.budget == 0       # everything released, budget reset
     # request 4 waited behind the refused request 2 of the same matrix, never ahead of it
     assert out[4].start >= out[2].finish
+
+
+def test_server_admission_waits_for_a_job_still_being_admitted(monkeypatch):
+    # matrix q's job holds its memory while its add call is still running; a request of matrix
+    # p that does not fit beside it arrives meanwhile.  Nothing counts as active yet, but the
+    # request must wait (and run once q's job has finished), not be refused as never fitting.
+    from paper_1802_05215_gb300 import inputs
+    fake = _FakeNative()
+    fake.slow_n = 144
+    monkeypatch.setattr(serve, "native", fake)
+    mats = {"p": inputs.laplacian_2d(10), "q": inputs.laplacian_2d(12)}
+    srv = serve.Server(mats, hbm_budget=400_000)       # p job 212 kB, q job 305 kB: one at a time
+    reqs = [serve.Request(0, 0.00, "q", 0.0, 5.0, 10.0),
+            serve.Request(1, 0.02, "p", 0.0, 5.0, 10.0)]
+    out = srv.run(reqs, batched=True)
+    assert [o.status for o in out] == [0, 0] and [o.nev for o in out] == [3, 3]
+    assert out[1].start >= out[0].finish - 0.01          # p admitted after q released its memory
+    assert fake.used == 0
