@@ -523,10 +523,10 @@ int oz_launch(evsl_ctx *c, const uint16_t *Ad, const int *Ea, int64_t M, const u
     CUtensorMap ma, mb;
     if (!make_map(&ma, Ad, M, K, kp, OZ_BM) || !make_map(&mb, Bd, N, K, kp, OZ_BN))
         return ctx_fail(c, EVSL_ERR_CUDA, "tensor-core GEMM: cannot encode the TMA maps");
-    static std::once_flag attr_once;
-    std::call_once(attr_once, []() {
-        cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
-    });
+    // the attribute belongs to the current device: set it on every call (a host-side call of
+    // about a microsecond), not once per process
+    cudaError_t ea = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    if (ea != cudaSuccess) return ctx_cuda(c, ea, "tensor-core GEMM shared memory");
     dim3 grid((unsigned)((N + OZ_BN - 1) / OZ_BN), (unsigned)((M + OZ_BM - 1) / OZ_BM));
     k_oz_gemm<<<grid, OZ_THREADS, OZ_SMEM, c->stream>>>(ma, mb, M, N, K, Ea, Eb, C, ldc, mode, dflag);
     c->launches++;
