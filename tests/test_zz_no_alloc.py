@@ -31,6 +31,10 @@ def nat():
 
 
 def _noalloc(lib, ctx, f, X, Y):
+    # the raw C call: torch's work on X and Y (fills, copies) must be complete first, since the
+    # context's stream does not wait for torch's
+    import torch
+    torch.cuda.current_stream().synchronize()
     return lib.evsl_filter_apply_noalloc(ctx.h, ctypes.byref(f.pol), X.shape[0],
                                          ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()))
 
